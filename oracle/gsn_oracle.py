@@ -1,0 +1,390 @@
+"""FP64 CPU oracle for the binned Poisson likelihood of a multi-species spectral fit.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this module; only the
+tests, the smoke check and the CPU-baseline leg of the benchmark may call it.
+It shares no code with the GPU path: it is a plain, slow restatement of what
+the method computes, written from the GooStats paper (arXiv:1812.05686):
+
+* section 4.1, Eq. (LL): the binned Poisson log-likelihood plus Gaussian pull
+  terms, minimised over the fit parameters;
+* section 3.2 (the analytic-fit cost law T = T0 + k1 sum_i N_vis^i N_true^i):
+  each species' expected visible spectrum is its fine true-energy spectrum
+  convolved with the detector response;
+* section 2.3: the analytic response (light yield, non-linear quenching,
+  resolution) -- the formulas are stripped from the paper, so the readings
+  below are used (they are listed with the design notes);
+* section 4.3: species types Ana (smeared fine spectrum), AnaShift (shifted in
+  true energy, then smeared) and AnaPeak (a peak with free position and width);
+* section 2.2: parameter synchronisation across datasets, expressed as a slot
+  map from per-dataset slots to global parameters.
+
+Readings (the paper gives no formula for them):
+* quenching: Birks' law E_q(E) = int_0^E dE' / (1 + kB S(E')) with the
+  two-term stopping power S(E) = s0 + s1/E, integrated in closed form;
+* visible mean mu = LY * E_q(E) [p.e.]; variance sigma^2 = a + b mu + c mu^2;
+* Gaussian response: the bin integral of N(x; mu, sigma);
+* "generalized gamma" response: the gamma density with shape d = mu^2/sigma^2
+  and scale s = sigma^2/mu (mean mu, variance sigma^2), bin-integrated with the
+  regularised incomplete gamma function;
+* spectra are point-sampled at the fine centres and normalised to unit sum;
+  AnaShift moves the normalised spectrum up by round(shift / dE) fine bins;
+* AnaPeak: a Gaussian of position m and width w directly in p.e.;
+* NLL = sum_d sum_{j in window} [mu - n + n ln(n/mu)] + 1/2 sum_pulls ((p-c)/sigma)^2,
+  i.e. -ln L of Eq. (LL) up to a data-only constant, with the pull term read
+  as the usual Gaussian constraint (Eq. (LL) prints its sign/factor garbled).
+
+Parity status of the gradient of the generalized-gamma response with respect to
+the shape d: the derivative of the regularised incomplete gamma function with
+respect to its shape has no library routine, so it is taken by fourth-order
+central differences in d (pinned against arbitrary-precision values in the
+tests).  Everything else is evaluated from closed forms or library special
+functions.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import special
+
+KIND_ANA, KIND_ANA_SHIFT, KIND_ANA_PEAK = 0, 1, 2
+RES_GAUSS, RES_GAMMA = 0, 1
+_RESP = ("LY", "kB", "a", "b", "c")
+
+
+# ------------------------------------------------------------ quenching -----
+def quenched_energy(E, kB, s0, s1):
+    """Birks-quenched energy E_q(E) = int_0^E dE'/(1 + kB (s0 + s1/E')) (section 2.3, reading).
+
+    With alpha = 1 + kB s0 and beta = kB s1 the integrand is E'/(alpha E' + beta), so
+    E_q = E/alpha - (beta/alpha^2) ln(1 + alpha E / beta); kB = 0 gives E_q = E.
+    """
+    E = np.asarray(E, np.float64)
+    alpha = 1.0 + kB * s0
+    beta = kB * s1
+    if beta == 0.0:
+        return E / alpha
+    return E / alpha - (beta / alpha**2) * np.log1p(alpha * E / beta)
+
+
+def quenched_energy_dkB(E, kB, s0, s1):
+    """d E_q / d kB of the closed form above (chain rule through alpha and beta)."""
+    E = np.asarray(E, np.float64)
+    alpha = 1.0 + kB * s0
+    beta = kB * s1
+    L = np.log1p(alpha * E / beta)
+    d_alpha = -E / alpha**2 + 2.0 * beta * L / alpha**3 - E * beta / (alpha**2 * (beta + alpha * E))
+    d_beta = -L / alpha**2 + E / (alpha * (beta + alpha * E))
+    return s0 * d_alpha + s1 * d_beta
+
+
+# ------------------------------------------------------------- spectra ------
+def species_spectra(work):
+    """Normalised (and, for AnaShift, shifted) fine spectra S'[s, k] (section 4.3, reading).
+
+    Rows of AnaPeak species are zero (they do not pass through the response).
+    """
+    E = np.asarray(work["fine_centres"], np.float64)
+    f = np.asarray(work["spectra"], np.float64)
+    S = np.zeros_like(f)
+    dE = (E[-1] - E[0]) / (E.size - 1) if E.size > 1 else 1.0
+    for s in range(f.shape[0]):
+        kind = int(work["kind"][s])
+        if kind == KIND_ANA_PEAK:
+            continue
+        tot = f[s].sum()
+        row = f[s] / tot if tot > 0 else np.zeros_like(f[s])
+        if kind == KIND_ANA_SHIFT:
+            n = int(math.floor(work["shift"][s] / dE + 0.5))
+            shifted = np.zeros_like(row)
+            if n >= 0:
+                if n < row.size:
+                    shifted[n:] = row[: row.size - n]
+            else:
+                shifted[: row.size + n] = row[-n:]
+            row = shifted
+        S[s] = row
+    return S
+
+
+# ------------------------------------------------------------ responses -----
+def _norm_cdf_diff(lo, hi):
+    """Phi(hi) - Phi(lo), taking upper tails where both points lie above 0."""
+    upper = lo >= 0.0
+    return np.where(upper, special.ndtr(-lo) - special.ndtr(-hi), special.ndtr(hi) - special.ndtr(lo))
+
+
+def response_gauss(edges, mu, sigma):
+    """R[j, k] = int_{x_j}^{x_{j+1}} N(x; mu_k, sigma_k) dx (section 2.3, reading)."""
+    x = np.asarray(edges, np.float64)[:, None]
+    z = (x - mu[None, :]) / sigma[None, :]
+    return _norm_cdf_diff(z[:-1], z[1:])
+
+
+def _gamma_cdf_diff(d, lo, hi):
+    """P(d, hi) - P(d, lo) with the regularised incomplete gamma, upper tails above the mean."""
+    upper = lo >= d
+    return np.where(upper, special.gammaincc(d, lo) - special.gammaincc(d, hi),
+                    special.gammainc(d, hi) - special.gammainc(d, lo))
+
+
+def gamma_shape_scale(mu, var):
+    """Moment matching: shape d = mu^2/var, scale s = var/mu (mean mu, variance var)."""
+    return mu * mu / var, var / mu
+
+
+def response_gamma(edges, mu, var):
+    """R[j, k] = P(d_k, x_{j+1}/s_k) - P(d_k, x_j/s_k), gamma density of mean mu, variance var."""
+    d, s = gamma_shape_scale(mu, var)
+    y = np.clip(np.asarray(edges, np.float64), 0.0, None)[:, None] / s[None, :]
+    dd = np.broadcast_to(d[None, :], y.shape)
+    return _gamma_cdf_diff(dd[:-1], y[:-1], y[1:])
+
+
+def _gamma_P_dshape(d, y):
+    """dP(d, y)/dd by fourth-order central differences in d (see module docstring)."""
+    h = 2e-3 * np.minimum(d, np.sqrt(np.maximum(d, 1.0)))
+    h = np.minimum(h, d / 4.0)
+    f = lambda dd: special.gammainc(dd, y)
+    return (8.0 * (f(d + h) - f(d - h)) - (f(d + 2 * h) - f(d - 2 * h))) / (12.0 * h)
+
+
+def _gamma_pdf_times_y(d, y):
+    """p(d, y) * y with p the standard gamma density y^(d-1) e^-y / Gamma(d); 0 at y = 0."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v = np.exp(d * np.log(y) - y - special.gammaln(d))
+    return np.where(y > 0.0, v, 0.0)
+
+
+def peak_profile(edges, m, w):
+    """AnaPeak: int over each bin of N(x; m, w) in p.e. (section 4.3, reading)."""
+    z = (np.asarray(edges, np.float64) - m) / w
+    return _norm_cdf_diff(z[:-1], z[1:])
+
+
+# ------------------------------------------------------- parameter map ------
+def dataset_values(work, params, d):
+    """Per-dataset slot values from the global parameters (section 2.2 synchronisation)."""
+    sm = np.asarray(work["slot_map"])[d]
+    vals = np.full(sm.size, np.nan)
+    used = sm >= 0
+    vals[used] = np.asarray(params, np.float64)[sm[used]]
+    return vals
+
+
+def _unpack(work, vals):
+    S = np.asarray(work["spectra"]).shape[0]
+    rates = vals[:S]
+    resp = dict(zip(_RESP, vals[S:S + 5]))
+    peaks = vals[S + 5:].reshape(S, 2)
+    return rates, resp, peaks
+
+
+def column_mean_var(work, resp):
+    """Per fine column: visible mean mu_k [p.e.] and resolution variance sigma_k^2."""
+    E = np.asarray(work["fine_centres"], np.float64)
+    Eq = quenched_energy(E, resp["kB"], work["birks_s0"], work["birks_s1"])
+    mu = resp["LY"] * Eq
+    var = resp["a"] + resp["b"] * mu + resp["c"] * mu * mu
+    return Eq, mu, var
+
+
+def response_matrix(work, edges, resp):
+    """Detector response matrix R[j, k] of a dataset (section 2.3 / 2.5 'two-dimensional mesh')."""
+    _, mu, var = column_mean_var(work, resp)
+    if np.any(var <= 0) or np.any(mu <= 0):
+        raise FloatingPointError("non-positive mean or variance")
+    if int(work["resolution"]) == RES_GAUSS:
+        return response_gauss(edges, mu, np.sqrt(var))
+    return response_gamma(edges, mu, var)
+
+
+# --------------------------------------------------------- expectation ------
+def expected_per_species(work, params, d):
+    """Expected counts per bin and species of dataset d, shape (J, S) (section 3.1 validation quantity).
+
+    Column s holds eps_d r_s sum_k R[j,k] S'[s,k] for Ana/AnaShift species and
+    eps_d r_s * peak_j(m_s, w_s) for AnaPeak species; zero where mask[s, d] = 0.
+    """
+    vals = dataset_values(work, params, d)
+    rates, resp, peaks = _unpack(work, vals)
+    edges = np.asarray(work["edges"][d], np.float64)
+    eps = float(work["exposure"][d])
+    Sp = species_spectra(work)
+    R = response_matrix(work, edges, resp)
+    J, S = edges.size - 1, Sp.shape[0]
+    out = np.zeros((J, S))
+    for s in range(S):
+        if not work["mask"][s][d]:
+            continue
+        if int(work["kind"][s]) == KIND_ANA_PEAK:
+            out[:, s] = eps * rates[s] * peak_profile(edges, peaks[s, 0], peaks[s, 1])
+        else:
+            out[:, s] = eps * rates[s] * (R @ Sp[s])
+    return out
+
+
+def expected_counts(work, params, d):
+    """mu_dj: the rate-weighted sum over species (section 3.2 analytic fit)."""
+    return expected_per_species(work, params, d).sum(axis=1)
+
+
+# ------------------------------------------------------------ likelihood ----
+def poisson_term(mu, n):
+    """mu - n + n ln(n/mu), i.e. -ln Poisson(n; mu) up to its value at mu = n (Eq. LL)."""
+    mu = np.asarray(mu, np.float64)
+    n = np.asarray(n, np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where(n > 0, mu - n + n * np.log(n / mu), mu)
+    return np.where((n > 0) & (mu <= 0), np.inf, t)
+
+
+def pull_term(work, params):
+    p = np.asarray(params, np.float64)
+    idx = np.asarray(work["pull_param"], np.int64)
+    if idx.size == 0:
+        return 0.0
+    r = (p[idx] - np.asarray(work["pull_centre"])) / np.asarray(work["pull_width"])
+    return 0.5 * float(np.sum(r * r))
+
+
+def _windows(work, windows):
+    D = len(work["edges"])
+    if windows is None:
+        return [(int(work["win_lo"][d]), int(work["win_hi"][d])) for d in range(D)]
+    return [(int(windows[d][0]), int(windows[d][1])) for d in range(D)]
+
+
+def _split_counts(work, counts):
+    if isinstance(counts, (list, tuple)):
+        return [np.asarray(c, np.float64) for c in counts]
+    c = np.asarray(counts, np.float64)
+    out, o = [], 0
+    for e in work["edges"]:
+        J = len(e) - 1
+        out.append(c[o:o + J]); o += J
+    return out
+
+
+def nll(work, params, counts, windows=None):
+    """NLL = sum_d sum_{j in window_d} [mu - n + n ln(n/mu)] + 1/2 sum pulls^2 (section 4.1, Eq. LL)."""
+    cs = _split_counts(work, counts)
+    total = 0.0
+    for d, (lo, hi) in enumerate(_windows(work, windows)):
+        if hi <= lo:
+            continue
+        mu = expected_counts(work, params, d)
+        total += float(np.sum(poisson_term(mu[lo:hi], cs[d][lo:hi])))
+    return total + pull_term(work, params)
+
+
+# -------------------------------------------------------------- gradient ----
+def nll_grad(work, params, counts, windows=None):
+    """Analytic gradient dNLL/dtheta by the chain rule (same readings as nll()).
+
+    dNLL/dmu_dj = 1 - n_dj/mu_dj inside the window; mu_dj depends on the
+    rates linearly, on (LY, kB, a, b, c) through every column's mean and
+    variance, and on (m, w) of AnaPeak species through the peak profile.
+    """
+    params = np.asarray(params, np.float64)
+    cs = _split_counts(work, counts)
+    P = int(work["n_params"])
+    g = np.zeros(P)
+    Sp = species_spectra(work)
+    E = np.asarray(work["fine_centres"], np.float64)
+    S = Sp.shape[0]
+    for d, (lo, hi) in enumerate(_windows(work, windows)):
+        if hi <= lo:
+            continue
+        vals = dataset_values(work, params, d)
+        rates, resp, peaks = _unpack(work, vals)
+        edges = np.asarray(work["edges"][d], np.float64)
+        eps = float(work["exposure"][d])
+        mask = np.asarray(work["mask"])[:, d].astype(bool)
+        n = cs[d]
+        mu = expected_counts(work, params, d)
+        w = np.zeros(edges.size - 1)
+        w[lo:hi] = 1.0 - n[lo:hi] / mu[lo:hi]
+        gs = np.zeros(vals.size)  # gradient wrt the dataset's slots
+        # smeared species
+        Eq, mu_k, var_k = column_mean_var(work, resp)
+        smeared = mask & (np.asarray(work["kind"]) != KIND_ANA_PEAK)
+        T = eps * (rates[smeared][:, None] * Sp[smeared]).sum(axis=0) if smeared.any() else np.zeros(E.size)
+        R = response_matrix(work, edges, resp)
+        u = w @ R  # u_k = sum_j w_j R_jk
+        for s in np.nonzero(smeared)[0]:
+            gs[s] += eps * float(Sp[s] @ u)
+        # response parameters through (mu_k, var_k)
+        x = edges[:, None]
+        if int(work["resolution"]) == RES_GAUSS:
+            sig = np.sqrt(var_k)
+            z = (x - mu_k[None, :]) / sig[None, :]
+            phi = np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+            dR_dmu = -(phi[1:] - phi[:-1]) / sig[None, :]
+            dR_dsig = -(z[1:] * phi[1:] - z[:-1] * phi[:-1]) / sig[None, :]
+            g_mu = (w @ dR_dmu) * T
+            g_sig = (w @ dR_dsig) * T
+            g_var = g_sig / (2.0 * sig)
+        else:
+            dsh, sc = gamma_shape_scale(mu_k, var_k)
+            y = np.clip(edges, 0.0, None)[:, None] / sc[None, :]
+            dd = np.broadcast_to(dsh[None, :], y.shape)
+            Pd = _gamma_P_dshape(dd, y)
+            py = _gamma_pdf_times_y(dd, y)
+            dR_dd = Pd[1:] - Pd[:-1]
+            dR_ds = -(py[1:] - py[:-1]) / sc[None, :]
+            g_d = (w @ dR_dd) * T
+            g_s = (w @ dR_ds) * T
+            g_mu = g_d * (2.0 * mu_k / var_k) + g_s * (-var_k / mu_k**2)
+            g_var = g_d * (-(mu_k**2) / var_k**2) + g_s / mu_k
+        g_mu_tot = g_mu + g_var * (resp["b"] + 2.0 * resp["c"] * mu_k)
+        base = S
+        gs[base + 0] += float(g_mu_tot @ Eq)
+        gs[base + 1] += float(g_mu_tot @ (resp["LY"] * quenched_energy_dkB(E, resp["kB"], work["birks_s0"], work["birks_s1"])))
+        gs[base + 2] += float(g_var.sum())
+        gs[base + 3] += float(g_var @ mu_k)
+        gs[base + 4] += float(g_var @ (mu_k * mu_k))
+        # peak species
+        for s in np.nonzero(mask & (np.asarray(work["kind"]) == KIND_ANA_PEAK))[0]:
+            m, wd = peaks[s]
+            zz = (edges - m) / wd
+            ph = np.exp(-0.5 * zz * zz) / math.sqrt(2.0 * math.pi)
+            prof = _norm_cdf_diff(zz[:-1], zz[1:])
+            gs[s] += eps * float(w @ prof)
+            gs[base + 5 + 2 * s] += eps * rates[s] * float(w @ (-(ph[1:] - ph[:-1]) / wd))
+            gs[base + 5 + 2 * s + 1] += eps * rates[s] * float(w @ (-(zz[1:] * ph[1:] - zz[:-1] * ph[:-1]) / wd))
+        sm = np.asarray(work["slot_map"])[d]
+        for slot, pidx in enumerate(sm):
+            if pidx >= 0:
+                g[pidx] += gs[slot]
+    idx = np.asarray(work["pull_param"], np.int64)
+    for i, p in enumerate(idx):
+        g[p] += (params[p] - work["pull_centre"][i]) / work["pull_width"][i] ** 2
+    return g
+
+
+def nll_grad_fd(work, params, counts, windows=None, rel=1e-5, which=None):
+    """Richardson-extrapolated central differences of nll() (a self-check of nll_grad)."""
+    params = np.asarray(params, np.float64)
+    idx = range(params.size) if which is None else which
+    g = np.full(params.size, np.nan)
+    for i in idx:
+        h = rel * (abs(params[i]) if params[i] != 0 else 1e-3)
+
+        def f(t):
+            p = params.copy(); p[i] += t
+            return nll(work, p, counts, windows)
+        d1 = (f(h) - f(-h)) / (2 * h)
+        d2 = (f(2 * h) - f(-2 * h)) / (4 * h)
+        g[i] = (4.0 * d1 - d2) / 3.0
+    return g
+
+
+# ----------------------------------------------------------------- batch ----
+def nll_batch(work, params, counts, windows):
+    """Per-toy NLL for a batch: params (T, P), counts (T, sum J_d), windows (T, D, 2)."""
+    return np.array([nll(work, params[t], counts[t], windows[t]) for t in range(len(params))])
+
+
+def nll_grad_batch(work, params, counts, windows):
+    return np.array([nll_grad(work, params[t], counts[t], windows[t]) for t in range(len(params))])

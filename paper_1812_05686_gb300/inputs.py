@@ -1,0 +1,258 @@
+"""Seeded synthetic workloads for the binned spectral-fit likelihood.
+
+This module only *draws inputs*: fine true-energy spectra shaped like the
+species of a liquid-scintillator solar-neutrino fit (section 4.3 of the paper:
+beta decays, mono-energetic lines, Compton-like shoulders, exponentials, a flat
+pile-up-like term, an alpha peak and a positron emitter), bin edges, exposures,
+parameter points, fit windows and Poisson counts drawn from a caller-supplied
+mean.  It holds none of the likelihood method's arithmetic (no quenching, no
+resolution, no convolution, no likelihood): the expected counts that the
+Poisson draws need are passed in by the caller.
+
+Both the oracle tests and the GPU path consume the dictionaries built here, so
+the integer codes below are interface values, not implementation details.
+
+Workload dictionary keys
+------------------------
+fine_centres (K,)        ascending fine true-energy centres [MeV]
+spectra      (S, K)      unnormalised species shapes at the centres
+kind         (S,)        0 = Ana, 1 = AnaShift, 2 = AnaPeak (section 4.3)
+shift        (S,)        true-energy shift of AnaShift species [MeV]
+mask         (S, D)      1 where species s contributes to dataset d
+edges        [D] arrays  visible-energy bin edges [p.e.], ascending
+exposure     (D,)        exposure of each dataset (section 4.1)
+win_lo/win_hi (D,)       default fit window [lo, hi) in bins
+resolution   int         0 = Gaussian, 1 = generalized gamma
+birks_s0/s1  float       stopping-power model S(E) = s0 + s1/E [MeV/cm, MeV^2/cm]
+n_params     int         number of global fit parameters
+slot_map     (D, 3S+5)   global parameter index of each per-dataset slot:
+                         [rate_0..rate_{S-1}, LY, kB, a, b, c, m_0, w_0, ..., m_{S-1}, w_{S-1}]
+                         (-1 = unused: peak slots of non-peak species, rates of
+                         species absent from the dataset)
+pull_param/pull_centre/pull_width   Gaussian pull terms (section 4.1, Eq. LL)
+theta0       (P,)        generating parameter point
+param_names  list[str]
+"""
+from __future__ import annotations
+
+import numpy as np
+
+KIND_ANA, KIND_ANA_SHIFT, KIND_ANA_PEAK = 0, 1, 2
+RES_GAUSS, RES_GAMMA = 0, 1
+
+# Stopping-power model constants used by every workload (MeV/cm and MeV^2/cm):
+# roughly electron dE/dx in a ~0.88 g/cm^3 organic scintillator.
+BIRKS_S0 = 1.55
+BIRKS_S1 = 0.155
+
+
+def n_slots(n_species: int) -> int:
+    """Per-dataset slot count: S rates, 5 response parameters, 2 peak slots per species."""
+    return 3 * n_species + 5
+
+
+def slot_rate(s: int) -> int:
+    return s
+
+
+def slot_response(n_species: int, which: str) -> int:
+    return n_species + ("LY", "kB", "a", "b", "c").index(which)
+
+
+def slot_peak(n_species: int, s: int, which: str) -> int:
+    return n_species + 5 + 2 * s + (0 if which == "m" else 1)
+
+
+# ----------------------------------------------------------------- shapes ----
+def fine_grid(n_fine: int, e_max: float) -> np.ndarray:
+    """Centres (k + 1/2) * dE of a uniform fine grid on [0, e_max) MeV."""
+    return (np.arange(n_fine, dtype=np.float64) + 0.5) * (e_max / n_fine)
+
+
+def shape_beta(E, Q):
+    """Allowed-beta-like shape E^2 (Q - E)^2 below the endpoint Q."""
+    return np.where(E < Q, E * E * (Q - E) ** 2, 0.0)
+
+
+def shape_line(E, E0):
+    """Mono-energetic line: 1 at the fine centre nearest E0 (ties to the lower index)."""
+    out = np.zeros_like(E)
+    out[int(np.argmin(np.abs(E - E0)))] = 1.0
+    return out
+
+
+def shape_expo(E, tau):
+    return np.exp(-E / tau)
+
+
+def shape_flat(E):
+    return np.ones_like(E)
+
+
+def shape_shoulder(E, edge):
+    """Flat up to a Compton-like edge, zero above it."""
+    return np.where(E < edge, 1.0, 0.0)
+
+
+def unit_edges(n_bins: int) -> np.ndarray:
+    """Bin edges 0, 1, ..., n_bins p.e. (1 p.e. wide bins)."""
+    return np.arange(n_bins + 1, dtype=np.float64)
+
+
+# -------------------------------------------------------------- workloads ----
+def _slot_map_shared(n_species, n_datasets, n_rates_offset=0, peaks=()):
+    """Every dataset shares every parameter (full synchronisation, section 2.2).
+
+    Global parameter order: rates 0..S-1, LY, kB, a, b, c, then (m, w) per peak.
+    """
+    ns = n_slots(n_species)
+    sm = -np.ones((n_datasets, ns), dtype=np.int32)
+    for d in range(n_datasets):
+        for s in range(n_species):
+            sm[d, slot_rate(s)] = s
+        for i, w in enumerate(("LY", "kB", "a", "b", "c")):
+            sm[d, slot_response(n_species, w)] = n_species + i
+        for i, s in enumerate(peaks):
+            sm[d, slot_peak(n_species, s, "m")] = n_species + 5 + 2 * i
+            sm[d, slot_peak(n_species, s, "w")] = n_species + 5 + 2 * i + 1
+    return sm
+
+
+def single_gauss(seed: int = 1, n_bins: int = 900, n_fine: int = 2000, e_max: float = 2.0) -> dict:
+    """Plain single-dataset workload: 8 species on a 1 keV grid, Gaussian resolution.
+
+    3 betas (Q ~ U[0.5, 2] MeV), 2 lines (E0 ~ U[0.2, 1.5]), 2 exponentials
+    (tau ~ U[0.1, 1]), 1 flat; LY = 500 p.e./MeV, kB = 0.011 cm/MeV,
+    sigma^2 = a + b mu with a = 4, b = 1 (c = 0); rates log-uniform in [10, 1e5].
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    E = fine_grid(n_fine, e_max)
+    rows, names = [], []
+    for i in range(3):
+        rows.append(shape_beta(E, rng.uniform(0.5, 2.0)))
+        names.append(f"beta{i}")
+    for i in range(2):
+        rows.append(shape_line(E, rng.uniform(0.2, 1.5)))
+        names.append(f"line{i}")
+    for i in range(2):
+        rows.append(shape_expo(E, rng.uniform(0.1, 1.0)))
+        names.append(f"expo{i}")
+    rows.append(shape_flat(E))
+    names.append("flat")
+    S = len(rows)
+    rates = 10.0 ** rng.uniform(1.0, 5.0, size=S)
+    theta0 = np.concatenate([rates, [500.0, 0.011, 4.0, 1.0, 0.0]])
+    return dict(
+        name=f"single_gauss_{n_bins}x{n_fine}",
+        fine_centres=E, spectra=np.array(rows), kind=np.zeros(S, np.int32),
+        shift=np.zeros(S), mask=np.ones((S, 1), np.uint8),
+        edges=[unit_edges(n_bins)], exposure=np.array([1.0]),
+        win_lo=np.array([0], np.int32), win_hi=np.array([n_bins], np.int32),
+        resolution=RES_GAUSS, birks_s0=BIRKS_S0, birks_s1=BIRKS_S1,
+        n_params=S + 5, slot_map=_slot_map_shared(S, 1),
+        pull_param=np.zeros(0, np.int32), pull_centre=np.zeros(0), pull_width=np.zeros(0),
+        theta0=theta0, param_names=[f"r_{n}" for n in names] + ["LY", "kB", "a", "b", "c"],
+    )
+
+
+def borexino_like(seed: int = 2, n_bins: int = 1000, n_fine: int = 20000, e_max: float = 2.0) -> dict:
+    """Two-dataset (tagged / subtracted) workload with generalized-gamma resolution.
+
+    16 species on a 0.1 keV grid: 6 betas, 2 lines, 2 shoulders, 3
+    exponentials, 1 flat, 1 alpha AnaPeak (m ~ 200 p.e., w ~ 10 p.e.), 1
+    positron AnaShift (Q = 0.96 MeV shifted by 1.022 MeV, tagged set only).
+    Exposures 1.0 and 0.6, resolution sigma^2 = a + b mu + c mu^2 with
+    a = 10, b = 1.1, c = 2e-4.  23 parameters: 16 rates, LY, kB, a, b, c, m, w.
+    Pulls on kB (0.011 +- 0.002) and on the peak position (200 +- 2 p.e.).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    E = fine_grid(n_fine, e_max)
+    rows, names, kinds, shifts = [], [], [], []
+
+    def add(row, name, kind=KIND_ANA, shift=0.0):
+        rows.append(row); names.append(name); kinds.append(kind); shifts.append(shift)
+
+    for i in range(6):
+        add(shape_beta(E, rng.uniform(0.5, 2.0)), f"beta{i}")
+    for i in range(2):
+        add(shape_line(E, rng.uniform(0.2, 1.5)), f"line{i}")
+    for i in range(2):
+        add(shape_shoulder(E, rng.uniform(0.3, 1.2)), f"shoulder{i}")
+    for i in range(3):
+        add(shape_expo(E, rng.uniform(0.1, 1.0)), f"expo{i}")
+    add(shape_flat(E), "flat")
+    add(np.zeros_like(E), "alpha", KIND_ANA_PEAK)
+    add(shape_beta(E, 0.96), "positron", KIND_ANA_SHIFT, 1.022)
+    S = len(rows)
+    D = 2
+    mask = np.ones((S, D), np.uint8)
+    mask[S - 1, 1] = 0  # the positron emitter is present only in the tagged set
+    peak_species = (S - 2,)
+    rates = 10.0 ** rng.uniform(1.0, 5.0, size=S)
+    m0, w0 = 200.0 + rng.uniform(-5, 5), 10.0 + rng.uniform(-1, 1)
+    theta0 = np.concatenate([rates, [500.0, 0.011, 10.0, 1.1, 2e-4, m0, w0]])
+    P = S + 7
+    return dict(
+        name=f"borexino_like_2x{n_bins}x{n_fine}",
+        fine_centres=E, spectra=np.array(rows), kind=np.array(kinds, np.int32),
+        shift=np.array(shifts), mask=mask,
+        edges=[unit_edges(n_bins), unit_edges(n_bins)], exposure=np.array([1.0, 0.6]),
+        win_lo=np.zeros(D, np.int32), win_hi=np.full(D, n_bins, np.int32),
+        resolution=RES_GAMMA, birks_s0=BIRKS_S0, birks_s1=BIRKS_S1,
+        n_params=P, slot_map=_slot_map_shared(S, D, peaks=peak_species),
+        pull_param=np.array([S + 1, S + 5], np.int32),
+        pull_centre=np.array([0.011, m0]), pull_width=np.array([0.002, 2.0]),
+        theta0=theta0,
+        param_names=[f"r_{n}" for n in names] + ["LY", "kB", "a", "b", "c", "m_alpha", "w_alpha"],
+    )
+
+
+def perturbed_points(theta0: np.ndarray, n: int, seed0: int, rel: float = 0.01) -> np.ndarray:
+    """Parameter points theta0 * (1 + rel * N(0,1)), point i drawn with seed seed0 + i.
+
+    Parameters whose generating value is 0 are perturbed additively by rel * 1e-4.
+    """
+    out = np.empty((n, theta0.size))
+    for i in range(n):
+        rng = np.random.Generator(np.random.PCG64(seed0 + i))
+        z = rng.standard_normal(theta0.size)
+        out[i] = np.where(theta0 != 0.0, theta0 * (1.0 + rel * z), rel * 1e-4 * np.abs(z))
+    return out
+
+
+def poisson_counts(mu: np.ndarray, seed: int) -> np.ndarray:
+    """Poisson draws (as float64) from a caller-supplied mean."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.poisson(np.clip(mu, 0.0, None)).astype(np.float64)
+
+
+def toy_windows(n_toys: int, n_bins: int, w_min: int, w_max: int, seed: int) -> np.ndarray:
+    """Per-toy fit windows [lo, hi): width ~ U{w_min..w_max}, start ~ U{0..n_bins-width}."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W = rng.integers(w_min, w_max + 1, size=n_toys)
+    lo = np.array([rng.integers(0, n_bins - w + 1) for w in W])
+    return np.stack([lo, lo + W], axis=1).astype(np.int32)
+
+
+def toy_batch(work: dict, mu0: list, n_toys: int, seed0: int = 1000,
+              w_min: int = 600, w_max: int = 1200, rel: float = 0.01) -> dict:
+    """Batched pseudo-experiments of a workload.
+
+    Toy t: counts ~ Poisson(mu0) drawn with seed seed0 + t (all datasets
+    concatenated), its own parameter vector theta0 * (1 + rel N(0,1)) (seed
+    seed0 + n_toys + t) and one fit window shared by its datasets, width
+    U{w_min..w_max} bins.  ``mu0`` holds the expected counts of each dataset at
+    theta0, supplied by the caller.
+    """
+    D = len(work["edges"])
+    nb = [len(e) - 1 for e in work["edges"]]
+    total = int(sum(nb))
+    mu_cat = np.concatenate([np.asarray(m, np.float64) for m in mu0])
+    assert mu_cat.size == total
+    counts = np.empty((n_toys, total))
+    for t in range(n_toys):
+        counts[t] = poisson_counts(mu_cat, seed0 + t)
+    params = perturbed_points(work["theta0"], n_toys, seed0 + n_toys, rel)
+    win = toy_windows(n_toys, min(nb), min(w_min, min(nb)), min(w_max, min(nb)), seed0 + 2 * n_toys)
+    windows = np.repeat(win[:, None, :], D, axis=1)  # (T, D, 2)
+    return dict(counts=counts, params=params, windows=windows)

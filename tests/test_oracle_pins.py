@@ -1,0 +1,325 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each pin checks the oracle against a closed form, an independent
+arbitrary-precision evaluation (mpmath quadrature / special functions), an
+invariant of the mathematics, or brute force on a tiny input.  The mutation
+tests at the end plant plausible mistakes in the oracle and check that at least
+one pin catches each of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize
+
+from oracle import gsn_oracle as O
+from paper_1812_05686_gb300 import inputs as I
+
+mpmath = pytest.importorskip("mpmath")
+mpmath.mp.dps = 40
+
+S0, S1 = I.BIRKS_S0, I.BIRKS_S1
+
+
+# --------------------------------------------------------------- helpers ----
+def tiny_workload(resolution, n_fine=64, n_bins=20, LY=16.0, a=1.0, b=0.5, c=0.01, seed=5):
+    """A tiny single-dataset workload (K = 64 fine points, J = 20 bins) for brute force."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    E = I.fine_grid(n_fine, 1.0)
+    rows = [I.shape_beta(E, 0.8), I.shape_line(E, 0.37), I.shape_expo(E, 0.3), I.shape_flat(E)]
+    S = len(rows)
+    theta0 = np.concatenate([10.0 ** rng.uniform(1, 3, S), [LY, 0.011, a, b, c]])
+    return dict(
+        fine_centres=E, spectra=np.array(rows), kind=np.zeros(S, np.int32), shift=np.zeros(S),
+        mask=np.ones((S, 1), np.uint8), edges=[I.unit_edges(n_bins)], exposure=np.array([0.7]),
+        win_lo=np.array([0]), win_hi=np.array([n_bins]), resolution=resolution,
+        birks_s0=S0, birks_s1=S1, n_params=S + 5, slot_map=I._slot_map_shared(S, 1),
+        pull_param=np.zeros(0, np.int32), pull_centre=np.zeros(0), pull_width=np.zeros(0),
+        theta0=theta0,
+    )
+
+
+def mp_quenched(E, kB):
+    """Birks integral by arbitrary-precision quadrature of its defining integrand."""
+    E = mpmath.mpf(E)
+    return mpmath.quad(lambda t: 1 / (1 + kB * (S0 + S1 / t)), [0, E])
+
+
+def brute_force_mu(work, params):
+    """mu_j by explicit loops in 40-digit arithmetic, independent of the oracle's code."""
+    S = work["spectra"].shape[0]
+    rates = params[:S]
+    LY, kB, a, b, c = params[S:S + 5]
+    E = work["fine_centres"]
+    f = work["spectra"]
+    eps = mpmath.mpf(float(work["exposure"][0]))
+    edges = work["edges"][0]
+    J = edges.size - 1
+    mu = [mpmath.mpf(0)] * J
+    norms = [mpmath.fsum(mpmath.mpf(float(v)) for v in f[s]) for s in range(S)]
+    for k in range(E.size):
+        m = LY * mp_quenched(E[k], kB)
+        var = a + b * m + c * m * m
+        for j in range(J):
+            lo, hi = mpmath.mpf(float(edges[j])), mpmath.mpf(float(edges[j + 1]))
+            if work["resolution"] == I.RES_GAUSS:
+                sd = mpmath.sqrt(var)
+                R = mpmath.ncdf((hi - m) / sd) - mpmath.ncdf((lo - m) / sd)
+            else:
+                d, s = m * m / var, var / m
+                R = mpmath.gammainc(d, lo / s, hi / s, regularized=True)
+            for sp in range(S):
+                if f[sp][k] != 0:
+                    mu[j] += eps * rates[sp] * mpmath.mpf(float(f[sp][k])) / norms[sp] * R
+    return np.array([float(v) for v in mu])
+
+
+def pin_quench_quadrature():
+    worst = 0.0
+    for kB in (0.005, 0.011, 0.03):
+        for E in (1e-4, 0.01, 0.3, 1.0, 1.99):
+            ref = integrate.quad(lambda t: 1.0 / (1.0 + kB * (S0 + S1 / t)), 0.0, E,
+                                 epsabs=0, epsrel=1e-13, limit=200)[0]
+            worst = max(worst, abs(O.quenched_energy(E, kB, S0, S1) / ref - 1.0))
+    return worst
+
+
+def pin_gauss_delta():
+    """A one-point spectrum reproduces the Gaussian bin integrals (libm erfc)."""
+    w = tiny_workload(I.RES_GAUSS)
+    w["spectra"] = np.array([I.shape_line(w["fine_centres"], 0.37)])
+    w["kind"] = np.zeros(1, np.int32); w["shift"] = np.zeros(1); w["mask"] = np.ones((1, 1), np.uint8)
+    w["slot_map"] = I._slot_map_shared(1, 1); w["n_params"] = 6
+    p = np.array([1234.5, 16.0, 0.011, 1.0, 0.5, 0.01])
+    mu = O.expected_counts(w, p, 0)
+    k = int(np.argmin(np.abs(w["fine_centres"] - 0.37)))
+    m = 16.0 * float(mp_quenched(w["fine_centres"][k], 0.011))
+    sd = math.sqrt(1.0 + 0.5 * m + 0.01 * m * m)
+    ref = np.array([0.7 * 1234.5 * 0.5 * (math.erfc(-(j + 1 - m) / (sd * math.sqrt(2)))
+                                          - math.erfc(-(j - m) / (sd * math.sqrt(2)))) for j in range(20)])
+    big = ref > 1e-3 * ref.max()
+    return float(np.max(np.abs(mu[big] / ref[big] - 1.0)))
+
+
+def pin_brute_force(resolution):
+    w = tiny_workload(resolution)
+    p = w["theta0"]
+    ref = brute_force_mu(w, p)
+    mu = O.expected_counts(w, p, 0)
+    big = ref > 1e-12 * ref.max()
+    return float(np.max(np.abs(mu[big] / ref[big] - 1.0)))
+
+
+def pin_rate_identity(work, params, counts):
+    """mu is homogeneous of degree 1 in the rates: sum_s r_s dNLL/dr_s = sum_j (mu_j - n_j)."""
+    g = O.nll_grad(work, params, counts)
+    S = work["spectra"].shape[0]
+    lhs = float(np.dot(params[:S], g[:S]))
+    rhs = 0.0
+    cs = O._split_counts(work, counts)
+    for d in range(len(work["edges"])):
+        lo, hi = int(work["win_lo"][d]), int(work["win_hi"][d])
+        rhs += float(np.sum(O.expected_counts(work, params, d)[lo:hi] - cs[d][lo:hi]))
+    return abs(lhs - rhs) / max(1.0, abs(rhs))
+
+
+# ------------------------------------------------------------- quenching ----
+def test_quench_matches_defining_integral():
+    assert pin_quench_quadrature() < 1e-12
+
+
+def test_quench_kB_zero_is_identity():
+    E = np.linspace(0.0, 2.0, 11)
+    assert np.array_equal(O.quenched_energy(E, 0.0, S0, S1), E)
+
+
+def test_quench_slope_is_birks_integrand():
+    # dE_q/dE = 1 / (1 + kB S(E)) by arbitrary-precision differentiation of the closed form
+    for E in (0.05, 0.5, 1.5):
+        slope = mpmath.diff(lambda t: t / (1 + 0.011 * S0) - (0.011 * S1 / (1 + 0.011 * S0) ** 2)
+                            * mpmath.log(1 + (1 + 0.011 * S0) * t / (0.011 * S1)), E)
+        assert abs(float(slope) * (1 + 0.011 * (S0 + S1 / E)) - 1.0) < 1e-14
+
+
+def test_quench_dkB_against_mpmath():
+    for E in (0.001, 0.2, 1.7):
+        for kB in (0.008, 0.011):
+            ref = mpmath.diff(lambda k: mp_quenched(E, k), kB)
+            assert abs(O.quenched_energy_dkB(E, kB, S0, S1) / float(ref) - 1.0) < 1e-10
+
+
+# -------------------------------------------------------------- responses ---
+def test_gauss_delta_spectrum_reproduces_bin_integrals():
+    assert pin_gauss_delta() < 1e-12
+
+
+def test_gauss_rows_sum_to_one_over_wide_window():
+    mu = np.array([50.0, 300.0, 777.7]); sd = np.array([3.0, 17.0, 29.0])
+    edges = np.arange(-400.0, 1300.0)
+    R = O.response_gauss(edges, mu, sd)
+    assert np.max(np.abs(R.sum(axis=0) - 1.0)) < 1e-14
+
+
+def test_gamma_rows_sum_to_one_from_zero():
+    mu = np.array([0.02, 2.0, 50.0, 500.0]); var = 10.0 + 1.1 * mu + 2e-4 * mu * mu
+    # the smallest mean has a long exponential tail (scale var/mu ~ 500 p.e.): go far out
+    edges = np.concatenate([np.arange(0.0, 3000.0), np.arange(3000.0, 40001.0, 100.0)])
+    R = O.response_gamma(edges, mu, var)
+    assert np.max(np.abs(R.sum(axis=0) - 1.0)) < 1e-13
+
+
+@pytest.mark.parametrize("m,var,lo,hi", [
+    (0.03, 10.0, 0.0, 1.0), (0.03, 10.0, 1.0, 2.0), (3.0, 13.3, 0.0, 1.0), (3.0, 13.3, 5.0, 6.0),
+    (50.0, 65.5, 49.0, 50.0), (50.0, 65.5, 80.0, 81.0), (480.0, 584.0, 470.0, 471.0),
+    (480.0, 584.0, 560.0, 561.0), (900.0, 1162.0, 901.0, 902.0)])
+def test_gamma_bin_integral_against_mpmath(m, var, lo, hi):
+    d, s = m * m / var, var / m
+    if lo > 0:  # regular integrand: arbitrary-precision quadrature of the density
+        ref = mpmath.quad(lambda x: x ** (d - 1) * mpmath.exp(-x / s) / (s ** d * mpmath.gamma(d)),
+                          [lo, (lo + hi) / 2, hi])
+    else:  # x^(d-1) singular at 0: mpmath's own incomplete gamma function
+        ref = mpmath.gammainc(d, 0, hi / s, regularized=True)
+    got = O.response_gamma(np.array([lo, hi]), np.array([m]), np.array([var]))[0, 0]
+    assert abs(got / float(ref) - 1.0) < 1e-11
+
+
+@pytest.mark.parametrize("d,y", [(0.05, 0.01), (0.5, 0.7), (3.0, 2.0), (38.0, 40.0), (410.0, 400.0), (410.0, 460.0)])
+def test_gamma_shape_derivative_against_mpmath(d, y):
+    ref = mpmath.diff(lambda t: mpmath.gammainc(t, 0, y, regularized=True), d)
+    got = float(O._gamma_P_dshape(np.array([d]), np.array([y]))[0])
+    assert abs(got - float(ref)) <= 1e-9 * max(abs(float(ref)), 1e-6)
+
+
+def test_peak_profile_against_libm():
+    edges = np.arange(150.0, 260.0)
+    prof = O.peak_profile(edges, 201.3, 9.7)
+    ref = [0.5 * (math.erfc(-(e1 - 201.3) / (9.7 * math.sqrt(2))) - math.erfc(-(e0 - 201.3) / (9.7 * math.sqrt(2))))
+           for e0, e1 in zip(edges[:-1], edges[1:])]
+    assert np.max(np.abs(prof - ref)) < 1e-15
+
+
+def test_shift_moves_normalised_spectrum():
+    E = I.fine_grid(2000, 2.0)
+    w = dict(fine_centres=E, spectra=np.array([I.shape_beta(E, 0.96)] * 2), kind=np.array([0, 1]),
+             shift=np.array([0.0, 1.022]))
+    S = O.species_spectra(w)
+    assert np.allclose(S[0].sum(), 1.0) and np.allclose(S[1].sum(), 1.0)
+    assert np.array_equal(S[1][1022:], S[0][:-1022]) and not S[1][:1022].any()
+
+
+# ---------------------------------------------------------- brute force -----
+def test_brute_force_tiny_gauss():
+    assert pin_brute_force(I.RES_GAUSS) < 1e-12
+
+
+def test_brute_force_tiny_gamma():
+    assert pin_brute_force(I.RES_GAMMA) < 1e-11
+
+
+# ------------------------------------------------------------ likelihood ----
+def test_single_bin_by_hand():
+    assert O.poisson_term(3.0, 5.0) == pytest.approx(3.0 - 5.0 + 5.0 * math.log(5.0 / 3.0), rel=1e-15)
+    assert O.poisson_term(2.5, 0.0) == 2.5
+    assert O.poisson_term(0.0, 1.0) == math.inf
+
+
+@pytest.mark.parametrize("maker", [lambda: I.single_gauss(n_bins=300, n_fine=600),
+                                   lambda: I.borexino_like(n_bins=300, n_fine=3000)])
+def test_asimov_nll_zero_and_gradient_zero(maker):
+    w = maker()
+    mu = np.concatenate([O.expected_counts(w, w["theta0"], d) for d in range(len(w["edges"]))])
+    assert O.nll(w, w["theta0"], mu) == pytest.approx(0.0, abs=1e-9)
+    g = O.nll_grad(w, w["theta0"], mu)
+    assert np.max(np.abs(g)) < 1e-8
+    # and it is a strict minimum: random small moves raise the NLL
+    rng = np.random.Generator(np.random.PCG64(9))
+    for _ in range(3):
+        p = w["theta0"] * (1 + 1e-3 * rng.standard_normal(w["theta0"].size))
+        assert O.nll(w, p, mu) > 0.0
+
+
+def test_rate_homogeneity_identity():
+    w = I.borexino_like(n_bins=250, n_fine=2500)
+    w["pull_param"] = np.zeros(0, np.int32); w["pull_centre"] = np.zeros(0); w["pull_width"] = np.zeros(0)
+    mu = np.concatenate([O.expected_counts(w, w["theta0"], d) for d in range(2)])
+    n = I.poisson_counts(mu, 11)
+    p = I.perturbed_points(w["theta0"], 1, 12)[0]
+    assert pin_rate_identity(w, p, n) < 1e-11
+
+
+@pytest.mark.parametrize("resolution", [I.RES_GAUSS, I.RES_GAMMA])
+def test_analytic_gradient_matches_finite_differences(resolution):
+    w = I.borexino_like(n_bins=220, n_fine=1500) if resolution == I.RES_GAMMA else I.single_gauss(n_bins=250, n_fine=500)
+    mu = np.concatenate([O.expected_counts(w, w["theta0"], d) for d in range(len(w["edges"]))])
+    n = I.poisson_counts(mu, 21)
+    p = I.perturbed_points(w["theta0"], 1, 22, rel=0.02)[0]
+    g = O.nll_grad(w, p, n)
+    gf = O.nll_grad_fd(w, p, n, rel=1e-4)
+    scale = np.abs(g) + 1e-3 * np.max(np.abs(g))
+    assert np.max(np.abs(g - gf) / scale) < 2e-6
+
+
+def test_synchronised_parameter_gradient_is_sum_over_datasets():
+    """Section 2.2: a parameter shared by two datasets gets the sum of their gradients."""
+    w = I.borexino_like(n_bins=200, n_fine=1500)
+    mu = np.concatenate([O.expected_counts(w, w["theta0"], d) for d in range(2)])
+    n = I.poisson_counts(mu, 31)
+    p = I.perturbed_points(w["theta0"], 1, 32)[0]
+    g_shared = O.nll_grad(w, p, n)
+    # unsynchronise LY: dataset 1 gets its own copy as a new parameter P
+    w2 = dict(w)
+    P = w["n_params"]
+    sm = w["slot_map"].copy()
+    S = w["spectra"].shape[0]
+    sm[1, I.slot_response(S, "LY")] = P
+    w2["slot_map"] = sm; w2["n_params"] = P + 1
+    p2 = np.concatenate([p, [p[S]]])
+    g2 = O.nll_grad(w2, p2, n)
+    assert g2[S] + g2[P] == pytest.approx(g_shared[S], rel=1e-12)
+    assert O.nll(w2, p2, n) == pytest.approx(O.nll(w, p, n), rel=1e-15)
+
+
+def test_asimov_fit_recovers_generating_parameters():
+    """The NLL of Asimov data is minimised at the generating parameters."""
+    w = I.single_gauss(n_bins=1000, n_fine=1000)
+    th = w["theta0"].copy()
+    mu = O.expected_counts(w, th, 0)
+    free = list(range(8)) + [8, 10, 11]  # rates, LY, a, b
+
+    def f(x):
+        p = th.copy(); p[free] = th[free] * x
+        return O.nll(w, p, mu), O.nll_grad(w, p, mu)[free] * th[free]
+    x0 = 1.0 + 0.03 * np.sin(np.arange(len(free)) + 1.0)
+    res = optimize.minimize(f, x0, jac=True, method="BFGS", options=dict(gtol=1e-11, maxiter=2000))
+    assert res.fun < 1e-10
+    assert np.max(np.abs(res.x - 1.0)) < 1e-5
+
+
+# -------------------------------------------------- planted mistakes --------
+MUTANTS = {
+    "quench drops log term": ("quenched_energy", lambda E, kB, s0, s1: np.asarray(E) / (1 + kB * s0)),
+    "gauss cdf sign flip": ("_norm_cdf_diff", lambda lo, hi: (O.special.ndtr(lo) - O.special.ndtr(hi))),
+    "gamma scale inverted": ("gamma_shape_scale", lambda mu, var: (mu * mu / var, mu / var)),
+    "rate term drops exposure": ("peak_profile", lambda e, m, w: O._norm_cdf_diff((e[:-1] - m) / w, (e[1:] - w) / m)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(monkeypatch, name):
+    attr, fn = MUTANTS[name]
+    monkeypatch.setattr(O, attr, fn)
+    caught = []
+    try:
+        caught.append(pin_quench_quadrature() > 1e-12)
+    except Exception:
+        caught.append(True)
+    for pin in (pin_gauss_delta, lambda: pin_brute_force(I.RES_GAMMA)):
+        try:
+            caught.append(pin() > 1e-11)
+        except Exception:
+            caught.append(True)
+    try:
+        caught.append(abs(float(O.peak_profile(np.arange(150.0, 260.0), 201.3, 9.7).sum()) - 1.0) > 1e-6)
+    except Exception:
+        caught.append(True)
+    assert any(caught), f"no pin caught the planted mistake '{name}'"
