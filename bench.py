@@ -1,0 +1,326 @@
+"""Benchmark: batched NLL + gradient evaluations per second on one GB300.
+
+Workload (the batched pseudo-experiment configuration): T toys of the
+two-dataset generalized-gamma workload -- 16 species on a 20000-point fine
+grid (0.1 keV, 0-2 MeV), 2 datasets (exposures 1.0 / 0.6) on a 1200-bin
+domain of 1 p.e. bins, 23 parameters, two pulls.  Toy t has Poisson counts
+drawn from the stored expected counts at theta0 (seed 1000 + t), its own
+parameter vector theta0 (1 + 0.01 N(0,1)) and a fit window of 600..1200 bins.
+One step = one NLL + gradient evaluation of every toy (column prologue,
+response build + contraction, FP64 deviance and reduction, adjoint, gradient
+reduction) in the mixed-precision path; inputs resident in HBM.
+
+Under torchrun each rank evaluates its own T toys (weak scaling, no collective
+on the data path; only the timing uses a barrier and a max over ranks).
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NLL+grad evals/sec (batched toys) on 1 GB300, mixed vs FP64 path at |dNLL|<1e-3"
+UNIT = "evals/s"
+WORKLOAD = "borexino_like toys: 2 datasets x 1200-bin domain, 16 species x 20000 fine points, gamma response, 23 params"
+
+# Algorithmic FP32 floating-point operations per evaluated (bin, column) pair of
+# the mixed generalized-gamma kernels (FMA = 2, SFU exponential = 1), counted from
+# the arithmetic each pair needs: window offset and t (3), ln(1+t)-t (21),
+# ln(1+t) (1), centre exponent (3), 3 Gauss-Legendre nodes (forward 7 each,
+# adjoint 11 each), contraction with 2 datasets (forward 4; adjoint 4 + 12).
+FLOP_PER_PAIR = {"forward": 53, "backward": 78}
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--toys", type=int, default=8192)
+    ap.add_argument("--fp64-toys", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ inputs -------
+def make_inputs(n_toys, seed0):
+    import numpy as np
+
+    from paper_1812_05686_gb300 import inputs as I
+    w = I.borexino_like(n_bins=1200)
+    mu0 = np.loadtxt(os.path.join(ROOT, "tests", "golden", "borexino_like_1200_mu0.txt"))
+    b = I.toy_batch(w, [mu0[:1200], mu0[1200:]], n_toys=n_toys, seed0=seed0)
+    return w, b
+
+
+# ------------------------------------------------------------ clocks -------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------ traffic ------
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_mixed_gamma.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"csrc_sha256:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
+    if not (m and t):
+        return None
+    return float(t.group(1)) if m.group(1) == csrc_sha() else None
+
+
+def csrc_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1812_05686_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------- oracle ------
+ORACLE_FINE = 2500     # fine columns of the oracle sample (the workload has 20000)
+ORACLE_SCALE = 20000 / ORACLE_FINE
+ORACLE_SAMPLE = ("1 toy (toy 0 of the batch: 2 datasets x 1200 bins, its own window), NLL + full gradient, "
+                 "FP64 oracle, one thread, on a 2500-point fine grid; time scaled x8 to 20000 points "
+                 "(the oracle's cost is linear in the fine columns)")
+
+
+def oracle_step_seconds(n_steps):
+    """Time the oracle in a child process (single-threaded BLAS), one toy per step."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import gsn_oracle as O
+from paper_1812_05686_gb300 import inputs as I
+w = I.borexino_like(n_bins=1200, n_fine=%d)
+mu0 = np.loadtxt(os.path.join(%r, "tests", "golden", "borexino_like_1200_mu0.txt"))
+b = I.toy_batch(w, [mu0[:1200], mu0[1200:]], n_toys=1, seed0=1000)
+ts = []
+for i in range(%d):
+    t = time.time()
+    O.nll(w, b["params"][0], b["counts"][0], b["windows"][0])
+    O.nll_grad(w, b["params"][0], b["counts"][0], b["windows"][0])
+    ts.append(time.time() - t)
+print(json.dumps(ts))
+""" % (ROOT, ORACLE_FINE, ROOT, n_steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return [t * ORACLE_SCALE for t in json.loads(r.stdout.strip().splitlines()[-1])]
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ts = oracle_step_seconds(args.warmup + args.steps)[args.warmup:]
+    sec = sum(ts) / len(ts)
+    value = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "toys_per_step": 1, "sample": ORACLE_SAMPLE},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- ours ------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1812_05686_gb300 import gsn
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    T = args.toys
+    w, b = make_inputs(T, 1000 + rank * T)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gsn.context_from_workload(w, gsn.GSN_MIXED, device=local_rank, stream=stream.cuda_stream)
+    P, B, D = w["n_params"], b["counts"].shape[1], 2
+    params = torch.from_numpy(b["params"]).to(dev)
+    counts = torch.from_numpy(b["counts"]).to(dev)
+    wins = torch.from_numpy(b["windows"].astype(np.int32)).to(dev)
+    nll = torch.empty(T, dtype=torch.float64, device=dev)
+    grad = torch.empty(T, P, dtype=torch.float64, device=dev)
+    status = torch.empty(T, dtype=torch.int32, device=dev)
+
+    def step():
+        rc = ctx.eval_grad_batch_dev(params, counts, wins, nll, grad, status)
+        if rc != 0:
+            raise RuntimeError(ctx.last_error())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ctx.profile(True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = status.cpu().numpy()
+    nll_mixed = nll.cpu().numpy()
+    value = world * T / (ms * 1e-3)
+
+    # FP64 path on the first toys: throughput and |dNLL| against the mixed path
+    nf = min(args.fp64_toys, T)
+    ctx64 = gsn.context_from_workload(w, gsn.GSN_FP64, device=local_rank, stream=stream.cuda_stream)
+    nll64 = torch.empty(nf, dtype=torch.float64, device=dev)
+    grad64 = torch.empty(nf, P, dtype=torch.float64, device=dev)
+    ctx64.eval_grad_batch_dev(params[:nf], counts[:nf], wins[:nf], nll64, grad64, None)
+    torch.cuda.synchronize(dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    ctx64.eval_grad_batch_dev(params[:nf], counts[:nf], wins[:nf], nll64, grad64, None)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    fp64_value = nf / (f0.elapsed_time(f1) * 1e-3)
+    dnll = float(np.max(np.abs(nll64.cpu().numpy() - nll_mixed[:nf])))
+    g64 = grad64.cpu().numpy()
+    gm = grad[:nf].cpu().numpy()
+    gerr = float(np.max(np.max(np.abs(gm - g64), axis=1) / np.maximum(np.max(np.abs(g64), axis=1), 1.0)))
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hp, hc, hw = b["params"], b["counts"], b["windows"].astype(np.int32)
+        ctx.eval_grad_batch(hp, hc, hw)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(max(1, min(args.steps, 3))):
+            rc, _, _ = ctx.eval_grad_batch(hp, hc, hw)
+        dt = (time.perf_counter() - t0) / max(1, min(args.steps, 3))
+        h2d = T * (P * 8 + B * 8 + D * 2 * 4)
+        d2h = T * (8 + P * 8 + 4)
+        e2e = {"value": world * T / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel (event time per launch, algorithmic FLOPs per launch)
+    dom = max(("forward", "backward"), key=lambda k: prof[k][0])
+    kms, kn, kunits = prof[dom]
+    per_launch_s = kms * 1e-3 / max(kn, 1)
+    flops = kunits / max(kn, 1) * FLOP_PER_PAIR[dom]
+    sm_mhz = clk.get("sm_mhz") or 1455.0
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = nsm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
+    achieved = flops / per_launch_s
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(dom), "kernel": dom,
+            "peak_basis": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock {sm_mhz:.0f} MHz",
+            "pairs_per_launch": kunits / max(kn, 1), "ms_per_launch": per_launch_s * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        ts = oracle_step_seconds(1)
+        cpu = {"value": 1.0 / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE}
+
+    launches = sum(v[1] for v in prof.values())
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 (f64 deviance and reductions)", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "toys_per_gpu": T, "fine_points": 20000, "bins": 1200,
+                           "species": 16, "precision": "mixed",
+                           "l2": "inputs and scratch per step (GBs) exceed the 129 MB L2"},
+                "fp64_path": {"value": fp64_value, "unit": UNIT, "toys": nf, "speedup_mixed_over_fp64": value / world / fp64_value,
+                              "max_abs_dnll_mixed_vs_fp64": dnll, "grad_normwise_err_mixed_vs_fp64": gerr},
+                "status_nonzero_toys": int(np.count_nonzero(st)),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "kernels": {k: {"ms_total": v[0], "launches": v[1], "pairs": v[2]} for k, v in prof.items() if v[1]}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * gsn.h -- C ABI of the GB300 binned spectral-fit likelihood engine.
+ *
+ * The library evaluates, at each minimiser step, the binned Poisson negative
+ * log-likelihood of a multi-species spectral model and its gradient
+ * (GooStats, arXiv:1812.05686, section 4.1, Eq. (LL)):
+ *
+ *   NLL(theta) = sum_d sum_{j in window_d} [ mu_dj - n_dj + n_dj ln(n_dj / mu_dj) ]
+ *                + 1/2 sum_p ((theta_p - c_p) / sigma_p)^2
+ *
+ *   mu_dj = eps_d [ sum_{s smeared} r_s sum_k R_jk(theta) S'_sk
+ *                   + sum_{s peak} r_s int_{bin j} N(x; m_s, w_s) dx ]
+ *
+ * with R_jk the bin integral of the analytic detector response of fine
+ * true-energy column k (section 2.3): visible mean mu_k = LY * E_q(E_k; kB)
+ * (Birks quenching with stopping power S(E) = s0 + s1/E), variance
+ * sigma_k^2 = a + b mu_k + c mu_k^2, and either a Gaussian or the
+ * moment-matched gamma ("generalized gamma") resolution.  n = 0 bins
+ * contribute mu.  The data-only constant of -ln L is dropped, so NLL = 0 for
+ * data equal to the model and an increase of 0.5 is one standard deviation.
+ *
+ * Conventions
+ *  - All calls return 0 (GSN_OK) or a negative GSN_ERR_* code; the message
+ *    of the last failure is available from gsn_last_error().
+ *  - Pointers are host pointers unless the name ends in _dev (device
+ *    pointers, valid on the context's device).
+ *  - The library copies every input of gsn_set_* to device memory; the caller
+ *    keeps ownership of its buffers.  Outputs are caller-allocated.
+ *  - A context is bound to one device and one CUDA stream and is not
+ *    thread-safe; use one context per host thread.
+ *  - Arrays indexed [a][b] are dense row-major.
+ */
+#ifndef GSN_H
+#define GSN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes -- */
+#define GSN_OK                    0
+#define GSN_ERR_ARG              -1  /* invalid argument or inconsistent sizes */
+#define GSN_ERR_CUDA             -2  /* a CUDA runtime call failed */
+#define GSN_ERR_NONPOSITIVE_MU   -3  /* mu <= 0 in a bin with n > 0: NLL set to +inf */
+#define GSN_ERR_NONFINITE        -4  /* a parameter, mu or the NLL is not finite */
+#define GSN_ERR_STATE            -5  /* set_data / set_species / set_params missing */
+#define GSN_ERR_NOMEM            -6  /* device allocation failed */
+
+/* precision of the response build and contraction (the deviance and the
+ * NLL reduction are FP64 in both modes) */
+#define GSN_FP64                  0
+#define GSN_MIXED                 1  /* FP32 response + contraction, FP64 deviance */
+
+/* resolution shape (section 2.3) */
+#define GSN_RES_GAUSS             0
+#define GSN_RES_GAMMA             1  /* gamma density with mean mu_k, variance sigma_k^2 */
+
+/* species kinds (section 4.3) */
+#define GSN_ANA                   0  /* fine spectrum smeared by the response */
+#define GSN_ANA_SHIFT             1  /* fine spectrum shifted up in true energy, then smeared */
+#define GSN_ANA_PEAK              2  /* Gaussian peak in p.e. with free position m and width w */
+
+/* per-dataset parameter slots: gsn_n_slots(S) = 3 S + 5
+ *   [0, S)              rate r_s of species s (counts per unit exposure)
+ *   S + 0 .. S + 4      LY [p.e./MeV], kB [cm/MeV], a [p.e.^2], b [p.e.], c
+ *   S + 5 + 2 s         peak position m_s [p.e.]   (AnaPeak species only)
+ *   S + 5 + 2 s + 1     peak width w_s [p.e.]      (AnaPeak species only)   */
+#define GSN_SLOT_LY(S)    ((S) + 0)
+#define GSN_SLOT_KB(S)    ((S) + 1)
+#define GSN_SLOT_A(S)     ((S) + 2)
+#define GSN_SLOT_B(S)     ((S) + 3)
+#define GSN_SLOT_C(S)     ((S) + 4)
+#define GSN_SLOT_M(S, s)  ((S) + 5 + 2 * (s))
+#define GSN_SLOT_W(S, s)  ((S) + 6 + 2 * (s))
+
+#define GSN_MAX_DATASETS  8
+#define GSN_MAX_SPECIES   64
+
+typedef struct gsn_ctx gsn_ctx;
+
+typedef struct gsn_options {
+    int    precision;      /* GSN_FP64 or GSN_MIXED */
+    int    resolution;     /* GSN_RES_GAUSS or GSN_RES_GAMMA */
+    double band_cut;       /* response band: a column is evaluated only where its
+                              density exceeds exp(-band_cut) times its value at
+                              the mean (<= 0: 34.5 for FP64, 20.7 for mixed) */
+    double birks_s0;       /* stopping power S(E) = s0 + s1/E, MeV/cm (<= 0: 1.55) */
+    double birks_s1;       /* MeV^2/cm (< 0: 0.155) */
+    int    device;         /* CUDA device ordinal */
+    void*  stream;         /* cudaStream_t for all work of the context; NULL = a
+                              stream created and owned by the context */
+    int    max_toys_per_launch; /* batch chunk bounding scratch memory (<= 0: 4096) */
+} gsn_options;
+
+/* Fill *opt with the defaults described above (FP64, Gaussian, device 0). */
+int gsn_default_options(gsn_options* opt);
+
+/* Create a context.  Errors: GSN_ERR_ARG (bad option), GSN_ERR_CUDA. */
+int gsn_create(gsn_ctx** out, const gsn_options* opt);
+
+/* Release the context and every device buffer it owns (NULL is a no-op). */
+void gsn_destroy(gsn_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none; static string if ctx is NULL). */
+const char* gsn_last_error(const gsn_ctx* ctx);
+
+/* Number of per-dataset slots for n_species species (3 n_species + 5). */
+int gsn_n_slots(int n_species);
+
+/* Observed histograms (section 4.1 inputs: histogram, exposure).
+ *   n_datasets    1 .. GSN_MAX_DATASETS
+ *   n_bins[d]     >= 1
+ *   bin_edges[d]  n_bins[d] + 1 strictly ascending edges in p.e., >= 0 for the
+ *                 gamma resolution
+ *   counts[d]     n_bins[d] observed counts (>= 0; integer values expected)
+ *   exposures[d]  > 0
+ *   win_lo/hi[d]  default fit window [lo, hi), 0 <= lo <= hi <= n_bins[d]
+ * Datasets with identical edges and identical response slots share one
+ * response evaluation. */
+int gsn_set_data(gsn_ctx* ctx, int n_datasets, const int* n_bins, const double* const* bin_edges,
+                 const double* const* counts, const double* exposures,
+                 const int* win_lo, const int* win_hi);
+
+/* Species (section 4.3).
+ *   fine_centres   n_fine ascending true energies [MeV] (> 0); uniformly spaced
+ *                  when an AnaShift species is present
+ *   spectra        [n_species][n_fine] non-negative unnormalised shapes; the
+ *                  library normalises each row to unit sum (rows of AnaPeak
+ *                  species are ignored)
+ *   kind           [n_species] GSN_ANA, GSN_ANA_SHIFT or GSN_ANA_PEAK
+ *   shift          [n_species] AnaShift offset [MeV], rounded to whole fine
+ *                  bins (NULL = no shifts)
+ *   dataset_mask   [n_species][n_datasets] 1 where the species contributes
+ * Requires gsn_set_data first (for n_datasets). */
+int gsn_set_species(gsn_ctx* ctx, int n_species, int n_fine, const double* fine_centres,
+                    const double* spectra, const int* kind, const double* shift,
+                    const unsigned char* dataset_mask);
+
+/* Parameter map (section 2.2 parameter synchronisation) and pull terms (Eq. LL).
+ *   slot_map   [n_datasets][gsn_n_slots(n_species)] global parameter index of
+ *              each slot, or -1 for an unused slot (rates of absent species,
+ *              peak slots of non-peak species).  A parameter referenced by
+ *              several datasets is synchronised; its gradient is the sum.
+ *   pull_*     n_pulls Gaussian constraints 1/2 ((theta_p - c)/sigma)^2
+ * Requires gsn_set_species first. */
+int gsn_set_params(gsn_ctx* ctx, int n_params, const int* slot_map, int n_pulls,
+                   const int* pull_param, const double* pull_centre, const double* pull_width);
+
+/* NLL at params[n_params] with the counts and windows of gsn_set_data.
+ * Errors: GSN_ERR_NONPOSITIVE_MU (nll = +inf), GSN_ERR_NONFINITE. */
+int gsn_eval(gsn_ctx* ctx, const double* params, double* nll);
+
+/* NLL and gradient grad[n_params] (hand-written adjoint). */
+int gsn_eval_grad(gsn_ctx* ctx, const double* params, double* nll, double* grad);
+
+/* Batched pseudo-experiments: each toy has its own parameters, counts and windows.
+ *   params      [n_toys][n_params]
+ *   toy_counts  [n_toys][sum_d n_bins[d]] (datasets concatenated)
+ *   toy_win     [n_toys][n_datasets][2] window [lo, hi) per toy and dataset
+ *   nll         [n_toys]
+ *   grad        [n_toys][n_params], or NULL for the NLL only
+ * Host buffers; the call copies them to the device and back, synchronously.
+ * n_toys = 0 is a no-op.  The first failing toy's status is returned; the
+ * other toys' results are still written. */
+int gsn_eval_grad_batch(gsn_ctx* ctx, int n_toys, const double* params, const double* toy_counts,
+                        const int* toy_win, double* nll, double* grad);
+
+/* Same as gsn_eval_grad_batch with device-resident inputs and outputs,
+ * enqueued on the context's stream.  status_dev (may be NULL) receives one
+ * int per toy (0 or a GSN_ERR_* code).  Asynchronous: the results are ready
+ * once the stream is synchronised; argument errors are reported at once. */
+int gsn_eval_grad_batch_dev(gsn_ctx* ctx, int n_toys, const double* params_dev,
+                            const double* toy_counts_dev, const int* toy_win_dev,
+                            double* nll_dev, double* grad_dev, int* status_dev);
+
+/* Expected counts per bin and species of one dataset (the validation quantity
+ * of section 3.1): mu_per_species[n_bins[d]][n_species]; columns of species
+ * absent from the dataset are zero. */
+int gsn_expected(gsn_ctx* ctx, const double* params, int dataset, double* mu_per_species);
+
+/* Stream of the context (cudaStream_t), e.g. to order caller work after it. */
+void* gsn_stream(gsn_ctx* ctx);
+
+/* ----------------------------------------------------------- tracing ----
+ * Per-kernel statistics.  While enabled, each kernel launch of the context is
+ * bracketed by CUDA events recorded on the context's stream, and the response
+ * kernels count the (bin, fine column) pairs they evaluate.  Not part of the
+ * paper's method: measurement support for the roofline of each kernel. */
+#define GSN_K_COLUMNS    0   /* column prologue: means, resolution, band, T_dk */
+#define GSN_K_FORWARD    1   /* response build + contraction -> mu */
+#define GSN_K_DEVIANCE   2   /* FP64 deviance, NLL reduction, w = 1 - n/mu */
+#define GSN_K_BACKWARD   3   /* adjoint over the band */
+#define GSN_K_GRADFINAL  4   /* partial-gradient reduction and slot-map scatter */
+#define GSN_K_SPECIES    5   /* per-species contraction (gsn_eval, gsn_expected) */
+#define GSN_K_MU         6   /* rate-weighted sum of cached per-species shapes */
+#define GSN_K_COUNT      7
+
+/* enable = 1 resets the statistics and starts recording; 0 stops. */
+int gsn_profile(gsn_ctx* ctx, int enable);
+
+/* Statistics of one kernel (GSN_K_*) since the last reset: summed event time
+ * [ms], number of launches, evaluated (bin, column) pairs (response kernels;
+ * 0 otherwise).  Synchronises the context's stream.  Any output may be NULL. */
+int gsn_profile_read(gsn_ctx* ctx, int kernel, double* total_ms, long long* launches,
+                     unsigned long long* units);
+
+/* Name of a GSN_K_* kernel class ("" when out of range). */
+const char* gsn_kernel_name(int kernel);
+
+/* Throughput probe: a synthetic loop of one instruction class on every SM of
+ * `device`, timed with CUDA events; returns operations per second.
+ *   GSN_PROBE_FFMA  FP32 fused multiply-adds
+ *   GSN_PROBE_EX2   SFU base-2 exponentials
+ *   GSN_PROBE_DFMA  FP64 fused multiply-adds
+ *   GSN_PROBE_NODE  one mixed-precision quadrature node: 2 FFMA + EX2 + FFMA */
+#define GSN_PROBE_FFMA 0
+#define GSN_PROBE_EX2  1
+#define GSN_PROBE_DFMA 2
+#define GSN_PROBE_NODE 3
+int gsn_peak_probe(int device, int which, double* ops_per_second);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSN_H */

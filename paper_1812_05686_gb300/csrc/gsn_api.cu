@@ -1,0 +1,796 @@
+// Host side of the C ABI declared in include/gsn.h.
+#include "../../include/gsn.h"
+#include "gsn_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace gsn;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct gsn_ctx {
+    gsn_options opt{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nsm = 1;
+    std::string err;
+    // problem, host copies
+    int D = 0;
+    std::vector<int> nb;
+    std::vector<std::vector<double>> edges, counts;
+    std::vector<double> eps;
+    std::vector<int> wlo, whi;
+    int S = 0, K = 0;
+    std::vector<double> E, Sn;        // fine centres, normalised shifted spectra [S][K]
+    std::vector<int> kind;
+    std::vector<unsigned char> mask;  // [S][D]
+    int P = 0;
+    std::vector<int> slot_map;
+    std::vector<int> pull_p;
+    std::vector<double> pull_c, pull_w;
+    bool have_data = false, have_species = false, have_params = false, ready = false;
+    // derived
+    int G = 0, total_bins = 0, Jmax = 0;
+    KArgs base{};
+    // persistent device buffers
+    std::vector<Buf> owned;
+    // scratch
+    Buf colbuf, blkbuf, mubuf, wbuf, partbuf, gdirect, params, counts_b, win_b, nll_b, grad_b, status_b, Mbuf, outbuf;
+    // response cache of gsn_eval (section 2.5: values are reused while the response parameters do not change)
+    std::vector<double> cache_key;
+    bool cache_valid = false;
+    // tracing: events around each launch, summed per kernel class
+    bool prof = false;
+    struct Pending { int kernel; cudaEvent_t e0, e1; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double prof_ms[K_COUNT] = {0};
+    long long prof_n[K_COUNT] = {0};
+    Buf work;  // unsigned long long[K_COUNT] on the device
+};
+
+namespace {
+
+int fail(gsn_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CUDA_TRY(ctx, expr)                                                                    \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ctx, GSN_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int ensure(gsn_ctx* c, Buf& b, size_t bytes) {
+    if (b.n >= bytes && b.p) return GSN_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr; b.n = 0;
+    if (bytes == 0) return GSN_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GSN_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    b.n = bytes;
+    return GSN_OK;
+}
+
+template <class T>
+int upload(gsn_ctx* c, const std::vector<T>& v, const T** out) {
+    Buf b;
+    int rc = ensure(c, b, std::max<size_t>(v.size(), 1) * sizeof(T));
+    if (rc) return rc;
+    if (!v.empty()) CUDA_TRY(c, cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    c->owned.push_back(b);
+    *out = static_cast<const T*>(b.p);
+    return GSN_OK;
+}
+
+void free_owned(gsn_ctx* c) {
+    for (auto& b : c->owned) cudaFree(b.p);
+    c->owned.clear();
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n)
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0); w.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5)), pp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                const double p3 = p2; p2 = p1;
+                p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            pp = n * (z * p1 - p2) / (z * z - 1.0);
+            const double dz = p1 / pp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+struct Plan {
+    int nsplit, ntile, bw_warps, bw_bsplit, nbtask;
+};
+
+Plan make_plan(const gsn_ctx* c, int T) {
+    Plan p{};
+    const bool e64g = c->opt.precision == GSN_FP64 && c->opt.resolution == GSN_RES_GAUSS;
+    const int bins_per_tile = 8 * (e64g ? 31 : 32);
+    p.ntile = (c->Jmax + bins_per_tile - 1) / bins_per_tile;
+    const long long target = 4LL * c->nsm;
+    const long long fw = (long long)T * c->G * p.ntile;
+    p.nsplit = (int)std::min<long long>(std::max<long long>(1, (target + fw - 1) / fw), std::max(1, c->K / 256));
+    p.bw_warps = 8;
+    const int ncb = (c->K + p.bw_warps * 32 - 1) / (p.bw_warps * 32);
+    const long long bw = (long long)T * c->G * ncb;
+    p.bw_bsplit = (int)std::min<long long>(std::max<long long>(1, (target + bw - 1) / bw), 16);
+    p.nbtask = ncb * p.bw_bsplit;
+    return p;
+}
+
+int finalize(gsn_ctx* c) {
+    if (c->ready) return GSN_OK;
+    if (!c->have_data || !c->have_species || !c->have_params)
+        return fail(c, GSN_ERR_STATE, "gsn_set_data, gsn_set_species and gsn_set_params must all be called");
+    free_owned(c);
+    c->cache_valid = false;
+    const bool mixed = c->opt.precision == GSN_MIXED;
+    const bool gamma = c->opt.resolution == GSN_RES_GAMMA;
+    const int NSLOT = gsn_n_slots(c->S);
+    KArgs& a = c->base;
+    a = KArgs{};
+    a.D = c->D; a.S = c->S; a.K = c->K; a.P = c->P; a.NSLOT = NSLOT;
+    a.res = gamma ? 1 : 0;
+    a.precision = mixed ? 1 : 0;
+    a.cut = c->opt.band_cut;
+    a.s0 = c->opt.birks_s0; a.s1 = c->opt.birks_s1;
+    a.n_pulls = (int)c->pull_p.size();
+    // species
+    for (int s = 0; s < c->S; ++s) {
+        a.sp_kind[s] = c->kind[s];
+        unsigned m = 0;
+        for (int d = 0; d < c->D; ++d) if (c->mask[s * c->D + d]) m |= 1u << d;
+        a.sp_mask[s] = m;
+    }
+    // response groups: identical edges and identical response slots
+    std::vector<int> gfirst;
+    c->G = 0;
+    int off = 0;
+    for (int d = 0; d < c->D; ++d) {
+        a.ds_bins[d] = c->nb[d]; a.ds_off[d] = off; a.ds_eps[d] = c->eps[d];
+        off += c->nb[d];
+        int gsel = -1;
+        for (int g = 0; g < c->G && gsel < 0; ++g) {
+            const int d0 = a.g_ds[g][0];
+            if (a.g_nds[g] >= MAXGDS || c->edges[d0] != c->edges[d]) continue;
+            bool same = true;
+            for (int i = 0; i < NRESP; ++i)
+                same = same && c->slot_map[d0 * NSLOT + c->S + i] == c->slot_map[d * NSLOT + c->S + i];
+            if (same) gsel = g;
+        }
+        if (gsel < 0) {
+            if (c->G >= MAXG) return fail(c, GSN_ERR_ARG, "too many distinct response groups");
+            gsel = c->G++;
+            a.g_nds[gsel] = 0;
+            for (int i = 0; i < NRESP; ++i) a.g_resp[gsel][i] = c->slot_map[d * NSLOT + c->S + i];
+        }
+        a.ds_group[d] = gsel;
+        a.ds_in_group[d] = a.g_nds[gsel];
+        a.g_ds[gsel][a.g_nds[gsel]++] = d;
+    }
+    c->total_bins = off;
+    a.total_bins = off;
+    a.G = c->G;
+    // edges and node tables per group
+    std::vector<double> edges_all, ntab_d;
+    std::vector<float> ntab_f, xc_f;
+    std::vector<unsigned char> bcls;
+    std::vector<double> gx_lin, gw_lin, gx_log, gw_log;
+    const int ng_lin = mixed ? NG_LIN_F : NG_LIN_D, ng_log = mixed ? NG_LOG_F : NG_LOG_D;
+    const int NGM = mixed ? NGM_F : NGM_D;
+    const double xlog = mixed ? XLOG_F : XLOG_D;
+    gauss_legendre(ng_lin, gx_lin, gw_lin);
+    gauss_legendre(ng_log, gx_log, gw_log);
+    c->Jmax = 0;
+    int noff = 0;
+    for (int g = 0; g < c->G; ++g) {
+        const std::vector<double>& x = c->edges[a.g_ds[g][0]];
+        const int J = (int)x.size() - 1;
+        a.g_bins[g] = J;
+        a.g_edge_off[g] = (int)edges_all.size();
+        a.g_node_off[g] = noff;
+        a.g_zero[g] = (gamma && x[0] == 0.0) ? 1 : 0;
+        c->Jmax = std::max(c->Jmax, J);
+        edges_all.insert(edges_all.end(), x.begin(), x.end());
+        for (int j = 0; j < J; ++j) {
+            const double lo = x[j], hi = x[j + 1], xc = 0.5 * (lo + hi);
+            double nx[NGM_D] = {0}, nw[NGM_D] = {0};
+            unsigned char cls = BIN_LIN;
+            int ng = ng_lin;
+            if (gamma && lo == 0.0) {
+                cls = BIN_ZERO; ng = 0;
+            } else if (gamma && lo < xlog) {
+                cls = BIN_LOG; ng = ng_log;
+                const double ul = std::log(lo), uh = std::log(hi);
+                for (int n = 0; n < ng; ++n) {
+                    nx[n] = std::exp(0.5 * (ul + uh) + 0.5 * (uh - ul) * gx_log[n]);
+                    nw[n] = 0.5 * (uh - ul) * gw_log[n] * nx[n];
+                }
+            } else {
+                for (int n = 0; n < ng; ++n) {
+                    nx[n] = xc + 0.5 * (hi - lo) * gx_lin[n];
+                    nw[n] = 0.5 * (hi - lo) * gw_lin[n];
+                }
+            }
+            bcls.push_back(cls);
+            if (mixed) {
+                const float xcf = (float)xc;
+                xc_f.push_back(xcf);
+                float t[3 * NGM_F] = {0};
+                for (int n = 0; n < ng; ++n) {
+                    t[n] = (float)(nx[n] - (double)xcf);
+                    t[NGM_F + n] = (float)(nx[n] > 0 ? std::log(nx[n] / (double)xcf) : 0.0);
+                    t[2 * NGM_F + n] = (float)nw[n];
+                }
+                ntab_f.insert(ntab_f.end(), t, t + 3 * NGM_F);
+            } else {
+                double t[3 * NGM_D] = {0};
+                for (int n = 0; n < ng; ++n) {
+                    t[n] = nx[n];
+                    t[NGM_D + n] = nx[n] > 0 ? std::log(nx[n]) : 0.0;
+                    t[2 * NGM_D + n] = nw[n];
+                }
+                ntab_d.insert(ntab_d.end(), t, t + 3 * NGM_D);
+            }
+            (void)NGM;
+        }
+        noff += J;
+    }
+    a.Jmax = c->Jmax;
+    int rc;
+    if ((rc = upload(c, edges_all, &a.edges))) return rc;
+    if ((rc = upload(c, bcls, &a.bclass))) return rc;
+    if (mixed) {
+        if ((rc = upload(c, ntab_f, &a.ntab_f))) return rc;
+        if ((rc = upload(c, xc_f, &a.xc_f))) return rc;
+    } else {
+        if ((rc = upload(c, ntab_d, &a.ntab_d))) return rc;
+    }
+    // fine centres and spectra
+    std::vector<float> Ehi(c->K), Elo(c->K), Sf(c->Sn.size());
+    for (int k = 0; k < c->K; ++k) { Ehi[k] = (float)c->E[k]; Elo[k] = (float)(c->E[k] - (double)Ehi[k]); }
+    for (size_t i = 0; i < Sf.size(); ++i) Sf[i] = (float)c->Sn[i];
+    if ((rc = upload(c, c->E, &a.E))) return rc;
+    if ((rc = upload(c, Ehi, &a.E_hi))) return rc;
+    if ((rc = upload(c, Elo, &a.E_lo))) return rc;
+    if (mixed) { if ((rc = upload(c, Sf, &a.Sf))) return rc; }
+    else       { if ((rc = upload(c, c->Sn, &a.Sd))) return rc; }
+    if ((rc = upload(c, c->slot_map, &a.slot_map))) return rc;
+    if ((rc = upload(c, c->pull_p, &a.pull_param))) return rc;
+    if ((rc = upload(c, c->pull_c, &a.pull_c))) return rc;
+    if ((rc = upload(c, c->pull_w, &a.pull_w))) return rc;
+    // default counts and windows (single-point calls)
+    std::vector<double> cnt;
+    std::vector<int> win;
+    for (int d = 0; d < c->D; ++d) {
+        cnt.insert(cnt.end(), c->counts[d].begin(), c->counts[d].end());
+        win.push_back(c->wlo[d]); win.push_back(c->whi[d]);
+    }
+    const double* dc; const int* dw;
+    if ((rc = upload(c, cnt, &dc))) return rc;
+    if ((rc = upload(c, win, &dw))) return rc;
+    a.counts = dc; a.win = dw;
+    a.nblk = (c->K + COLBLK - 1) / COLBLK;
+    a.NPART = NRESP + MAXGDS * c->S;
+    c->ready = true;
+    return GSN_OK;
+}
+
+// allocate scratch for T toys under plan p and fill the launch fields of a
+int prepare(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
+    a.work = nullptr;
+    const size_t rs = c->opt.precision == GSN_MIXED ? sizeof(float) : sizeof(double);
+    int rc;
+    if ((rc = ensure(c, c->colbuf, (size_t)T * c->G * c->K * NFP * rs))) return rc;
+    if ((rc = ensure(c, c->blkbuf, (size_t)T * c->G * a.nblk * 2 * rs))) return rc;
+    if ((rc = ensure(c, c->mubuf, (size_t)T * p.nsplit * c->total_bins * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->wbuf, (size_t)T * c->total_bins * rs))) return rc;
+    if ((rc = ensure(c, c->partbuf, (size_t)T * c->G * p.nbtask * a.NPART * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->gdirect, (size_t)T * c->P * sizeof(double)))) return rc;
+    a.T = T;
+    a.nsplit = p.nsplit; a.ntile = p.ntile;
+    a.bw_warps = p.bw_warps; a.bw_bsplit = p.bw_bsplit; a.nbtask = p.nbtask;
+    a.colbuf = c->colbuf.p; a.blkbuf = c->blkbuf.p; a.mubuf = (double*)c->mubuf.p;
+    a.wbuf = c->wbuf.p; a.partbuf = (double*)c->partbuf.p; a.gdirect = (double*)c->gdirect.p;
+    return GSN_OK;
+}
+
+cudaEvent_t take_event(gsn_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// resolve recorded event pairs into the per-kernel sums (synchronises the stream)
+int drain_profile(gsn_ctx* c) {
+    if (c->pending.empty()) return GSN_OK;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.e0, p.e1);
+        c->prof_ms[p.kernel] += ms;
+        c->prof_n[p.kernel] += 1;
+        c->event_pool.push_back(p.e0);
+        c->event_pool.push_back(p.e1);
+    }
+    c->pending.clear();
+    return GSN_OK;
+}
+
+// launch one kernel class, bracketed by events while tracing is on
+template <class F>
+int launch(gsn_ctx* c, int kernel, KArgs& a, F fn) {
+    a.work = c->prof ? (unsigned long long*)c->work.p : nullptr;
+    if (!c->prof) {
+        CUDA_TRY(c, fn(a, c->stream));
+        return GSN_OK;
+    }
+    gsn_ctx::Pending p{kernel, take_event(c), take_event(c)};
+    CUDA_TRY(c, cudaEventRecord(p.e0, c->stream));
+    CUDA_TRY(c, fn(a, c->stream));
+    CUDA_TRY(c, cudaEventRecord(p.e1, c->stream));
+    c->pending.push_back(p);
+    if (c->pending.size() > 4096) return drain_profile(c);
+    return GSN_OK;
+}
+
+int run_step(gsn_ctx* c, KArgs& a, bool grad) {
+    int rc;
+    if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
+    if ((rc = launch(c, K_FORWARD, a, launch_forward))) return rc;
+    if ((rc = launch(c, K_DEVIANCE, a, launch_deviance))) return rc;
+    if (grad) {
+        if ((rc = launch(c, K_BACKWARD, a, launch_backward))) return rc;
+        if ((rc = launch(c, K_GRADFINAL, a, launch_gradfinal))) return rc;
+    }
+    return GSN_OK;
+}
+
+int status_message(gsn_ctx* c, int st, int toy) {
+    if (st == 0) return GSN_OK;
+    char buf[160];
+    if (st == GSN_ERR_NONPOSITIVE_MU)
+        snprintf(buf, sizeof buf, "toy %d: expected counts <= 0 in a bin with observed counts", toy);
+    else
+        snprintf(buf, sizeof buf, "toy %d: non-finite expected counts, NLL or gradient", toy);
+    return fail(c, st, buf);
+}
+
+int check_params_host(gsn_ctx* c, const double* params) {
+    if (!params) return fail(c, GSN_ERR_ARG, "params is NULL");
+    for (int p = 0; p < c->P; ++p)
+        if (!std::isfinite(params[p])) return fail(c, GSN_ERR_NONFINITE, "parameter " + std::to_string(p) + " is not finite");
+    return GSN_OK;
+}
+
+// batched step on device pointers; T toys, chunked by max_toys_per_launch
+int batch_device(gsn_ctx* c, int n_toys, const double* params, const double* counts, const int* win,
+                 double* nll, double* grad, int* status) {
+    int rc;
+    if ((rc = finalize(c))) return rc;
+    const int chunk = std::max(1, c->opt.max_toys_per_launch);
+    for (int t0 = 0; t0 < n_toys; t0 += chunk) {
+        const int T = std::min(chunk, n_toys - t0);
+        KArgs a = c->base;
+        const Plan p = make_plan(c, T);
+        if ((rc = prepare(c, T, p, a))) return rc;
+        a.params = params + (size_t)t0 * c->P; a.params_stride = c->P;
+        a.counts = counts + (size_t)t0 * c->total_bins; a.counts_stride = c->total_bins;
+        a.win = win + (size_t)t0 * c->D * 2; a.win_stride = 2 * c->D;
+        a.nll = nll + t0;
+        a.grad = grad ? grad + (size_t)t0 * c->P : nullptr;
+        a.status = status ? status + t0 : nullptr;
+        a.want_grad = grad ? 1 : 0;
+        if ((rc = run_step(c, a, grad != nullptr))) return rc;
+    }
+    return GSN_OK;
+}
+
+}  // namespace
+
+// ======================================================================= API
+extern "C" {
+
+int gsn_default_options(gsn_options* o) {
+    if (!o) return GSN_ERR_ARG;
+    std::memset(o, 0, sizeof *o);
+    o->precision = GSN_FP64;
+    o->resolution = GSN_RES_GAUSS;
+    o->band_cut = 0.0;
+    o->birks_s0 = 1.55;
+    o->birks_s1 = 0.155;
+    o->device = 0;
+    o->stream = nullptr;
+    o->max_toys_per_launch = 4096;
+    return GSN_OK;
+}
+
+int gsn_n_slots(int n_species) { return 3 * n_species + 5; }
+
+int gsn_create(gsn_ctx** out, const gsn_options* opt) {
+    if (!out) return GSN_ERR_ARG;
+    *out = nullptr;
+    gsn_ctx* c = new gsn_ctx();
+    if (opt) c->opt = *opt; else gsn_default_options(&c->opt);
+    gsn_options& o = c->opt;
+    if (o.precision != GSN_FP64 && o.precision != GSN_MIXED) { delete c; return GSN_ERR_ARG; }
+    if (o.resolution != GSN_RES_GAUSS && o.resolution != GSN_RES_GAMMA) { delete c; return GSN_ERR_ARG; }
+    if (!(o.band_cut > 0)) o.band_cut = o.precision == GSN_FP64 ? 34.5 : 20.7;
+    if (!(o.birks_s0 > 0)) o.birks_s0 = 1.55;
+    if (o.birks_s1 < 0) o.birks_s1 = 0.155;
+    if (o.max_toys_per_launch <= 0) o.max_toys_per_launch = 4096;
+    o.max_toys_per_launch = std::min(o.max_toys_per_launch, 65535 / MAXG);
+    c->dev = o.device;
+    if (cudaSetDevice(c->dev) != cudaSuccess) { cudaGetLastError(); delete c; return GSN_ERR_CUDA; }
+    if (o.stream) {
+        c->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return GSN_ERR_CUDA; }
+        c->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
+    if (c->nsm <= 0) c->nsm = 1;
+    *out = c;
+    return GSN_OK;
+}
+
+void gsn_destroy(gsn_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_owned(c);
+    for (Buf* b : {&c->colbuf, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->params, &c->counts_b,
+                   &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf})
+        if (b->p) cudaFree(b->p);
+    if (c->work.p) cudaFree(c->work.p);
+    for (auto& p : c->pending) { c->event_pool.push_back(p.e0); c->event_pool.push_back(p.e1); }
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int gsn_profile(gsn_ctx* c, int enable) {
+    if (!c) return GSN_ERR_ARG;
+    int rc;
+    if ((rc = drain_profile(c))) return rc;
+    if (enable) {
+        if ((rc = ensure(c, c->work, K_COUNT * sizeof(unsigned long long)))) return rc;
+        CUDA_TRY(c, cudaMemsetAsync(c->work.p, 0, K_COUNT * sizeof(unsigned long long), c->stream));
+        for (int i = 0; i < K_COUNT; ++i) { c->prof_ms[i] = 0.0; c->prof_n[i] = 0; }
+    }
+    c->prof = enable != 0;
+    return GSN_OK;
+}
+
+int gsn_profile_read(gsn_ctx* c, int kernel, double* total_ms, long long* launches, unsigned long long* units) {
+    if (!c || kernel < 0 || kernel >= K_COUNT) return GSN_ERR_ARG;
+    int rc;
+    if ((rc = drain_profile(c))) return rc;
+    unsigned long long w[K_COUNT] = {0};
+    if (c->work.p) {
+        CUDA_TRY(c, cudaMemcpyAsync(w, c->work.p, sizeof w, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    if (total_ms) *total_ms = c->prof_ms[kernel];
+    if (launches) *launches = c->prof_n[kernel];
+    if (units) *units = w[kernel];
+    return GSN_OK;
+}
+
+const char* gsn_kernel_name(int kernel) {
+    static const char* names[K_COUNT] = {"columns", "forward", "deviance", "backward", "gradfinal", "species", "mu"};
+    return (kernel >= 0 && kernel < K_COUNT) ? names[kernel] : "";
+}
+
+int gsn_peak_probe(int device, int which, double* ops) {
+    if (!ops || which < 0 || which > 3) return GSN_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return GSN_ERR_CUDA; }
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    if (run_probe(which, nsm, ops) != cudaSuccess) { cudaGetLastError(); return GSN_ERR_CUDA; }
+    return GSN_OK;
+}
+
+const char* gsn_last_error(const gsn_ctx* c) {
+    if (!c) return "no context";
+    return c->err.c_str();
+}
+
+void* gsn_stream(gsn_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int gsn_set_data(gsn_ctx* c, int n_datasets, const int* n_bins, const double* const* bin_edges,
+                 const double* const* counts, const double* exposures, const int* win_lo, const int* win_hi) {
+    if (!c) return GSN_ERR_ARG;
+    if (n_datasets < 1 || n_datasets > GSN_MAX_DATASETS)
+        return fail(c, GSN_ERR_ARG, "n_datasets must be in 1.." + std::to_string(GSN_MAX_DATASETS));
+    if (!n_bins || !bin_edges || !counts || !exposures || !win_lo || !win_hi) return fail(c, GSN_ERR_ARG, "NULL argument");
+    std::vector<int> nb(n_datasets);
+    std::vector<std::vector<double>> ed(n_datasets), cn(n_datasets);
+    std::vector<double> ex(n_datasets);
+    std::vector<int> lo(n_datasets), hi(n_datasets);
+    for (int d = 0; d < n_datasets; ++d) {
+        if (n_bins[d] < 1) return fail(c, GSN_ERR_ARG, "n_bins must be >= 1");
+        if (!bin_edges[d] || !counts[d]) return fail(c, GSN_ERR_ARG, "NULL edges or counts");
+        nb[d] = n_bins[d];
+        ed[d].assign(bin_edges[d], bin_edges[d] + n_bins[d] + 1);
+        cn[d].assign(counts[d], counts[d] + n_bins[d]);
+        for (int j = 0; j < n_bins[d]; ++j) {
+            if (!(ed[d][j + 1] > ed[d][j]) || !std::isfinite(ed[d][j + 1]) || !std::isfinite(ed[d][j]))
+                return fail(c, GSN_ERR_ARG, "bin edges must be finite and strictly ascending");
+            if (!(cn[d][j] >= 0.0) || !std::isfinite(cn[d][j])) return fail(c, GSN_ERR_ARG, "counts must be finite and >= 0");
+        }
+        if (!(exposures[d] > 0.0) || !std::isfinite(exposures[d])) return fail(c, GSN_ERR_ARG, "exposures must be > 0");
+        ex[d] = exposures[d];
+        if (win_lo[d] < 0 || win_hi[d] > n_bins[d] || win_lo[d] > win_hi[d])
+            return fail(c, GSN_ERR_ARG, "window must satisfy 0 <= lo <= hi <= n_bins");
+        lo[d] = win_lo[d]; hi[d] = win_hi[d];
+    }
+    if (c->have_species && n_datasets != c->D) c->have_species = c->have_params = false;
+    c->D = n_datasets; c->nb = nb; c->edges = ed; c->counts = cn; c->eps = ex; c->wlo = lo; c->whi = hi;
+    c->have_data = true;
+    c->ready = false;
+    return GSN_OK;
+}
+
+int gsn_set_species(gsn_ctx* c, int n_species, int n_fine, const double* fine_centres, const double* spectra,
+                    const int* kind, const double* shift, const unsigned char* dataset_mask) {
+    if (!c) return GSN_ERR_ARG;
+    if (!c->have_data) return fail(c, GSN_ERR_STATE, "gsn_set_data must come first");
+    if (n_species < 1 || n_species > GSN_MAX_SPECIES) return fail(c, GSN_ERR_ARG, "n_species must be in 1..64");
+    if (n_fine < 2) return fail(c, GSN_ERR_ARG, "n_fine must be >= 2");
+    if (!fine_centres || !spectra || !kind || !dataset_mask) return fail(c, GSN_ERR_ARG, "NULL argument");
+    std::vector<double> E(fine_centres, fine_centres + n_fine);
+    for (int k = 0; k < n_fine; ++k) {
+        if (!(E[k] > 0.0) || !std::isfinite(E[k])) return fail(c, GSN_ERR_ARG, "fine centres must be finite and > 0");
+        if (k && !(E[k] > E[k - 1])) return fail(c, GSN_ERR_ARG, "fine centres must be strictly ascending");
+    }
+    const double dE = (E[n_fine - 1] - E[0]) / (n_fine - 1);
+    std::vector<double> Sn((size_t)n_species * n_fine, 0.0);
+    std::vector<int> kd(kind, kind + n_species);
+    for (int s = 0; s < n_species; ++s) {
+        if (kd[s] < GSN_ANA || kd[s] > GSN_ANA_PEAK) return fail(c, GSN_ERR_ARG, "unknown species kind");
+        if (kd[s] == GSN_ANA_PEAK) continue;
+        double tot = 0.0;
+        for (int k = 0; k < n_fine; ++k) {
+            const double v = spectra[(size_t)s * n_fine + k];
+            if (!(v >= 0.0) || !std::isfinite(v)) return fail(c, GSN_ERR_ARG, "spectra must be finite and >= 0");
+            tot += v;
+        }
+        long n = 0;
+        if (kd[s] == GSN_ANA_SHIFT && shift) {
+            for (int k = 1; k < n_fine; ++k)
+                if (std::fabs((E[k] - E[k - 1]) - dE) > 1e-9 * dE)
+                    return fail(c, GSN_ERR_ARG, "AnaShift needs uniformly spaced fine centres");
+            n = (long)std::floor(shift[s] / dE + 0.5);
+        }
+        if (tot <= 0.0) continue;
+        for (int k = 0; k < n_fine; ++k) {
+            const long src = (long)k - n;
+            if (src >= 0 && src < n_fine) Sn[(size_t)s * n_fine + k] = spectra[(size_t)s * n_fine + src] / tot;
+        }
+    }
+    c->S = n_species; c->K = n_fine; c->E = E; c->Sn = Sn; c->kind = kd;
+    c->mask.assign(dataset_mask, dataset_mask + (size_t)n_species * c->D);
+    c->have_species = true;
+    c->have_params = false;
+    c->ready = false;
+    return GSN_OK;
+}
+
+int gsn_set_params(gsn_ctx* c, int n_params, const int* slot_map, int n_pulls, const int* pull_param,
+                   const double* pull_centre, const double* pull_width) {
+    if (!c) return GSN_ERR_ARG;
+    if (!c->have_species) return fail(c, GSN_ERR_STATE, "gsn_set_species must come first");
+    if (n_params < 1 || !slot_map) return fail(c, GSN_ERR_ARG, "n_params must be >= 1 and slot_map non-NULL");
+    const int NS = gsn_n_slots(c->S);
+    std::vector<int> sm(slot_map, slot_map + (size_t)c->D * NS);
+    for (int d = 0; d < c->D; ++d) {
+        for (int i = 0; i < NS; ++i)
+            if (sm[d * NS + i] < -1 || sm[d * NS + i] >= n_params) return fail(c, GSN_ERR_ARG, "slot_map entry out of range");
+        for (int i = 0; i < 5; ++i)
+            if (sm[d * NS + c->S + i] < 0) return fail(c, GSN_ERR_ARG, "response slots (LY, kB, a, b, c) must be mapped");
+        for (int s = 0; s < c->S; ++s)
+            if (c->kind[s] == GSN_ANA_PEAK && c->mask[s * c->D + d] &&
+                (sm[d * NS + GSN_SLOT_M(c->S, s)] < 0 || sm[d * NS + GSN_SLOT_W(c->S, s)] < 0))
+                return fail(c, GSN_ERR_ARG, "AnaPeak species need mapped position and width slots");
+    }
+    if (n_pulls < 0 || (n_pulls > 0 && (!pull_param || !pull_centre || !pull_width)))
+        return fail(c, GSN_ERR_ARG, "bad pull arguments");
+    std::vector<int> pp(pull_param, pull_param + n_pulls);
+    std::vector<double> pc(pull_centre, pull_centre + n_pulls), pw(pull_width, pull_width + n_pulls);
+    for (int i = 0; i < n_pulls; ++i)
+        if (pp[i] < 0 || pp[i] >= n_params || !(pw[i] > 0)) return fail(c, GSN_ERR_ARG, "bad pull term");
+    c->P = n_params; c->slot_map = sm; c->pull_p = pp; c->pull_c = pc; c->pull_w = pw;
+    c->have_params = true;
+    c->ready = false;
+    return GSN_OK;
+}
+
+int gsn_eval_grad(gsn_ctx* c, const double* params, double* nll, double* grad) {
+    if (!c) return GSN_ERR_ARG;
+    int rc;
+    if ((rc = finalize(c))) return rc;
+    if (!nll) return fail(c, GSN_ERR_ARG, "nll is NULL");
+    if ((rc = check_params_host(c, params))) return rc;
+    if ((rc = ensure(c, c->params, c->P * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->nll_b, sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->grad_b, c->P * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->status_b, sizeof(int)))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->params.p, params, c->P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    KArgs a = c->base;
+    const Plan p = make_plan(c, 1);
+    if ((rc = prepare(c, 1, p, a))) return rc;
+    a.params = (const double*)c->params.p; a.params_stride = c->P;
+    a.counts_stride = 0; a.win_stride = 0;
+    a.nll = (double*)c->nll_b.p; a.grad = grad ? (double*)c->grad_b.p : nullptr; a.status = (int*)c->status_b.p;
+    a.want_grad = grad ? 1 : 0;
+    if ((rc = run_step(c, a, grad != nullptr))) return rc;
+    int st = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(nll, c->nll_b.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (grad) CUDA_TRY(c, cudaMemcpyAsync(grad, c->grad_b.p, c->P * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(&st, c->status_b.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return status_message(c, st, 0);
+}
+
+// per-species expected shapes M[g][s][j] at the response parameters of params (T = 1)
+static int compute_species(gsn_ctx* c, const double* params_dev) {
+    int rc;
+    KArgs a = c->base;
+    const Plan p = make_plan(c, 1);
+    if ((rc = prepare(c, 1, p, a))) return rc;
+    if ((rc = ensure(c, c->Mbuf, (size_t)c->G * c->S * c->Jmax * sizeof(double)))) return rc;
+    a.params = params_dev; a.params_stride = c->P;
+    a.counts_stride = 0; a.win_stride = 0;
+    a.Mbuf = (double*)c->Mbuf.p;
+    a.sp_first = 0; a.sp_count = c->S;
+    if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
+    if ((rc = launch(c, K_SPECIES, a, launch_species))) return rc;
+    return GSN_OK;
+}
+
+int gsn_eval(gsn_ctx* c, const double* params, double* nll) {
+    if (!c) return GSN_ERR_ARG;
+    int rc;
+    if ((rc = finalize(c))) return rc;
+    if (!nll) return fail(c, GSN_ERR_ARG, "nll is NULL");
+    if ((rc = check_params_host(c, params))) return rc;
+    if ((rc = ensure(c, c->params, c->P * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->nll_b, sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->status_b, sizeof(int)))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->params.p, params, c->P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    std::vector<double> key;
+    for (int g = 0; g < c->G; ++g)
+        for (int i = 0; i < NRESP; ++i) key.push_back(params[c->base.g_resp[g][i]]);
+    const bool hit = c->cache_valid && key.size() == c->cache_key.size() &&
+                     std::memcmp(key.data(), c->cache_key.data(), key.size() * sizeof(double)) == 0;
+    if (!hit) {
+        if ((rc = compute_species(c, (const double*)c->params.p))) return rc;
+        c->cache_key = key;
+        c->cache_valid = true;
+    }
+    KArgs a = c->base;
+    Plan p = make_plan(c, 1);
+    p.nsplit = 1;
+    if ((rc = prepare(c, 1, p, a))) return rc;
+    a.params = (const double*)c->params.p; a.params_stride = c->P;
+    a.counts_stride = 0; a.win_stride = 0;
+    a.Mbuf = (double*)c->Mbuf.p;
+    a.nll = (double*)c->nll_b.p; a.grad = nullptr; a.status = (int*)c->status_b.p;
+    a.want_grad = 0;
+    if ((rc = launch(c, K_MU, a, launch_mu_from_species))) return rc;
+    if ((rc = launch(c, K_DEVIANCE, a, launch_deviance))) return rc;
+    int st = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(nll, c->nll_b.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(&st, c->status_b.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return status_message(c, st, 0);
+}
+
+int gsn_expected(gsn_ctx* c, const double* params, int dataset, double* mu_per_species) {
+    if (!c) return GSN_ERR_ARG;
+    int rc;
+    if ((rc = finalize(c))) return rc;
+    if (dataset < 0 || dataset >= c->D || !mu_per_species) return fail(c, GSN_ERR_ARG, "bad dataset or NULL output");
+    if ((rc = check_params_host(c, params))) return rc;
+    if ((rc = ensure(c, c->params, c->P * sizeof(double)))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->params.p, params, c->P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if ((rc = compute_species(c, (const double*)c->params.p))) return rc;
+    c->cache_valid = false;
+    const size_t n = (size_t)c->nb[dataset] * c->S;
+    if ((rc = ensure(c, c->outbuf, n * sizeof(double)))) return rc;
+    KArgs a = c->base;
+    a.T = 1;
+    a.params = (const double*)c->params.p;
+    a.Mbuf = (double*)c->Mbuf.p;
+    a.out_species = (double*)c->outbuf.p;
+    a.out_dataset = dataset;
+    if ((rc = launch(c, K_SPECIES, a, launch_expected_out))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(mu_per_species, c->outbuf.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return GSN_OK;
+}
+
+int gsn_eval_grad_batch_dev(gsn_ctx* c, int n_toys, const double* params_dev, const double* toy_counts_dev,
+                            const int* toy_win_dev, double* nll_dev, double* grad_dev, int* status_dev) {
+    if (!c) return GSN_ERR_ARG;
+    if (n_toys < 0) return fail(c, GSN_ERR_ARG, "n_toys must be >= 0");
+    if (n_toys == 0) return GSN_OK;
+    if (!params_dev || !toy_counts_dev || !toy_win_dev || !nll_dev) return fail(c, GSN_ERR_ARG, "NULL argument");
+    return batch_device(c, n_toys, params_dev, toy_counts_dev, toy_win_dev, nll_dev, grad_dev, status_dev);
+}
+
+int gsn_eval_grad_batch(gsn_ctx* c, int n_toys, const double* params, const double* toy_counts, const int* toy_win,
+                        double* nll, double* grad) {
+    if (!c) return GSN_ERR_ARG;
+    int rc;
+    if ((rc = finalize(c))) return rc;
+    if (n_toys < 0) return fail(c, GSN_ERR_ARG, "n_toys must be >= 0");
+    if (n_toys == 0) return GSN_OK;
+    if (!params || !toy_counts || !toy_win || !nll) return fail(c, GSN_ERR_ARG, "NULL argument");
+    for (long long i = 0; i < (long long)n_toys * c->P; ++i)
+        if (!std::isfinite(params[i])) return fail(c, GSN_ERR_NONFINITE, "toy parameter not finite");
+    for (long long i = 0; i < (long long)n_toys * c->D; ++i) {
+        const int d = (int)(i % c->D);
+        const int lo = toy_win[2 * i], hi = toy_win[2 * i + 1];
+        if (lo < 0 || hi > c->nb[d] || lo > hi) return fail(c, GSN_ERR_ARG, "toy window out of range");
+    }
+    const size_t TB = (size_t)n_toys;
+    if ((rc = ensure(c, c->params, TB * c->P * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->counts_b, TB * c->total_bins * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->win_b, TB * c->D * 2 * sizeof(int)))) return rc;
+    if ((rc = ensure(c, c->nll_b, TB * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->grad_b, TB * c->P * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->status_b, TB * sizeof(int)))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->params.p, params, TB * c->P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->counts_b.p, toy_counts, TB * c->total_bins * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->win_b.p, toy_win, TB * c->D * 2 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    if ((rc = batch_device(c, n_toys, (const double*)c->params.p, (const double*)c->counts_b.p, (const int*)c->win_b.p,
+                           (double*)c->nll_b.p, grad ? (double*)c->grad_b.p : nullptr, (int*)c->status_b.p)))
+        return rc;
+    std::vector<int> st(n_toys);
+    CUDA_TRY(c, cudaMemcpyAsync(nll, c->nll_b.p, TB * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (grad) CUDA_TRY(c, cudaMemcpyAsync(grad, c->grad_b.p, TB * c->P * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(st.data(), c->status_b.p, TB * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int t = 0; t < n_toys; ++t)
+        if (st[t]) return status_message(c, st[t], t);
+    return GSN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal definitions shared by the host API and the kernels of libgsn.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gsn {
+
+constexpr int MAXD = 8;      // datasets
+constexpr int MAXS = 64;     // species
+constexpr int MAXG = 8;      // response groups
+constexpr int MAXGDS = 3;    // datasets sharing one response group
+
+// Gauss-Legendre nodes per bin.  Mixed: 3 linear nodes, 6 log-spaced nodes for
+// bins whose lower edge lies below XLOG_F.  FP64: 5 linear, 10 log-spaced below XLOG_D.
+constexpr int NGM_F = 6, NG_LIN_F = 3, NG_LOG_F = 6;
+constexpr int NGM_D = 10, NG_LIN_D = 5, NG_LOG_D = 10;
+constexpr double XLOG_F = 8.0, XLOG_D = 16.0;
+
+// bin classes of the node table
+constexpr unsigned char BIN_LIN = 0, BIN_LOG = 1, BIN_ZERO = 2;
+
+constexpr int COLBLK = 256;  // columns per column-kernel block and per band summary
+constexpr int NFP = 16;      // fields per column record
+
+// Column record fields.
+//  mixed gamma : MUH/MUL double-float mean, A = 1/mu, B = d, C = -1/s,
+//                N = density at the mean, KAPPA = ln d - psi(d)
+//  mixed gauss : MUH/MUL, A = 1/sigma, N = 1/(sigma sqrt(2 pi))
+//  fp64 gamma  : MUH = mu, A = -d ln s - lgamma(d), B = d-1, C = 1/s,
+//                KAPPA = ln s + psi(d), N = 1
+//  fp64 gauss  : MUH = mu, A = 1/sigma, N = 1
+//  all         : DEQ = d E_q / d kB, XMIN/XMAX = band in p.e., P0/P0D/P0S =
+//                bin-at-zero content and its d- and s-derivatives (gamma, / N,
+//                P0S times s^2), TN0.. = N_k * T_dk of each dataset of the group
+enum { F_MUH = 0, F_MUL, F_A, F_B, F_C, F_N, F_KAPPA, F_DEQ, F_XMIN, F_XMAX,
+       F_P0, F_P0D, F_P0S, F_TN0 };
+static_assert(F_TN0 + MAXGDS <= NFP, "column record too small");
+
+constexpr int NRESP = 5;  // LY, kB, a, b, c
+
+struct KArgs {
+    // problem
+    int T, D, S, K, P, NSLOT, G, total_bins, nsplit, n_pulls;
+    int res;          // 0 gauss, 1 gamma
+    int precision;    // 0 fp64, 1 mixed
+    double cut;       // band cut on the log-density
+    double s0, s1;    // stopping power model
+    int ds_bins[MAXD], ds_off[MAXD], ds_group[MAXD], ds_in_group[MAXD];
+    double ds_eps[MAXD];
+    int g_nds[MAXG], g_ds[MAXG][MAXGDS], g_bins[MAXG], g_edge_off[MAXG], g_node_off[MAXG];
+    int g_resp[MAXG][NRESP];
+    int g_zero[MAXG];           // first edge of the group is 0 (gamma bin-at-zero)
+    int sp_kind[MAXS];
+    unsigned sp_mask[MAXS];     // bit d set when species contributes to dataset d
+    // device-resident problem arrays
+    const double* edges;        // per group, J_g + 1 edges, concatenated
+    const float* ntab_f;        // [bin][3][NGM_F]: offset from centre, ln(x/xc), weight
+    const float* xc_f;          // [bin] bin centre
+    const unsigned char* bclass;// [bin] BIN_LIN / BIN_LOG / BIN_ZERO
+    const double* ntab_d;       // [bin][3][NGM_D]: x, ln x, weight
+    const double* E;            // fine centres [K]
+    const float* E_hi;          // double-float split of E
+    const float* E_lo;
+    const float* Sf;            // normalised shifted spectra [S][K]
+    const double* Sd;
+    const int* slot_map;        // [D][NSLOT]
+    const int* pull_param;
+    const double* pull_c;
+    const double* pull_w;
+    // per launch
+    const double* params;  long long params_stride;   // [T][P]
+    const double* counts;  long long counts_stride;   // [T][total_bins]
+    const int* win;        long long win_stride;      // [T][D][2]
+    // scratch
+    void* colbuf;          // [T][G][K][NFP] of Real
+    void* blkbuf;          // [T][G][nblk][2] of Real: min xmin, max xmax
+    double* mubuf;         // [T][nsplit][total_bins]
+    void* wbuf;            // [T][total_bins] of Real
+    double* partbuf;       // [T][G][nbtask][NPART]
+    double* gdirect;       // [T][P]
+    int nblk;
+    int nbtask, bw_warps, bw_bsplit, NPART;
+    int ntile;             // forward tiles per group (max over groups)
+    // outputs
+    double* nll;
+    double* grad;
+    int* status;
+    int want_grad;
+    // per-species path (eval with response cache, expected counts)
+    double* Mbuf;          // [G][S][J_g max]
+    int Jmax;
+    int sp_first, sp_count;
+    double* out_species;   // [J][S] for gsn_expected
+    int out_dataset;
+    // statistics: evaluated (bin, column) pairs per kernel class (NULL = off)
+    unsigned long long* work;
+};
+
+// launchers (gsn_kernels.cu); return cudaError_t of the launches
+cudaError_t launch_columns(const KArgs& a, cudaStream_t st);
+cudaError_t launch_forward(const KArgs& a, cudaStream_t st);
+cudaError_t launch_deviance(const KArgs& a, cudaStream_t st);
+cudaError_t launch_backward(const KArgs& a, cudaStream_t st);
+cudaError_t launch_gradfinal(const KArgs& a, cudaStream_t st);
+cudaError_t launch_species(const KArgs& a, cudaStream_t st);
+cudaError_t launch_mu_from_species(const KArgs& a, cudaStream_t st);
+cudaError_t launch_expected_out(const KArgs& a, cudaStream_t st);
+cudaError_t run_probe(int which, int nsm, double* ops_per_second);
+
+constexpr int K_COLUMNS = 0, K_FORWARD = 1, K_DEVIANCE = 2, K_BACKWARD = 3, K_GRADFINAL = 4,
+              K_SPECIES = 5, K_MU = 6, K_COUNT = 7;
+
+}  // namespace gsn

@@ -1,0 +1,1143 @@
+// Kernels of the binned spectral-fit likelihood (GooStats, arXiv:1812.05686).
+//
+// One minimiser step for T parameter points ("toys") runs as
+//   k_columns   per fine column k: visible mean mu_k (Birks quenching, section
+//               2.3 reading), resolution, response band, rate-weighted spectra
+//               T_dk = eps_d sum_s r_s S'_sk of each dataset (section 3.2)
+//   k_forward   mu_dj = sum_k R_jk T_dk: the response bin integrals R_jk are
+//               generated in registers and contracted at once (the
+//               "response mesh" and "smearing convolution" of section 2.5 fused)
+//   k_deviance  FP64 Poisson deviance of Eq. (LL), pulls, fixed-order reduction,
+//               w_dj = 1 - n_dj / mu_dj for the adjoint, AnaPeak terms
+//   k_backward  adjoint: per column, sums over the band of w-weighted response
+//               values and their derivatives, then the chain rule to
+//               (LY, kB, a, b, c) and S'^T u for the rates
+//   k_gradfinal fixed-order sum of the per-task partial gradients and scatter
+//               through the slot map (section 2.2 parameter synchronisation)
+// Mixed precision: FP32 response build and contraction with double-float
+// column means, FP32 partial sums flushed to FP64 per column block, FP64
+// deviance and reductions.  FP64: everything in double.
+#include "gsn_internal.cuh"
+
+#include <math.h>
+
+namespace gsn {
+
+#define DEV __device__ __forceinline__
+
+constexpr float L2E = 1.4426950408889634f;           // log2(e)
+constexpr double INV_SQRT2 = 0.70710678118654752440;
+constexpr double INV_SQRT2PI = 0.39894228040143267794;
+constexpr int FWD_WARPS = 8;
+
+// ------------------------------------------------------------------ math --
+DEV float ex2f(float x) {  // 2^x on the SFU
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// D(t) = ln(1 + t) - t with relative precision: for t in [-1/2, 1] from the
+// series ln(1+t) = 2 atanh(u), u = t/(2+t), rearranged so that no leading
+// terms cancel: D = -t u + 2 u^3 (1/3 + u^2/5 + u^4/7 + ...).
+DEV float log1pmx_f(float t) {
+    if (t >= -0.5f && t <= 1.0f) {
+        float u = __fdividef(t, 2.0f + t);
+        float v = u * u;
+        float p = fmaf(v, 1.0f / 15.0f, 1.0f / 13.0f);
+        p = fmaf(p, v, 1.0f / 11.0f);
+        p = fmaf(p, v, 1.0f / 9.0f);
+        p = fmaf(p, v, 1.0f / 7.0f);
+        p = fmaf(p, v, 1.0f / 5.0f);
+        p = fmaf(p, v, 1.0f / 3.0f);
+        return fmaf(2.0f * u * v, p, -t * u);
+    }
+    return log1pf(t) - t;
+}
+// D(t) and L1 = ln(1 + t) together; L1 directly from log1p where |t| is large
+DEV float log1pmx2_f(float t, float& L1) {
+    if (t >= -0.5f && t <= 1.0f) {
+        const float D = log1pmx_f(t);
+        L1 = D + t;
+        return D;
+    }
+    L1 = log1pf(t);
+    return L1 - t;
+}
+
+// digamma by upward recurrence and the asymptotic series (Abramowitz & Stegun 6.3.18)
+DEV double digamma_d(double x) {
+    double acc = 0.0;
+    while (x < 12.0) { acc -= 1.0 / x; x += 1.0; }
+    double ix = 1.0 / x, ix2 = ix * ix;
+    double s = ix2 * (1.0 / 12 - ix2 * (1.0 / 120 - ix2 * (1.0 / 252 - ix2 * (1.0 / 240 - ix2 * (1.0 / 132)))));
+    return acc + log(x) - 0.5 * ix - s;
+}
+DEV float digamma_f(float x) {
+    float acc = 0.0f;
+    while (x < 6.0f) { acc -= 1.0f / x; x += 1.0f; }
+    float ix = 1.0f / x, ix2 = ix * ix;
+    float s = ix2 * (1.0f / 12 - ix2 * (1.0f / 120 - ix2 * (1.0f / 252 - ix2 * (1.0f / 240))));
+    return acc + logf(x) - 0.5f * ix - s;
+}
+
+// double-float helpers (error-free products and sums)
+DEV void df_mul(float ah, float al, float bh, float bl, float& rh, float& rl) {
+    float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, fmaf(al, bh, e));
+    rh = p + e;
+    rl = e - (rh - p);
+}
+DEV void df_add(float ah, float al, float b, float& rh, float& rl) {
+    float s = ah + b;
+    float bb = s - ah;
+    float e = (ah - (s - bb)) + (b - bb);
+    e += al;
+    rh = s + e;
+    rl = e - (rh - s);
+}
+
+// Phi(z1) - Phi(z0) for z0 <= z1 without cancellation in the tails
+DEV double ncdf_diff(double z0, double z1) {
+    if (z0 >= 0.0) return 0.5 * (erfc(z0 * INV_SQRT2) - erfc(z1 * INV_SQRT2));
+    if (z1 <= 0.0) return 0.5 * (erfc(-z1 * INV_SQRT2) - erfc(-z0 * INV_SQRT2));
+    return 1.0 - 0.5 * (erfc(-z0 * INV_SQRT2) + erfc(z1 * INV_SQRT2));
+}
+
+template <class R> DEV R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <class R> DEV R warp_min(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <class R> DEV R warp_max(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// fixed-order block sum of one double per thread (result valid in thread 0)
+DEV double block_sum_d(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) s += sh[i];
+    return s;
+}
+
+DEV void toy_window_union(const KArgs& a, int t, int g, int& wlo, int& whi) {
+    const int J = a.g_bins[g];
+    wlo = J; whi = 0;
+    for (int dd = 0; dd < a.g_nds[g]; ++dd) {
+        const int d = a.g_ds[g][dd];
+        int lo = a.win[t * a.win_stride + 2 * d], hi = a.win[t * a.win_stride + 2 * d + 1];
+        lo = max(lo, 0); hi = min(hi, J);
+        if (hi > lo) { wlo = min(wlo, lo); whi = max(whi, hi); }
+    }
+}
+
+template <class R> DEV R* colrec(const KArgs& a, int t, int g, int k) {
+    return reinterpret_cast<R*>(a.colbuf) + (((long long)t * a.G + g) * a.K + k) * NFP;
+}
+
+// ------------------------------------------------------- bin-at-zero -------
+// P(d, y) = e^-y sum_n y^(d+n) / Gamma(d+n+1), its d-derivative (through
+// psi(d+n+1) = psi(d+1) + sum_{m<=n} 1/(d+m)), and s^2 dP/ds = -s y^d e^-y / Gamma(d).
+template <class R> DEV void gamma_bin_zero(R d, R s, R x1, R& P, R& Pd, R& Ps2) {
+    const R y = x1 / s;
+    const R ly = log(y);
+    const R pref = exp(d * ly - y - lgamma(d + R(1)));
+    R term = 1, sum = 1, H = 0, hsum = 0;
+    const int nmax = sizeof(R) == 8 ? 80 : 40;
+    for (int n = 1; n < nmax; ++n) {
+        term *= y / (d + R(n));
+        H += R(1) / (d + R(n));
+        sum += term;
+        hsum += term * H;
+        if (term < R(sizeof(R) == 8 ? 1e-18 : 1e-9) * sum) break;
+    }
+    P = pref * sum;
+    const R psi1 = sizeof(R) == 8 ? (R)digamma_d((double)d + 1.0) : (R)digamma_f((float)d + 1.0f);
+    Pd = P * (ly - psi1) - pref * hsum;
+    Ps2 = -s * exp(d * ly - y - lgamma(d));
+}
+
+// ------------------------------------------------------------- columns -----
+template <class R, int RES>
+__global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
+    const int t = blockIdx.z, g = blockIdx.y;
+    const int k = blockIdx.x * COLBLK + threadIdx.x;
+    __shared__ double sres[NRESP];
+    __shared__ R srate[MAXGDS][MAXS];
+    __shared__ float sdf[8];      // per-toy double-float constants (mixed)
+    __shared__ R sred[2][COLBLK / 32];
+    const double* prm = a.params + (long long)t * a.params_stride;
+    if (threadIdx.x < NRESP) sres[threadIdx.x] = prm[a.g_resp[g][threadIdx.x]];
+    for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
+        const int dd = i / a.S, s = i % a.S;
+        R v = 0;
+        if (dd < a.g_nds[g]) {
+            const int d = a.g_ds[g][dd];
+            if (a.sp_kind[s] != 2 && ((a.sp_mask[s] >> d) & 1u)) {
+                const int p = a.slot_map[d * a.NSLOT + s];
+                if (p >= 0) v = (R)(a.ds_eps[d] * prm[p]);
+            }
+        }
+        srate[dd][s] = v;
+    }
+    __syncthreads();
+    const double LY = sres[0], kB = sres[1], ra = sres[2], rb = sres[3], rc = sres[4];
+    const double alpha = 1.0 + kB * a.s0, beta = kB * a.s1;
+    if (sizeof(R) == 4 && threadIdx.x == 0) {
+        const double ia = 1.0 / alpha;
+        sdf[0] = (float)ia; sdf[1] = (float)(ia - (double)(float)ia);
+        sdf[2] = (float)LY; sdf[3] = (float)(LY - (double)(float)LY);
+        sdf[4] = (float)(beta / (alpha * alpha));                 // beta / alpha^2
+        sdf[5] = beta > 0 ? (float)(alpha / beta) : 0.0f;         // alpha / beta
+        sdf[6] = (float)(a.s0 * beta / alpha);
+        sdf[7] = (float)(1.0 / (alpha * alpha));
+    }
+    __syncthreads();
+
+    R xmin = (R)INFINITY, xmax = (R)-INFINITY;
+    if (k < a.K) {
+        R* rec = colrec<R>(a, t, g, k);
+        R f[NFP];
+#pragma unroll
+        for (int i = 0; i < NFP; ++i) f[i] = 0;
+        R mu, var, deq;
+        if constexpr (sizeof(R) == 4) {
+            // E_q = E/alpha - (beta/alpha^2) ln(1 + alpha E / beta), mean in double-float
+            const float Eh = a.E_hi[k], El = a.E_lo[k];
+            float qh, ql;
+            df_mul(Eh, El, sdf[0], sdf[1], qh, ql);
+            float Dy = 0.f, y = 0.f;
+            if (beta > 0) {
+                y = Eh * sdf[5];
+                Dy = log1pmx_f(y);
+                if (y < 1.0f) { qh = -sdf[4] * Dy; ql = 0.f; }
+                else df_add(qh, ql, -sdf[4] * log1pf(y), qh, ql);
+            }
+            float muh, mul;
+            df_mul(qh, ql, sdf[2], sdf[3], muh, mul);
+            f[F_MUH] = muh; f[F_MUL] = mul;
+            mu = muh;
+            const float r1 = y / (1.0f + y);
+            // dE_q/dkB = (1/alpha^2) [ s0 (beta/alpha) (2 D + y^2/(1+y)) - s1 (D + y^2/(1+y)) ]
+            deq = beta > 0 ? sdf[7] * (sdf[6] * (2.0f * Dy + y * r1) - (float)a.s1 * (Dy + y * r1)) : (float)NAN;
+        } else {
+            const double E = a.E[k];
+            double Eq = E / alpha;
+            double L = 0, y = 0;
+            if (beta > 0) {
+                y = alpha * E / beta;
+                L = log1p(y);
+                Eq = y < 1.0 ? -(beta / (alpha * alpha)) * (L - y) : E / alpha - (beta / (alpha * alpha)) * L;
+            }
+            mu = LY * Eq;
+            f[F_MUH] = mu;
+            const double D = L - y, r1 = y / (1.0 + y);
+            deq = beta > 0 ? (a.s0 * (beta / alpha) * (2.0 * D + y * r1) - a.s1 * (D + y * r1)) / (alpha * alpha) : NAN;
+        }
+        var = (R)ra + mu * ((R)rb + (R)rc * mu);
+        f[F_DEQ] = deq;
+        R Nk = 1;
+        if constexpr (RES == 0) {
+            const R sig = sqrt(var), isg = R(1) / sig;
+            f[F_A] = isg;
+            if constexpr (sizeof(R) == 4) Nk = isg * (R)INV_SQRT2PI;
+            const R zc = sqrt(R(2) * (R)a.cut);
+            xmin = mu - zc * sig;
+            xmax = mu + zc * sig;
+        } else {
+            const R d = mu * mu / var, s = var / mu;
+            if constexpr (sizeof(R) == 4) {
+                f[F_A] = 1.0f / mu;
+                f[F_B] = d;
+                f[F_C] = -1.0f / s;
+                if (d >= 8.0f) {
+                    // density at the mean: exp(-corr(d)) / (sigma sqrt(2 pi)), corr = Stirling remainder
+                    const float id = 1.0f / d, id2 = id * id;
+                    const float corr = id * (1.0f / 12 - id2 * (1.0f / 360 - id2 * (1.0f / 1260 - id2 * (1.0f / 1680))));
+                    Nk = expf(-corr) * rsqrtf(var) * (float)INV_SQRT2PI;
+                    f[F_KAPPA] = 0.5f * id + id2 * (1.0f / 12 - id2 * (1.0f / 120 - id2 * (1.0f / 252 - id2 * (1.0f / 240))));
+                } else {
+                    const double dd = (double)mu * (double)mu / (double)var, sd = (double)var / (double)mu;
+                    Nk = (float)exp((dd - 1.0) * log((double)mu) - (double)mu / sd - dd * log(sd) - lgamma(dd));
+                    f[F_KAPPA] = (float)(log(dd) - digamma_d(dd));
+                }
+            } else {
+                f[F_A] = -d * log(s) - lgamma(d);
+                f[F_B] = d - 1.0;
+                f[F_C] = 1.0 / s;
+                f[F_KAPPA] = log(s) + digamma_d(d);
+            }
+            // conservative band from bounds on h(t) = (d-1) D(t) - t, x = mu (1 + t)
+            const R c = (R)a.cut;
+            R thi;
+            if (d >= R(1)) {
+                const R bq = R(2) - R(2) * c;
+                thi = (-bq + sqrt(bq * bq + R(8) * c * (d + R(1)))) / (R(2) * (d + R(1)));
+            } else {
+                thi = c / d;
+            }
+            xmax = mu * (R(1) + thi);
+            xmin = 0;
+            if (d > R(1)) {
+                const R tlo = -(R(1) + sqrt(R(1) + R(2) * c * (d - R(1)))) / (d - R(1));
+                xmin = tlo > R(-1) ? mu * (R(1) + tlo) : R(0);
+            }
+            if (a.g_zero[g]) {
+                const R x1 = (R)a.edges[a.g_edge_off[g] + 1];
+                if (xmin <= x1) {
+                    R P, Pd, Ps2;
+                    gamma_bin_zero<R>(d, s, x1, P, Pd, Ps2);
+                    f[F_P0] = P / Nk; f[F_P0D] = Pd / Nk; f[F_P0S] = Ps2 / Nk;
+                }
+            }
+        }
+        f[F_N] = Nk;
+        f[F_XMIN] = xmin;
+        f[F_XMAX] = xmax;
+        for (int dd = 0; dd < a.g_nds[g]; ++dd) {
+            R T = 0;
+            if constexpr (sizeof(R) == 4) {
+                for (int s = 0; s < a.S; ++s) T = fmaf(srate[dd][s], a.Sf[(long long)s * a.K + k], T);
+            } else {
+                for (int s = 0; s < a.S; ++s) T = fma(srate[dd][s], a.Sd[(long long)s * a.K + k], T);
+            }
+            f[F_TN0 + dd] = T * Nk;
+        }
+#pragma unroll
+        for (int i = 0; i < NFP; ++i) rec[i] = f[i];
+    }
+    // band summary of this column block
+    R mn = warp_min<R>(xmin), mx = warp_max<R>(xmax);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sred[0][w] = mn; sred[1][w] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < COLBLK / 32; ++i) { mn = fmin(mn, sred[0][i]); mx = fmax(mx, sred[1][i]); }
+        R* b = reinterpret_cast<R*>(a.blkbuf) + (((long long)t * a.G + g) * a.nblk + blockIdx.x) * 2;
+        b[0] = mn; b[1] = mx;
+    }
+}
+
+// --------------------------------------------------- response evaluators ---
+// Mixed: unnormalised bin value rho_jk = sum_n w_n exp(E_n) of a column record.
+template <int RES, int NG>
+DEV float bin_value_f(const float* c, float xc, const float* del, const float* lam, const float* wt) {
+    const float Dx = (xc - c[F_MUH]) - c[F_MUL];
+    float rho = 0.0f;
+    if constexpr (RES == 0) {
+        const float z = Dx * c[F_A];
+#pragma unroll
+        for (int n = 0; n < NG; ++n) {
+            const float zn = fmaf(del[n], c[F_A], z);
+            rho = fmaf(wt[n], ex2f(-0.5f * L2E * zn * zn), rho);
+        }
+    } else {
+        // log f(x) - log f(mu) = (d-1) D(t) - t = d D(t) - ln(1+t), t = x/mu - 1
+        const float t = Dx * c[F_A];
+        float L1;
+        const float Dt = log1pmx2_f(t, L1);
+        const float B2 = L2E * (c[F_B] - 1.0f), C2 = L2E * c[F_C];
+        const float Ec = fmaf(L2E * c[F_B], Dt, -L2E * L1);
+#pragma unroll
+        for (int n = 0; n < NG; ++n)
+            rho = fmaf(wt[n], ex2f(Ec + fmaf(C2, del[n], B2 * lam[n])), rho);
+    }
+    return rho;
+}
+
+// FP64 gamma: sum_n w_n exp((d-1) ln x_n - x_n/s - d ln s - lgamma(d))
+template <int NG>
+DEV double bin_value_gamma_d(const double* c, const double* x, const double* lx, const double* wt) {
+    double rho = 0.0;
+#pragma unroll
+    for (int n = 0; n < NG; ++n) rho = fma(wt[n], exp(fma(c[F_B], lx[n], fma(-c[F_C], x[n], c[F_A]))), rho);
+    return rho;
+}
+
+// ------------------------------------------------------------- forward -----
+template <class R, int RES, int NG>
+DEV int forward_loop(const KArgs& a, int t, int g, int split, float xlo_w, float xhi_w, bool valid,
+                     bool is_zero, const R* nodes, R xc, double* accd) {
+    int ncol = 0;
+    const int nds = a.g_nds[g];
+    const int kchunk = (a.K + a.nsplit - 1) / a.nsplit;
+    const int k_beg = split * kchunk, k_end = min(a.K, k_beg + kchunk);
+    const R* blk = reinterpret_cast<const R*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
+    R del[NG], lam[NG], wt[NG];
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int n = 0; n < NG; ++n) {
+            del[n] = nodes[n]; lam[n] = nodes[NGM_F + n]; wt[n] = valid ? nodes[2 * NGM_F + n] : R(0);
+        }
+    } else {
+#pragma unroll
+        for (int n = 0; n < NG; ++n) {
+            del[n] = nodes[n]; lam[n] = nodes[NGM_D + n]; wt[n] = valid ? nodes[2 * NGM_D + n] : R(0);
+        }
+    }
+    for (int b = k_beg / COLBLK; b * COLBLK < k_end; ++b) {
+        if (blk[2 * b + 1] < (R)xlo_w || blk[2 * b] > (R)xhi_w) continue;
+        R acc[MAXGDS] = {0, 0, 0};
+        const int kb = max(b * COLBLK, k_beg), ke = min((b + 1) * COLBLK, k_end);
+        for (int k = kb; k < ke; ++k) {
+            const R* c = colrec<R>(a, t, g, k);
+            if (c[F_XMAX] < (R)xlo_w || c[F_XMIN] > (R)xhi_w) continue;
+            ++ncol;
+            R v;
+            if constexpr (sizeof(R) == 4) {
+                v = bin_value_f<RES, NG>(c, xc, del, lam, wt);
+                if (RES == 1 && is_zero) v = valid ? c[F_P0] : 0.0f;
+            } else {
+                v = bin_value_gamma_d<NG>(c, del, lam, wt);
+                if (is_zero) v = valid ? c[F_P0] : 0.0;
+            }
+#pragma unroll
+            for (int dd = 0; dd < MAXGDS; ++dd)
+                if (dd < nds) acc[dd] = fma(v, c[F_TN0 + dd], acc[dd]);
+        }
+#pragma unroll
+        for (int dd = 0; dd < MAXGDS; ++dd) accd[dd] += (double)acc[dd];
+    }
+    return ncol;
+}
+
+// statistics: (bin, column) pairs evaluated by a warp
+DEV void count_work(const KArgs& a, int kind, bool lane_valid, long long n_other) {
+    if (!a.work) return;
+    const unsigned m = __ballot_sync(0xffffffffu, lane_valid);
+    if ((threadIdx.x & 31) == 0 && n_other > 0)
+        atomicAdd(&a.work[kind], (unsigned long long)n_other * (unsigned long long)__popc(m));
+}
+
+// lanes <-> bins (32 per warp), loop over the columns of the band
+template <class R, int RES>
+__global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(KArgs a) {
+    const int tile = blockIdx.x, split = blockIdx.y;
+    const int t = blockIdx.z / a.G, g = blockIdx.z % a.G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int wlo, whi;
+    toy_window_union(a, t, g, wlo, whi);
+    const int j0 = (tile * FWD_WARPS + warp) * 32;
+    if (j0 >= whi || j0 + 32 <= wlo) return;
+    const int j = j0 + lane;
+    const bool valid = j >= wlo && j < whi;
+    const int jr = min(max(j, wlo), whi - 1);
+    const int nb = a.g_node_off[g] + jr;
+    const int jf = max(j0, wlo), jl = min(j0 + 31, whi - 1);
+    const float xlo_w = (float)a.edges[a.g_edge_off[g] + jf];
+    const float xhi_w = (float)a.edges[a.g_edge_off[g] + jl + 1];
+    const unsigned char cls = a.bclass[nb];
+    const bool low = __any_sync(0xffffffffu, cls != BIN_LIN);
+    double accd[MAXGDS] = {0.0, 0.0, 0.0};
+    int ncol;
+    if constexpr (sizeof(R) == 4) {
+        const float* nodes = a.ntab_f + (long long)nb * 3 * NGM_F;
+        const float xc = a.xc_f[nb];
+        if (low) ncol = forward_loop<float, RES, NG_LOG_F>(a, t, g, split, xlo_w, xhi_w, valid, cls == BIN_ZERO, nodes, xc, accd);
+        else     ncol = forward_loop<float, RES, NG_LIN_F>(a, t, g, split, xlo_w, xhi_w, valid, false, nodes, xc, accd);
+    } else {
+        const double* nodes = a.ntab_d + (long long)nb * 3 * NGM_D;
+        if (low) ncol = forward_loop<double, RES, NG_LOG_D>(a, t, g, split, xlo_w, xhi_w, valid, cls == BIN_ZERO, nodes, 0.0, accd);
+        else     ncol = forward_loop<double, RES, NG_LIN_D>(a, t, g, split, xlo_w, xhi_w, valid, false, nodes, 0.0, accd);
+    }
+    count_work(a, K_FORWARD, valid, ncol);
+    if (valid) {
+        double* out = a.mubuf + ((long long)t * a.nsplit + split) * a.total_bins;
+        for (int dd = 0; dd < a.g_nds[g]; ++dd) out[a.ds_off[a.g_ds[g][dd]] + j] = accd[dd];
+    }
+}
+
+// FP64 Gaussian: exact bin integrals from erfc at the edges.  Lanes <-> edges,
+// 31 bins per warp; the upper edge of a bin comes from the next lane.
+__global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_gauss64(KArgs a) {
+    const int tile = blockIdx.x, split = blockIdx.y;
+    const int t = blockIdx.z / a.G, g = blockIdx.z % a.G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int wlo, whi;
+    toy_window_union(a, t, g, wlo, whi);
+    const int j0 = (tile * FWD_WARPS + warp) * 31;
+    if (j0 >= whi || j0 + 31 <= wlo) return;
+    const int J = a.g_bins[g];
+    const int j = j0 + lane;
+    const bool valid = lane < 31 && j >= wlo && j < whi;
+    const double xe = a.edges[a.g_edge_off[g] + min(j, J)];
+    const int jf = max(j0, wlo), jl = min(j0 + 30, whi - 1);
+    const double xlo_w = a.edges[a.g_edge_off[g] + jf], xhi_w = a.edges[a.g_edge_off[g] + jl + 1];
+    const int nds = a.g_nds[g];
+    const int kchunk = (a.K + a.nsplit - 1) / a.nsplit;
+    const int k_beg = split * kchunk, k_end = min(a.K, k_beg + kchunk);
+    const double* blk = reinterpret_cast<const double*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
+    double acc[MAXGDS] = {0.0, 0.0, 0.0};
+    int ncol = 0;
+    for (int b = k_beg / COLBLK; b * COLBLK < k_end; ++b) {
+        if (blk[2 * b + 1] < xlo_w || blk[2 * b] > xhi_w) continue;
+        const int kb = max(b * COLBLK, k_beg), ke = min((b + 1) * COLBLK, k_end);
+        for (int k = kb; k < ke; ++k) {
+            const double* c = colrec<double>(a, t, g, k);
+            if (c[F_XMAX] < xlo_w || c[F_XMIN] > xhi_w) continue;
+            ++ncol;
+            const double z = (xe - c[F_MUH]) * c[F_A];
+            const bool up = z >= 0.0;
+            const double q = 0.5 * erfc(fabs(z) * INV_SQRT2);
+            const double q1 = __shfl_down_sync(0xffffffffu, q, 1);
+            const bool up1 = __shfl_down_sync(0xffffffffu, (int)up, 1) != 0;
+            double v = (up == up1) ? (up ? q - q1 : q1 - q) : 1.0 - q - q1;
+            if (!valid) v = 0.0;
+#pragma unroll
+            for (int dd = 0; dd < MAXGDS; ++dd)
+                if (dd < nds) acc[dd] = fma(v, c[F_TN0 + dd], acc[dd]);
+        }
+    }
+    count_work(a, K_FORWARD, valid, ncol);
+    if (valid) {
+        double* out = a.mubuf + ((long long)t * a.nsplit + split) * a.total_bins;
+        for (int dd = 0; dd < nds; ++dd) out[a.ds_off[a.g_ds[g][dd]] + j] = acc[dd];
+    }
+}
+
+// ------------------------------------------------------------ deviance -----
+template <class R>
+__global__ void __launch_bounds__(256) k_deviance(KArgs a) {
+    const int t = blockIdx.x;
+    __shared__ double sh[32];
+    const double* prm = a.params + (long long)t * a.params_stride;
+    const double* cnt = a.counts + (long long)t * a.counts_stride;
+    R* wout = reinterpret_cast<R*>(a.wbuf) + (long long)t * a.total_bins;
+    double* gdir = a.gdirect + (long long)t * a.P;
+    for (int p = threadIdx.x; p < a.P; p += blockDim.x) gdir[p] = 0.0;
+    double part = 0.0;
+    int bad_mu = 0, bad_fin = 0;
+    for (int d = 0; d < a.D; ++d) {
+        const int J = a.ds_bins[d], off = a.ds_off[d];
+        int lo = a.win[t * a.win_stride + 2 * d], hi = a.win[t * a.win_stride + 2 * d + 1];
+        lo = max(lo, 0); hi = min(hi, J);
+        const double eps = a.ds_eps[d];
+        const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
+        for (int j = threadIdx.x; j < J; j += blockDim.x) {
+            double w = 0.0;
+            if (j >= lo && j < hi) {
+                double mu = 0.0;
+                for (int s = 0; s < a.nsplit; ++s) mu += a.mubuf[((long long)t * a.nsplit + s) * a.total_bins + off + j];
+                for (int s = 0; s < a.S; ++s) {
+                    if (a.sp_kind[s] != 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
+                    const int pr = a.slot_map[d * a.NSLOT + s];
+                    const double r = pr >= 0 ? prm[pr] : 0.0;
+                    const double m = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
+                    const double wd = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
+                    mu += eps * r * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
+                }
+                const double n = cnt[off + j];
+                double term;
+                if (n > 0.0) {
+                    if (!(mu > 0.0)) { bad_mu = 1; term = INFINITY; }
+                    else term = mu - n + n * log(n / mu);
+                } else {
+                    term = mu;
+                }
+                if (!isfinite(mu)) bad_fin = 1;
+                part += term;
+                w = mu > 0.0 ? 1.0 - n / mu : 0.0;
+            }
+            wout[off + j] = (R)w;
+        }
+    }
+    double nll = block_sum_d(part, sh);
+    const int any_bad_mu = __syncthreads_or(bad_mu), any_bad_fin = __syncthreads_or(bad_fin);
+    // AnaPeak gradient terms: rate, position, width (closed form per bin)
+    if (a.want_grad) {
+        __syncthreads();  // wout visible to the block
+        for (int d = 0; d < a.D; ++d) {
+            const int J = a.ds_bins[d], off = a.ds_off[d];
+            const double eps = a.ds_eps[d];
+            const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
+            for (int s = 0; s < a.S; ++s) {
+                if (a.sp_kind[s] != 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
+                const int pr = a.slot_map[d * a.NSLOT + s];
+                const int pm = a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s];
+                const int pw = a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s];
+                const double r = pr >= 0 ? prm[pr] : 0.0, m = prm[pm], wd = prm[pw];
+                double gr = 0.0, gm = 0.0, gw = 0.0;
+                for (int j = threadIdx.x; j < J; j += blockDim.x) {
+                    const double wj = (double)wout[off + j];
+                    if (wj == 0.0) continue;
+                    const double z0 = (ed[j] - m) / wd, z1 = (ed[j + 1] - m) / wd;
+                    const double p0 = exp(-0.5 * z0 * z0) * INV_SQRT2PI, p1 = exp(-0.5 * z1 * z1) * INV_SQRT2PI;
+                    gr += wj * ncdf_diff(z0, z1);
+                    gm += wj * (-(p1 - p0) / wd);
+                    gw += wj * (-(z1 * p1 - z0 * p0) / wd);
+                }
+                gr = block_sum_d(gr, sh);
+                gm = block_sum_d(gm, sh);
+                gw = block_sum_d(gw, sh);
+                if (threadIdx.x == 0) {
+                    if (pr >= 0) gdir[pr] += eps * gr;
+                    gdir[pm] += eps * r * gm;
+                    gdir[pw] += eps * r * gw;
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < a.n_pulls; ++i) {
+            const int p = a.pull_param[i];
+            const double z = (prm[p] - a.pull_c[i]) / a.pull_w[i];
+            nll += 0.5 * z * z;
+            if (a.want_grad) gdir[p] += z / a.pull_w[i];
+        }
+        int st = 0;
+        if (any_bad_mu) { st = -3; nll = INFINITY; }
+        else if (any_bad_fin || !isfinite(nll)) st = -4;
+        a.nll[t] = nll;
+        if (a.status) a.status[t] = st;
+    }
+}
+
+// ------------------------------------------------------------ backward -----
+// lanes <-> columns; each warp sweeps the bins of its columns' band.
+template <class R, int RES>
+__global__ void __launch_bounds__(256) k_backward(KArgs a) {
+    const int task = blockIdx.x, g = blockIdx.y, t = blockIdx.z;
+    const int W = a.bw_warps;
+    const int cbw = task / a.bw_bsplit, bsp = task % a.bw_bsplit;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kbase = cbw * W * 32;
+    const int k = kbase + warp * 32 + lane;
+    const bool kval = k < a.K;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* su = reinterpret_cast<R*>(smem_raw);                        // [MAXGDS][W*32]
+    double* sresp = reinterpret_cast<double*>(smem_raw + sizeof(R) * MAXGDS * W * 32 + 16);  // [W][NRESP]
+    const int nds = a.g_nds[g];
+    const int J = a.g_bins[g];
+    const double* ed = a.edges + a.g_edge_off[g];
+    const double* prm = a.params + (long long)t * a.params_stride;
+    const double LY = prm[a.g_resp[g][0]], rb = prm[a.g_resp[g][3]], rc = prm[a.g_resp[g][4]];
+    int wlo, whi;
+    toy_window_union(a, t, g, wlo, whi);
+
+    R c[NFP];
+    {
+        const R* cr = colrec<R>(a, t, g, kval ? k : a.K - 1);
+#pragma unroll
+        for (int i = 0; i < NFP; ++i) c[i] = cr[i];
+    }
+    const R xmn = warp_min<R>(kval ? c[F_XMIN] : (R)INFINITY);
+    const R xmx = warp_max<R>(kval ? c[F_XMAX] : (R)-INFINITY);
+    int ja = 0, jb = -1;
+    if (xmx >= xmn) {
+        // first bin whose upper edge exceeds xmn, last bin whose lower edge is below xmx
+        int lo = 0, hi = J;
+        while (lo < hi) { const int m = (lo + hi) >> 1; if (ed[m + 1] <= (double)xmn) lo = m + 1; else hi = m; }
+        ja = lo;
+        lo = 0; hi = J;
+        while (lo < hi) { const int m = (lo + hi) >> 1; if (ed[m] < (double)xmx) lo = m + 1; else hi = m; }
+        jb = lo - 1;
+        ja = max(ja, wlo); jb = min(jb, whi - 1);
+        const int len = jb - ja + 1;
+        if (len > 0) {
+            const int ch = (len + a.bw_bsplit - 1) / a.bw_bsplit;
+            const int na = ja + bsp * ch;
+            jb = min(jb, na + ch - 1);
+            ja = na;
+        }
+    }
+    const R* wv[MAXGDS];
+    for (int dd = 0; dd < MAXGDS; ++dd)
+        wv[dd] = reinterpret_cast<const R*>(a.wbuf) + (long long)t * a.total_bins + a.ds_off[a.g_ds[g][dd < nds ? dd : 0]];
+    R U0[MAXGDS] = {0, 0, 0};
+    R U1 = 0, U2 = 0;
+    const int nbase = a.g_node_off[g];
+    if constexpr (sizeof(R) == 8 && RES == 0) {
+        // exact Gaussian bin integrals from the edges, derivatives from the edge densities
+        const double mu = c[F_MUH], isg = c[F_A];
+        double zp = 0, qp = 0, pp = 0;
+        bool upp = false;
+        for (int e = ja; e <= jb + 1; ++e) {
+            const double z = (ed[e] - mu) * isg;
+            const bool up = z >= 0.0;
+            const double q = 0.5 * erfc(fabs(z) * INV_SQRT2);
+            const double ph = exp(-0.5 * z * z) * INV_SQRT2PI;
+            if (e > ja) {
+                const int j = e - 1;
+                const double Rv = (up == upp) ? (upp ? qp - q : q - qp) : 1.0 - qp - q;
+                double Wj = 0.0;
+#pragma unroll
+                for (int dd = 0; dd < MAXGDS; ++dd)
+                    if (dd < nds) { const double w = wv[dd][j]; U0[dd] = fma(w, Rv, U0[dd]); Wj = fma(w, c[F_TN0 + dd], Wj); }
+                // d R / d mu = U1 / sigma, d R / d sigma = U2 / sigma (applied per column below)
+                U1 = fma(Wj, -(ph - pp), U1);
+                U2 = fma(Wj, -(z * ph - zp * pp), U2);
+            }
+            zp = z; qp = q; pp = ph; upp = up;
+        }
+    } else {
+        for (int j = ja; j <= jb; ++j) {
+            R wj[MAXGDS];
+            R Wj = 0;
+#pragma unroll
+            for (int dd = 0; dd < MAXGDS; ++dd) {
+                wj[dd] = dd < nds ? wv[dd][j] : R(0);
+                Wj = fma(wj[dd], c[F_TN0 + dd], Wj);
+            }
+            const unsigned char cls = a.bclass[nbase + j];
+            R rho = 0;
+            if (RES == 1 && cls == BIN_ZERO) {
+                rho = c[F_P0];
+                U1 = fma(Wj, c[F_P0D], U1);
+                U2 = fma(Wj, c[F_P0S], U2);
+            } else if constexpr (sizeof(R) == 4) {
+                const float* nd = a.ntab_f + (long long)(nbase + j) * 3 * NGM_F;
+                const float Dx = (a.xc_f[nbase + j] - c[F_MUH]) - c[F_MUL];
+                const int NG = cls == BIN_LOG ? NG_LOG_F : NG_LIN_F;
+                if constexpr (RES == 0) {
+                    const float z = Dx * c[F_A];
+                    float Z1 = 0.f, Z2 = 0.f;
+                    for (int n = 0; n < NG; ++n) {
+                        const float zn = fmaf(nd[n], c[F_A], z);
+                        const float fw = nd[2 * NGM_F + n] * ex2f(-0.5f * L2E * zn * zn);
+                        rho += fw; Z1 = fmaf(fw, zn, Z1); Z2 = fmaf(fw, fmaf(zn, zn, -1.0f), Z2);
+                    }
+                    U1 = fmaf(Wj, Z1, U1);
+                    U2 = fmaf(Wj, Z2, U2);
+                } else {
+                    const float tt = Dx * c[F_A];
+                    float L1;
+                    const float Dt = log1pmx2_f(tt, L1);
+                    const float B2 = L2E * (c[F_B] - 1.0f), C2 = L2E * c[F_C];
+                    const float Ec = fmaf(L2E * c[F_B], Dt, -L2E * L1);
+                    float L = 0.f, X = 0.f;
+                    for (int n = 0; n < NG; ++n) {
+                        const float fw = nd[2 * NGM_F + n] * ex2f(Ec + fmaf(C2, nd[n], B2 * nd[NGM_F + n]));
+                        rho += fw; L = fmaf(fw, nd[NGM_F + n], L); X = fmaf(fw, nd[n], X);
+                    }
+                    const float tau = L1 + c[F_KAPPA];
+                    U1 = fmaf(Wj, fmaf(tau, rho, L), U1);
+                    U2 = fmaf(Wj, fmaf(Dx, rho, X), U2);
+                }
+            } else {
+                // FP64 gamma: f = exp((d-1) ln x - x/s + A); df/dd = f (ln x - ln s - psi(d)); df/ds = f (x - mu)/s^2
+                const double* nd = a.ntab_d + (long long)(nbase + j) * 3 * NGM_D;
+                const int NG = cls == BIN_LOG ? NG_LOG_D : NG_LIN_D;
+                double L = 0.0, X = 0.0;
+                for (int n = 0; n < NG; ++n) {
+                    const double fw = nd[2 * NGM_D + n] * exp(fma(c[F_B], nd[NGM_D + n], fma(-c[F_C], nd[n], c[F_A])));
+                    rho += fw; L = fma(fw, nd[NGM_D + n] - c[F_KAPPA], L); X = fma(fw, nd[n] - c[F_MUH], X);
+                }
+                U1 = fma(Wj, L, U1);
+                U2 = fma(Wj, X, U2);
+            }
+#pragma unroll
+            for (int dd = 0; dd < MAXGDS; ++dd) U0[dd] = fma(wj[dd], rho, U0[dd]);
+        }
+    }
+    count_work(a, K_BACKWARD, kval, (long long)(jb - ja + 1));
+    // chain rule per column
+    R r[NRESP] = {0, 0, 0, 0, 0};
+    if (kval) {
+        const R mu = sizeof(R) == 4 ? c[F_MUH] + c[F_MUL] : c[F_MUH];
+        R g_mu, g_var;
+        if constexpr (RES == 0) {
+            g_mu = U1 * c[F_A];
+            g_var = R(0.5) * U2 * c[F_A] * c[F_A];
+        } else {
+            // mixed: B = d, C = -1/s; fp64: C = 1/s, d = mu / s
+            const R d = sizeof(R) == 4 ? c[F_B] : mu * c[F_C];
+            const R s = sizeof(R) == 4 ? R(-1) / c[F_C] : R(1) / c[F_C];
+            const R var = d * s * s;
+            const R gd = U1, gs = U2 * c[F_C] * c[F_C];
+            g_mu = gd * (R(2) * d / mu) - gs * (s / mu);
+            g_var = -gd * (d / var) + gs / mu;
+        }
+        const R g_mt = g_mu + g_var * ((R)rb + R(2) * (R)rc * mu);
+        r[0] = g_mt * (mu / (R)LY);
+        r[1] = g_mt * (R)LY * c[F_DEQ];
+        r[2] = g_var;
+        r[3] = g_var * mu;
+        r[4] = g_var * mu * mu;
+    }
+#pragma unroll
+    for (int i = 0; i < NRESP; ++i) {
+        const R v = warp_sum<R>(r[i]);
+        if (lane == 0) sresp[warp * NRESP + i] = (double)v;
+    }
+    for (int dd = 0; dd < MAXGDS; ++dd) su[dd * W * 32 + warp * 32 + lane] = kval ? U0[dd] * c[F_N] : R(0);
+    __syncthreads();
+    double* part = a.partbuf + (((long long)t * a.G + g) * a.nbtask + task) * a.NPART;
+    if (threadIdx.x < NRESP) {
+        double s = 0.0;
+        for (int w = 0; w < W; ++w) s += sresp[w * NRESP + threadIdx.x];
+        part[threadIdx.x] = s;
+    }
+    const int ncol = min(W * 32, a.K - kbase);
+    for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
+        const int dd = i / a.S, s = i % a.S;
+        double v = 0.0;
+        if (dd < nds && a.sp_kind[s] != 2 && ((a.sp_mask[s] >> a.g_ds[g][dd]) & 1u)) {
+            R acc = 0;
+            if constexpr (sizeof(R) == 4) {
+                const float* Srow = a.Sf + (long long)s * a.K + kbase;
+                for (int cc = 0; cc < ncol; ++cc) acc = fmaf(Srow[cc], su[dd * W * 32 + cc], acc);
+            } else {
+                const double* Srow = a.Sd + (long long)s * a.K + kbase;
+                for (int cc = 0; cc < ncol; ++cc) acc = fma(Srow[cc], su[dd * W * 32 + cc], acc);
+            }
+            v = (double)acc;
+        }
+        part[NRESP + i] = v;
+    }
+}
+
+// ------------------------------------------------------------ gradfinal ----
+__global__ void __launch_bounds__(128) k_gradfinal(KArgs a) {
+    const int t = blockIdx.x;
+    extern __shared__ double vals[];  // [G][NPART]
+    for (int i = threadIdx.x; i < a.G * a.NPART; i += blockDim.x) {
+        const int g = i / a.NPART, v = i % a.NPART;
+        const double* p = a.partbuf + ((long long)t * a.G + g) * a.nbtask * a.NPART + v;
+        double s = 0.0;
+        for (int task = 0; task < a.nbtask; ++task) s += p[(long long)task * a.NPART];
+        vals[i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double* gr = a.grad + (long long)t * a.P;
+        const double* gd = a.gdirect + (long long)t * a.P;
+        for (int p = 0; p < a.P; ++p) gr[p] = gd[p];
+        for (int g = 0; g < a.G; ++g) {
+            const double* v = vals + g * a.NPART;
+            for (int i = 0; i < NRESP; ++i) gr[a.g_resp[g][i]] += v[i];
+            for (int dd = 0; dd < a.g_nds[g]; ++dd) {
+                const int d = a.g_ds[g][dd];
+                for (int s = 0; s < a.S; ++s) {
+                    if (a.sp_kind[s] == 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
+                    const int p = a.slot_map[d * a.NSLOT + s];
+                    if (p >= 0) gr[p] += a.ds_eps[d] * v[NRESP + dd * a.S + s];
+                }
+            }
+        }
+        bool fin = true;
+        for (int p = 0; p < a.P; ++p) fin = fin && isfinite(gr[p]);
+        if (!fin && a.status && a.status[t] == 0) a.status[t] = -4;
+    }
+}
+
+// ---------------------------------------------------- per-species path -----
+// M[g][s][j] = sum_k R_jk S'_sk for species s in [sp_first, sp_first + sp_count)
+template <class R, int RES, int NG>
+DEV void species_loop(const KArgs& a, int g, float xlo_w, float xhi_w, bool valid, bool is_zero,
+                      const R* nodes, R xc, double* accd, int nsp) {
+    R del[NG], lam[NG], wt[NG];
+    constexpr int NGM = sizeof(R) == 4 ? NGM_F : NGM_D;
+#pragma unroll
+    for (int n = 0; n < NG; ++n) { del[n] = nodes[n]; lam[n] = nodes[NGM + n]; wt[n] = valid ? nodes[2 * NGM + n] : R(0); }
+    const R* blk = reinterpret_cast<const R*>(a.blkbuf) + (long long)g * a.nblk * 2;
+    for (int b = 0; b < a.nblk; ++b) {
+        if (blk[2 * b + 1] < (R)xlo_w || blk[2 * b] > (R)xhi_w) continue;
+        R acc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] = 0;
+        const int kb = b * COLBLK, ke = min(a.K, kb + COLBLK);
+        for (int k = kb; k < ke; ++k) {
+            const R* c = colrec<R>(a, 0, g, k);
+            if (c[F_XMAX] < (R)xlo_w || c[F_XMIN] > (R)xhi_w) continue;
+            R v;
+            if constexpr (sizeof(R) == 4) {
+                v = bin_value_f<RES, NG>(c, xc, del, lam, wt);
+                if (RES == 1 && is_zero) v = valid ? c[F_P0] : 0.0f;
+            } else {
+                v = bin_value_gamma_d<NG>(c, del, lam, wt);
+                if (is_zero) v = valid ? c[F_P0] : 0.0;
+            }
+            v *= c[F_N];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (i < nsp) {
+                    const R sv = sizeof(R) == 4 ? (R)a.Sf[(long long)(a.sp_first + i) * a.K + k]
+                                                : (R)a.Sd[(long long)(a.sp_first + i) * a.K + k];
+                    acc[i] = fma(v, sv, acc[i]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) accd[i] += (double)acc[i];
+    }
+}
+
+template <class R, int RES>
+__global__ void __launch_bounds__(FWD_WARPS * 32) k_species(KArgs a) {
+    const int tile = blockIdx.x, g = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int J = a.g_bins[g];
+    const int j0 = (tile * FWD_WARPS + warp) * 32;
+    if (j0 >= J) return;
+    const int j = j0 + lane;
+    const bool valid = j < J;
+    const int jr = min(j, J - 1);
+    const int nb = a.g_node_off[g] + jr;
+    const int jl = min(j0 + 31, J - 1);
+    const float xlo_w = (float)a.edges[a.g_edge_off[g] + j0];
+    const float xhi_w = (float)a.edges[a.g_edge_off[g] + jl + 1];
+    const unsigned char cls = a.bclass[nb];
+    const bool low = __any_sync(0xffffffffu, cls != BIN_LIN);
+    const int nsp = min(16, a.sp_count - blockIdx.z * 16);
+    KArgs b = a;
+    b.sp_first = a.sp_first + blockIdx.z * 16;
+    double accd[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) accd[i] = 0.0;
+    if constexpr (sizeof(R) == 4) {
+        const float* nodes = a.ntab_f + (long long)nb * 3 * NGM_F;
+        const float xc = a.xc_f[nb];
+        if (low) species_loop<float, RES, NG_LOG_F>(b, g, xlo_w, xhi_w, valid, cls == BIN_ZERO, nodes, xc, accd, nsp);
+        else     species_loop<float, RES, NG_LIN_F>(b, g, xlo_w, xhi_w, valid, false, nodes, xc, accd, nsp);
+    } else {
+        const double* nodes = a.ntab_d + (long long)nb * 3 * NGM_D;
+        if (low) species_loop<double, RES, NG_LOG_D>(b, g, xlo_w, xhi_w, valid, cls == BIN_ZERO, nodes, 0.0, accd, nsp);
+        else     species_loop<double, RES, NG_LIN_D>(b, g, xlo_w, xhi_w, valid, false, nodes, 0.0, accd, nsp);
+    }
+    if (valid)
+        for (int i = 0; i < nsp; ++i) a.Mbuf[((long long)g * a.S + b.sp_first + i) * a.Jmax + j] = accd[i];
+}
+
+// FP64 Gaussian per-species path: exact erfc bin integrals (lanes <-> edges, 31 bins per warp)
+__global__ void __launch_bounds__(FWD_WARPS * 32) k_species_gauss64(KArgs a) {
+    const int tile = blockIdx.x, g = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int J = a.g_bins[g];
+    const int j0 = (tile * FWD_WARPS + warp) * 31;
+    if (j0 >= J) return;
+    const int j = j0 + lane;
+    const bool valid = lane < 31 && j < J;
+    const double xe = a.edges[a.g_edge_off[g] + min(j, J)];
+    const int jl = min(j0 + 30, J - 1);
+    const double xlo_w = a.edges[a.g_edge_off[g] + j0], xhi_w = a.edges[a.g_edge_off[g] + jl + 1];
+    const int sp0 = a.sp_first + blockIdx.z * 16;
+    const int nsp = min(16, a.sp_count - blockIdx.z * 16);
+    const double* blk = reinterpret_cast<const double*>(a.blkbuf) + (long long)g * a.nblk * 2;
+    double acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+    for (int b = 0; b < a.nblk; ++b) {
+        if (blk[2 * b + 1] < xlo_w || blk[2 * b] > xhi_w) continue;
+        const int kb = b * COLBLK, ke = min(a.K, kb + COLBLK);
+        for (int k = kb; k < ke; ++k) {
+            const double* c = colrec<double>(a, 0, g, k);
+            if (c[F_XMAX] < xlo_w || c[F_XMIN] > xhi_w) continue;
+            const double z = (xe - c[F_MUH]) * c[F_A];
+            const bool up = z >= 0.0;
+            const double q = 0.5 * erfc(fabs(z) * INV_SQRT2);
+            const double q1 = __shfl_down_sync(0xffffffffu, q, 1);
+            const bool up1 = __shfl_down_sync(0xffffffffu, (int)up, 1) != 0;
+            double v = (up == up1) ? (up ? q - q1 : q1 - q) : 1.0 - q - q1;
+            if (!valid) v = 0.0;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (i < nsp) acc[i] = fma(v, a.Sd[(long long)(sp0 + i) * a.K + k], acc[i]);
+        }
+    }
+    if (valid)
+        for (int i = 0; i < nsp; ++i) a.Mbuf[((long long)g * a.S + sp0 + i) * a.Jmax + j] = acc[i];
+}
+
+// mu_dj = eps_d sum_s mask r_s M[g][s][j] (smeared species; peaks are added by k_deviance)
+__global__ void k_mu_from_species(KArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.total_bins) return;
+    int d = 0;
+    while (d + 1 < a.D && i >= a.ds_off[d + 1]) ++d;
+    const int j = i - a.ds_off[d];
+    const int g = a.ds_group[d];
+    const double* prm = a.params;
+    double mu = 0.0;
+    for (int s = 0; s < a.S; ++s) {
+        if (a.sp_kind[s] == 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
+        const int p = a.slot_map[d * a.NSLOT + s];
+        if (p < 0) continue;
+        mu = fma(prm[p], a.Mbuf[((long long)g * a.S + s) * a.Jmax + j], mu);
+    }
+    a.mubuf[i] = a.ds_eps[d] * mu;
+}
+
+// expected counts per bin and species of one dataset
+__global__ void k_expected_out(KArgs a) {
+    const int d = a.out_dataset;
+    const int J = a.ds_bins[d];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= J * a.S) return;
+    const int j = i / a.S, s = i % a.S;
+    const int g = a.ds_group[d];
+    const double* prm = a.params;
+    double v = 0.0;
+    if ((a.sp_mask[s] >> d) & 1u) {
+        const int pr = a.slot_map[d * a.NSLOT + s];
+        const double r = pr >= 0 ? prm[pr] : 0.0;
+        if (a.sp_kind[s] == 2) {
+            const double* ed = a.edges + a.g_edge_off[g];
+            const double m = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
+            const double wd = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
+            v = a.ds_eps[d] * r * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
+        } else {
+            v = a.ds_eps[d] * r * a.Mbuf[((long long)g * a.S + s) * a.Jmax + j];
+        }
+    }
+    a.out_species[i] = v;
+}
+
+
+// ------------------------------------------------------------- probes ------
+// Synthetic throughput loops: 8 independent chains per thread, every SM busy.
+constexpr int PROBE_ITERS = 2048;
+template <int WHICH>
+__global__ void __launch_bounds__(256) k_probe(float* sink, double* sinkd, float seed) {
+    float x[8];
+    double y[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { x[i] = seed * (0.1f + 0.01f * i) + 1e-3f * threadIdx.x; y[i] = (double)x[i]; }
+    const float b = 0.999f, c = 1e-4f;
+    for (int it = 0; it < PROBE_ITERS; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if constexpr (WHICH == 0) x[i] = fmaf(x[i], b, c);
+            if constexpr (WHICH == 1) x[i] = ex2f(-x[i]);
+            if constexpr (WHICH == 2) y[i] = fma(y[i], 0.999, 1e-4);
+            if constexpr (WHICH == 3) x[i] = fmaf(0.7f, ex2f(fmaf(-0.5f, x[i], fmaf(0.25f, x[i], -0.3f))), x[i] * 0.5f);
+        }
+    }
+    float s = 0.f; double sd = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { s += x[i]; sd += y[i]; }
+    if (s == 12345.678f) sink[threadIdx.x] = s;
+    if (sd == 12345.678) sinkd[threadIdx.x] = sd;
+}
+
+cudaError_t run_probe(int which, int nsm, double* ops) {
+    float* sink = nullptr;
+    double* sinkd = nullptr;
+    cudaStream_t st;
+    cudaEvent_t e0, e1;
+    cudaError_t err;
+    if ((err = cudaMalloc(&sink, 256 * sizeof(float)))) return err;
+    if ((err = cudaMalloc(&sinkd, 256 * sizeof(double)))) { cudaFree(sink); return err; }
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    const int blocks = nsm * 8;
+    auto launch = [&](void) {
+        switch (which) {
+            case 0: k_probe<0><<<blocks, 256, 0, st>>>(sink, sinkd, 0.5f); break;
+            case 1: k_probe<1><<<blocks, 256, 0, st>>>(sink, sinkd, 0.5f); break;
+            case 2: k_probe<2><<<blocks, 256, 0, st>>>(sink, sinkd, 0.5f); break;
+            default: k_probe<3><<<blocks, 256, 0, st>>>(sink, sinkd, 0.5f); break;
+        }
+    };
+    launch();  // warm-up
+    float best = 1e30f;
+    for (int rep = 0; rep < 5; ++rep) {
+        cudaEventRecord(e0, st);
+        launch();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = fminf(best, ms);
+    }
+    err = cudaGetLastError();
+    *ops = (double)blocks * 256.0 * 8.0 * PROBE_ITERS / (best * 1e-3);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(sink); cudaFree(sinkd);
+    return err;
+}
+
+// ------------------------------------------------------------ launchers ----
+cudaError_t launch_columns(const KArgs& a, cudaStream_t st) {
+    dim3 grid(a.nblk, a.G, a.T);
+    if (a.precision == 1) {
+        if (a.res == 0) k_columns<float, 0><<<grid, COLBLK, 0, st>>>(a);
+        else            k_columns<float, 1><<<grid, COLBLK, 0, st>>>(a);
+    } else {
+        if (a.res == 0) k_columns<double, 0><<<grid, COLBLK, 0, st>>>(a);
+        else            k_columns<double, 1><<<grid, COLBLK, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const KArgs& a, cudaStream_t st) {
+    dim3 grid(a.ntile, a.nsplit, a.T * a.G);
+    if (a.precision == 1) {
+        if (a.res == 0) k_forward<float, 0><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else            k_forward<float, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    } else {
+        if (a.res == 0) k_forward_gauss64<<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else            k_forward<double, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deviance(const KArgs& a, cudaStream_t st) {
+    if (a.precision == 1) k_deviance<float><<<a.T, 256, 0, st>>>(a);
+    else                  k_deviance<double><<<a.T, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const KArgs& a, cudaStream_t st) {
+    dim3 grid(a.nbtask, a.G, a.T);
+    const int threads = a.bw_warps * 32;
+    if (a.precision == 1) {
+        const size_t sm = sizeof(float) * MAXGDS * threads + 16 + sizeof(double) * a.bw_warps * NRESP;
+        if (a.res == 0) k_backward<float, 0><<<grid, threads, sm, st>>>(a);
+        else            k_backward<float, 1><<<grid, threads, sm, st>>>(a);
+    } else {
+        const size_t sm = sizeof(double) * MAXGDS * threads + 16 + sizeof(double) * a.bw_warps * NRESP;
+        if (a.res == 0) k_backward<double, 0><<<grid, threads, sm, st>>>(a);
+        else            k_backward<double, 1><<<grid, threads, sm, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradfinal(const KArgs& a, cudaStream_t st) {
+    k_gradfinal<<<a.T, 128, sizeof(double) * a.G * a.NPART, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_species(const KArgs& a, cudaStream_t st) {
+    const int nchunk = (a.sp_count + 15) / 16;
+    if (a.precision == 0 && a.res == 0) {
+        dim3 grid((a.Jmax + FWD_WARPS * 31 - 1) / (FWD_WARPS * 31), a.G, nchunk);
+        k_species_gauss64<<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    dim3 grid((a.Jmax + FWD_WARPS * 32 - 1) / (FWD_WARPS * 32), a.G, nchunk);
+    if (a.precision == 1) {
+        if (a.res == 0) k_species<float, 0><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else            k_species<float, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    } else {
+        k_species<double, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu_from_species(const KArgs& a, cudaStream_t st) {
+    k_mu_from_species<<<(a.total_bins + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expected_out(const KArgs& a, cudaStream_t st) {
+    const int n = a.ds_bins[a.out_dataset] * a.S;
+    k_expected_out<<<(n + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gsn

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libgsn (include/gsn.h): argument marshalling only.
+
+Every step of the likelihood runs in the CUDA kernels of libgsn.so; this module
+only converts numpy arrays / torch tensors into the pointers and sizes of the C
+ABI.  There is no fallback: if the library was not built, load_library()
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsn.so")
+
+GSN_OK = 0
+GSN_ERR_ARG, GSN_ERR_CUDA, GSN_ERR_NONPOSITIVE_MU, GSN_ERR_NONFINITE, GSN_ERR_STATE, GSN_ERR_NOMEM = -1, -2, -3, -4, -5, -6
+GSN_FP64, GSN_MIXED = 0, 1
+GSN_RES_GAUSS, GSN_RES_GAMMA = 0, 1
+GSN_ANA, GSN_ANA_SHIFT, GSN_ANA_PEAK = 0, 1, 2
+
+
+class gsn_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("resolution", C.c_int), ("band_cut", C.c_double),
+                ("birks_s0", C.c_double), ("birks_s1", C.c_double), ("device", C.c_int),
+                ("stream", C.c_void_p), ("max_toys_per_launch", C.c_int)]
+
+
+class GsnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gsn error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int)
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgsn.so once; raises if it has not been built (no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgsn.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    sig = {
+        "gsn_default_options": (C.c_int, [C.POINTER(gsn_options)]),
+        "gsn_create": (C.c_int, [C.POINTER(vp), C.POINTER(gsn_options)]),
+        "gsn_destroy": (None, [vp]),
+        "gsn_last_error": (C.c_char_p, [vp]),
+        "gsn_n_slots": (C.c_int, [C.c_int]),
+        "gsn_set_data": (C.c_int, [vp, C.c_int, _IP, C.POINTER(_DP), C.POINTER(_DP), _DP, _IP, _IP]),
+        "gsn_set_species": (C.c_int, [vp, C.c_int, C.c_int, _DP, _DP, _IP, _DP, C.POINTER(C.c_ubyte)]),
+        "gsn_set_params": (C.c_int, [vp, C.c_int, _IP, C.c_int, _IP, _DP, _DP]),
+        "gsn_eval": (C.c_int, [vp, _DP, _DP]),
+        "gsn_eval_grad": (C.c_int, [vp, _DP, _DP, _DP]),
+        "gsn_eval_grad_batch": (C.c_int, [vp, C.c_int, _DP, _DP, _IP, _DP, _DP]),
+        "gsn_eval_grad_batch_dev": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, vp, vp]),
+        "gsn_expected": (C.c_int, [vp, _DP, C.c_int, _DP]),
+        "gsn_stream": (vp, [vp]),
+        "gsn_profile": (C.c_int, [vp, C.c_int]),
+        "gsn_profile_read": (C.c_int, [vp, C.c_int, _DP, C.POINTER(C.c_longlong), C.POINTER(C.c_ulonglong)]),
+        "gsn_kernel_name": (C.c_char_p, [C.c_int]),
+        "gsn_peak_probe": (C.c_int, [C.c_int, C.c_int, _DP]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export (one per declaration of gsn.h)."""
+    return ["gsn_default_options", "gsn_create", "gsn_destroy", "gsn_last_error", "gsn_n_slots",
+            "gsn_set_data", "gsn_set_species", "gsn_set_params", "gsn_eval", "gsn_eval_grad",
+            "gsn_eval_grad_batch", "gsn_eval_grad_batch_dev", "gsn_expected", "gsn_stream",
+            "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe"]
+
+
+GSN_K_COUNT = 7
+GSN_PROBE_FFMA, GSN_PROBE_EX2, GSN_PROBE_DFMA, GSN_PROBE_NODE = 0, 1, 2, 3
+
+
+def peak_probe(which, device=0):
+    """Operations per second of one instruction class on every SM (gsn_peak_probe)."""
+    lib = load_library()
+    out = C.c_double()
+    rc = lib.gsn_peak_probe(device, which, C.byref(out))
+    if rc != GSN_OK:
+        raise GsnError(rc, "gsn_peak_probe failed")
+    return out.value
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_DP)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_IP)
+
+
+class Context:
+    """One gsn_ctx: a problem (data, species, parameter map) on one device and stream."""
+
+    def __init__(self, precision=GSN_FP64, resolution=GSN_RES_GAUSS, band_cut=0.0, device=0, stream=None,
+                 birks_s0=1.55, birks_s1=0.155, max_toys_per_launch=0):
+        self.lib = load_library()
+        o = gsn_options()
+        self.lib.gsn_default_options(C.byref(o))
+        o.precision, o.resolution, o.band_cut = precision, resolution, band_cut
+        o.birks_s0, o.birks_s1, o.device = birks_s0, birks_s1, device
+        o.stream = stream
+        o.max_toys_per_launch = max_toys_per_launch
+        h = C.c_void_p()
+        rc = self.lib.gsn_create(C.byref(h), C.byref(o))
+        if rc != GSN_OK:
+            raise GsnError(rc, "gsn_create failed")
+        self.h = h
+        self.precision = precision
+        self.n_params = 0
+        self.total_bins = 0
+        self.n_datasets = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gsn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != GSN_OK:
+            raise GsnError(rc, self.lib.gsn_last_error(self.h).decode())
+        return rc
+
+    def last_error(self):
+        return self.lib.gsn_last_error(self.h).decode()
+
+    # ---------------------------------------------------------- setup ----
+    def set_data(self, edges, counts, exposures, win_lo, win_hi):
+        D = len(edges)
+        keep = [_d(e) for e in edges] + [_d(c) for c in counts]
+        nb = np.array([len(e) - 1 for e in edges], np.int32)
+        eptr = (_DP * D)(*[k[1] for k in keep[:D]])
+        cptr = (_DP * D)(*[k[1] for k in keep[D:]])
+        nb_, nbp = _i(nb)
+        ex_, exp_ = _d(exposures)
+        lo_, lop = _i(win_lo)
+        hi_, hip = _i(win_hi)
+        self._check(self.lib.gsn_set_data(self.h, D, nbp, eptr, cptr, exp_, lop, hip))
+        self.n_datasets = D
+        self.total_bins = int(nb.sum())
+        self.n_bins = [int(x) for x in nb]
+
+    def set_species(self, fine_centres, spectra, kind, shift, dataset_mask):
+        spectra = np.ascontiguousarray(spectra, np.float64)
+        S, K = spectra.shape
+        E_, Ep = _d(fine_centres)
+        S_, Sp = _d(spectra)
+        k_, kp = _i(kind)
+        sh_, shp = _d(shift if shift is not None else np.zeros(S))
+        m = np.ascontiguousarray(dataset_mask, np.uint8)
+        self._check(self.lib.gsn_set_species(self.h, S, K, Ep, Sp, kp, shp, m.ctypes.data_as(C.POINTER(C.c_ubyte))))
+        self.n_species = S
+
+    def set_params(self, n_params, slot_map, pull_param=(), pull_centre=(), pull_width=()):
+        sm_, smp = _i(np.asarray(slot_map).reshape(-1))
+        pp_, ppp = _i(np.asarray(pull_param, np.int32).reshape(-1))
+        pc_, pcp = _d(np.asarray(pull_centre, np.float64).reshape(-1))
+        pw_, pwp = _d(np.asarray(pull_width, np.float64).reshape(-1))
+        self._check(self.lib.gsn_set_params(self.h, n_params, smp, len(pp_), ppp, pcp, pwp))
+        self.n_params = n_params
+
+    # ------------------------------------------------------------ calls ----
+    def eval(self, params):
+        p_, pp = _d(params)
+        out = C.c_double()
+        rc = self.lib.gsn_eval(self.h, pp, C.byref(out))
+        return rc, out.value
+
+    def eval_grad(self, params):
+        p_, pp = _d(params)
+        out = C.c_double()
+        g = np.zeros(self.n_params)
+        rc = self.lib.gsn_eval_grad(self.h, pp, C.byref(out), g.ctypes.data_as(_DP))
+        return rc, out.value, g
+
+    def eval_grad_batch(self, params, counts, windows, want_grad=True):
+        params = np.ascontiguousarray(params, np.float64)
+        T = params.shape[0]
+        c_, cp = _d(counts)
+        w_, wp = _i(windows)
+        nll = np.zeros(T)
+        g = np.zeros((T, self.n_params)) if want_grad else None
+        rc = self.lib.gsn_eval_grad_batch(self.h, T, params.ctypes.data_as(_DP), cp, wp, nll.ctypes.data_as(_DP),
+                                          g.ctypes.data_as(_DP) if want_grad else None)
+        return rc, nll, g
+
+    def eval_grad_batch_dev(self, params, counts, windows, nll, grad=None, status=None):
+        """Device tensors (torch): params (T,P) f64, counts (T,B) f64, windows (T,D,2) i32, nll (T,) f64."""
+        T = int(params.shape[0])
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        return self.lib.gsn_eval_grad_batch_dev(self.h, T, ptr(params), ptr(counts), ptr(windows), ptr(nll),
+                                                ptr(grad), ptr(status))
+
+    def expected(self, params, dataset):
+        p_, pp = _d(params)
+        out = np.zeros((self.n_bins[dataset], self.n_species))
+        self._check(self.lib.gsn_expected(self.h, pp, dataset, out.ctypes.data_as(_DP)))
+        return out
+
+    def stream(self):
+        return self.lib.gsn_stream(self.h)
+
+    def profile(self, enable=True):
+        self._check(self.lib.gsn_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches, evaluated (bin, column) pairs)} since the last reset."""
+        out = {}
+        for k in range(GSN_K_COUNT):
+            ms, n, u = C.c_double(), C.c_longlong(), C.c_ulonglong()
+            self._check(self.lib.gsn_profile_read(self.h, k, C.byref(ms), C.byref(n), C.byref(u)))
+            out[self.lib.gsn_kernel_name(k).decode()] = (ms.value, n.value, u.value)
+        return out
+
+
+def context_from_workload(work: dict, precision=GSN_FP64, counts=None, **kw) -> Context:
+    """Configure a Context from a workload dictionary (see inputs.py)."""
+    ctx = Context(precision=precision, resolution=int(work["resolution"]),
+                  birks_s0=work["birks_s0"], birks_s1=work["birks_s1"], **kw)
+    edges = work["edges"]
+    if counts is None:
+        counts = [np.zeros(len(e) - 1) for e in edges]
+    elif not isinstance(counts, (list, tuple)):
+        flat = np.asarray(counts, np.float64)
+        counts, o = [], 0
+        for e in edges:
+            counts.append(flat[o:o + len(e) - 1]); o += len(e) - 1
+    ctx.set_data(edges, counts, work["exposure"], work["win_lo"], work["win_hi"])
+    ctx.set_species(work["fine_centres"], work["spectra"], work["kind"], work["shift"], work["mask"])
+    ctx.set_params(int(work["n_params"]), work["slot_map"], work["pull_param"], work["pull_centre"], work["pull_width"])
+    return ctx
+
+
+# --------------------------------------------------------------- autograd ----
+def make_autograd():
+    """torch.autograd.Function whose forward is gsn_eval_grad and whose backward
+    scales the analytic gradient of the adjoint kernel."""
+    import torch
+
+    class GsnNLL(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, params, ctx):
+            rc, nll, g = ctx.eval_grad(params.detach().cpu().double().numpy())
+            if rc != GSN_OK:
+                raise GsnError(rc, ctx.last_error())
+            fctx.save_for_backward(torch.from_numpy(g).to(params.device, params.dtype))
+            return torch.tensor(nll, dtype=params.dtype, device=params.device)
+
+        @staticmethod
+        def backward(fctx, gout):
+            (g,) = fctx.saved_tensors
+            return gout * g, None
+
+    return GsnNLL
