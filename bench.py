@@ -200,7 +200,9 @@ def run_ours(args, rank, world, local_rank):
 
     T = args.toys
     w, b = make_inputs(T, 1000 + rank * T)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the library launches on it and the timing events are recorded on it
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     ctx = gsn.context_from_workload(w, gsn.GSN_MIXED, device=local_rank, stream=stream.cuda_stream)
     P, B, D = w["n_params"], b["counts"].shape[1], 2
     params = torch.from_numpy(b["params"]).to(dev)

@@ -220,7 +220,8 @@ def test_toy_batch_sampled(toys, precision):
         rc1, n1, g1 = ctx.eval_grad_batch(b["params"][t:t + 1], b["counts"][t:t + 1], b["windows"][t:t + 1])
         tol = 1e-12 * abs(n1[0]) if precision == FP64 else 1e-4
         assert abs(n1[0] - nll[t]) < tol
-        assert norm_rel(g1[0], g[t]) < (1e-11 if precision == FP64 else 1e-6)
+        # one toy alone runs with another split plan (summation order) than the batch
+        assert norm_rel(g1[0], g[t]) < (1e-11 if precision == FP64 else 1e-5)
 
 
 def test_toy_gradient_against_oracle(toys):
