@@ -183,6 +183,32 @@ int gsn_expected(gsn_ctx* ctx, const double* params, int dataset, double* mu_per
 /* Stream of the context (cudaStream_t), e.g. to order caller work after it. */
 void* gsn_stream(gsn_ctx* ctx);
 
+/* NLL and gradient at one parameter point without allocating device memory.
+ * The paper has no counterpart: this entry point serves callers that must not
+ * call cudaMalloc while they run -- code inside a stream-ordered region that
+ * forbids allocation (a step being captured into a CUDA graph, a real-time
+ * loop with a pre-reserved memory budget, an allocator that owns the device).
+ * The intermediate buffers of the step (column records, band summaries,
+ * partial sums of mu, w = 1 - n/mu, partial gradients) live in one static
+ * device array of GSN_NOALLOC_SCRATCH_BYTES that the library reserves on
+ * every GPU it is loaded on, until the process exits.
+ *   params_dev  [n_params] device pointer
+ *   nll_dev     [1] device output; grad_dev [n_params] device output
+ *   status_dev  [1] device output (0 or a GSN_ERR_* code of the step), or NULL
+ * Counts and windows are those of gsn_set_data.  The context's problem must
+ * already be on the device: call gsn_eval or gsn_eval_grad once during set-up
+ * (else GSN_ERR_STATE).  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  Problems
+ * needing more scratch than the array holds are rejected with GSN_ERR_ARG and
+ * a message giving the size needed.  Enqueued on the context's stream without
+ * synchronising.  Every call, from any context, uses the same array: calls
+ * whose kernels overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.  Nothing in the array needs to start
+ * at zero; each call overwrites what it reads. */
+#define GSN_NOALLOC_SCRATCH_BYTES (16u << 20)
+int gsn_eval_grad_noalloc(gsn_ctx* ctx, const double* params_dev, double* nll_dev, double* grad_dev,
+                          int* status_dev);
+
 /* ----------------------------------------------------------- tracing ----
  * Per-kernel statistics.  While enabled, each kernel launch of the context is
  * bracketed by CUDA events recorded on the context's stream, and the response

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -793,4 +794,78 @@ int gsn_eval_grad_batch(gsn_ctx* c, int n_toys, const double* params, const doub
     return GSN_OK;
 }
 
+
 }  // extern "C"
+
+// ============================================================ no-allocation
+// One static device array holds the intermediate buffers of
+// gsn_eval_grad_noalloc; its device address is looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GSN_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+void* noalloc_address(int dev, std::string& err) {
+    static std::mutex mu;
+    static void* addr[64] = {nullptr};
+    if (dev < 0 || dev >= 64) { err = "device ordinal out of range"; return nullptr; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (addr[dev]) return addr[dev];
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != dev && cudaSetDevice(dev) != cudaSuccess) { cudaGetLastError(); err = "cudaSetDevice failed"; return nullptr; }
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        err = std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e);
+        return nullptr;
+    }
+    addr[dev] = p;
+    return p;
+}
+
+}  // namespace
+
+extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, double* nll_dev, double* grad_dev,
+                                     int* status_dev) {
+    if (!c) return GSN_ERR_ARG;
+    if (!params_dev || !nll_dev || !grad_dev) return fail(c, GSN_ERR_ARG, "NULL device pointer");
+    if (!c->ready)
+        return fail(c, GSN_ERR_STATE, "the problem is not on the device yet: call gsn_eval or gsn_eval_grad once first");
+    std::string err;
+    unsigned char* base = static_cast<unsigned char*>(noalloc_address(c->dev, err));
+    if (!base) return fail(c, GSN_ERR_CUDA, err);
+    KArgs a = c->base;
+    const Plan p = make_plan(c, 1);
+    const size_t rs = c->opt.precision == GSN_MIXED ? sizeof(float) : sizeof(double);
+    const size_t sizes[6] = {
+        (size_t)c->G * c->K * NFP * rs,                         // column records
+        (size_t)c->G * a.nblk * 2 * rs,                         // band summaries
+        (size_t)p.nsplit * c->total_bins * sizeof(double),      // partial mu
+        (size_t)c->total_bins * rs,                             // w
+        (size_t)c->G * p.nbtask * a.NPART * sizeof(double),     // partial gradients
+        (size_t)c->P * sizeof(double)};                         // direct gradient terms
+    size_t off[6], total = 0;
+    for (int i = 0; i < 6; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
+    if (total > GSN_NOALLOC_SCRATCH_BYTES)
+        return fail(c, GSN_ERR_ARG, "this problem needs " + std::to_string(total) + " bytes of scratch; the "
+                    "no-allocation entry point holds " + std::to_string((size_t)GSN_NOALLOC_SCRATCH_BYTES));
+    a.T = 1;
+    a.nsplit = p.nsplit; a.ntile = p.ntile;
+    a.bw_warps = p.bw_warps; a.bw_bsplit = p.bw_bsplit; a.nbtask = p.nbtask;
+    a.colbuf = base + off[0]; a.blkbuf = base + off[1]; a.mubuf = (double*)(base + off[2]);
+    a.wbuf = base + off[3]; a.partbuf = (double*)(base + off[4]); a.gdirect = (double*)(base + off[5]);
+    a.params = params_dev; a.params_stride = c->P;
+    a.counts_stride = 0; a.win_stride = 0;
+    a.nll = nll_dev; a.grad = grad_dev; a.status = status_dev;
+    a.want_grad = 1;
+    a.work = nullptr;
+    CUDA_TRY(c, launch_columns(a, c->stream));
+    CUDA_TRY(c, launch_forward(a, c->stream));
+    CUDA_TRY(c, launch_deviance(a, c->stream));
+    CUDA_TRY(c, launch_backward(a, c->stream));
+    CUDA_TRY(c, launch_gradfinal(a, c->stream));
+    return GSN_OK;
+}
+

@@ -68,6 +68,7 @@ def load_library(path: str = LIB_PATH):
         "gsn_profile_read": (C.c_int, [vp, C.c_int, _DP, C.POINTER(C.c_longlong), C.POINTER(C.c_ulonglong)]),
         "gsn_kernel_name": (C.c_char_p, [C.c_int]),
         "gsn_peak_probe": (C.c_int, [C.c_int, C.c_int, _DP]),
+        "gsn_eval_grad_noalloc": (C.c_int, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -82,7 +83,7 @@ def exported_symbols():
     return ["gsn_default_options", "gsn_create", "gsn_destroy", "gsn_last_error", "gsn_n_slots",
             "gsn_set_data", "gsn_set_species", "gsn_set_params", "gsn_eval", "gsn_eval_grad",
             "gsn_eval_grad_batch", "gsn_eval_grad_batch_dev", "gsn_expected", "gsn_stream",
-            "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe"]
+            "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe", "gsn_eval_grad_noalloc"]
 
 
 GSN_K_COUNT = 7
