@@ -204,7 +204,7 @@ int finalize(gsn_ctx* c) {
     a.G = c->G;
     // edges and node tables per group
     std::vector<double> edges_all, ntab_d;
-    std::vector<float> ntab_f, xc_f;
+    std::vector<float> ntab_f, xc_f, btab_f;
     std::vector<unsigned char> bcls;
     std::vector<double> gx_lin, gw_lin, gx_log, gw_log;
     const int ng_lin = mixed ? NG_LIN_F : NG_LIN_D, ng_log = mixed ? NG_LOG_F : NG_LOG_D;
@@ -221,6 +221,9 @@ int finalize(gsn_ctx* c) {
         a.g_edge_off[g] = (int)edges_all.size();
         a.g_node_off[g] = noff;
         a.g_zero[g] = (gamma && x[0] == 0.0) ? 1 : 0;
+        a.g_jlin[g] = 0;
+        if (gamma)
+            while (a.g_jlin[g] < J && !(x[a.g_jlin[g]] >= xlog && x[a.g_jlin[g]] > 0.0)) ++a.g_jlin[g];
         c->Jmax = std::max(c->Jmax, J);
         edges_all.insert(edges_all.end(), x.begin(), x.end());
         for (int j = 0; j < J; ++j) {
@@ -244,6 +247,16 @@ int finalize(gsn_ctx* c) {
                 }
             }
             bcls.push_back(cls);
+            if (mixed) {
+                // symmetric 3-node rule of linear bins: centre and +-offset
+                const float xcf = (float)xc;
+                const double off = 0.5 * (hi - lo) * std::sqrt(0.6);
+                float bt[8] = {xcf, (float)(xc + off - (double)xcf), (float)std::log1p(off / xc),
+                               (float)std::log1p(-off / xc), (float)(0.5 * (hi - lo) * 8.0 / 9.0),
+                               (float)(0.5 * (hi - lo) * 5.0 / 9.0), 0.f, 0.f};
+                if (cls != BIN_LIN) for (int q = 1; q < 8; ++q) bt[q] = 0.f;
+                btab_f.insert(btab_f.end(), bt, bt + 8);
+            }
             if (mixed) {
                 const float xcf = (float)xc;
                 xc_f.push_back(xcf);
@@ -273,6 +286,7 @@ int finalize(gsn_ctx* c) {
     if ((rc = upload(c, bcls, &a.bclass))) return rc;
     if (mixed) {
         if ((rc = upload(c, ntab_f, &a.ntab_f))) return rc;
+        if ((rc = upload(c, btab_f, &a.btab_f))) return rc;
         if ((rc = upload(c, xc_f, &a.xc_f))) return rc;
     } else {
         if ((rc = upload(c, ntab_d, &a.ntab_d))) return rc;

@@ -29,9 +29,10 @@ constexpr int NFP = 16;      // fields per column record
 //  fp64 gamma  : MUH = mu, A = -d ln s - lgamma(d), B = d-1, C = 1/s,
 //                KAPPA = ln s + psi(d), N = 1
 //  fp64 gauss  : MUH = mu, A = 1/sigma, N = 1
-//  all         : DEQ = d E_q / d kB, XMIN/XMAX = band in p.e., P0/P0D/P0S =
-//                bin-at-zero content and its d- and s-derivatives (gamma, / N,
-//                P0S times s^2), TN0.. = N_k * T_dk of each dataset of the group
+//  all         : DEQ = d E_q / d kB, XMIN/XMAX = band in p.e., P0 = bin-at-zero
+//                content / N; P0D/P0S its derivatives: fp64 dP/dd and s^2 dP/ds,
+//                mixed (mu/d) dP/dmu|var / N and s^2 dP/dvar|mu / N;
+//                TN0.. = N_k * T_dk of each dataset of the group
 enum { F_MUH = 0, F_MUL, F_A, F_B, F_C, F_N, F_KAPPA, F_DEQ, F_XMIN, F_XMAX,
        F_P0, F_P0D, F_P0S, F_TN0 };
 static_assert(F_TN0 + MAXGDS <= NFP, "column record too small");
@@ -58,6 +59,9 @@ struct KArgs {
     const float* xc_f;          // [bin] bin centre
     const unsigned char* bclass;// [bin] BIN_LIN / BIN_LOG / BIN_ZERO
     const double* ntab_d;       // [bin][3][NGM_D]: x, ln x, weight
+    const float* btab_f;        // [bin][8] linear bins, symmetric 3-node rule: xc, offset, ln(1+offset/xc),
+                                // ln(1-offset/xc), centre weight, side weight, -, -
+    int g_jlin[MAXG];           // first bin of the group from which every bin is linear
     const double* E;            // fine centres [K]
     const float* E_hi;          // double-float split of E
     const float* E_lo;
@@ -106,6 +110,8 @@ cudaError_t launch_species(const KArgs& a, cudaStream_t st);
 cudaError_t launch_mu_from_species(const KArgs& a, cudaStream_t st);
 cudaError_t launch_expected_out(const KArgs& a, cudaStream_t st);
 cudaError_t run_probe(int which, int nsm, double* ops_per_second);
+cudaError_t launch_forward_mixed(const KArgs& a, cudaStream_t st);
+cudaError_t launch_backward_mixed(const KArgs& a, cudaStream_t st);
 
 constexpr int K_COLUMNS = 0, K_FORWARD = 1, K_DEVIANCE = 2, K_BACKWARD = 3, K_GRADFINAL = 4,
               K_SPECIES = 5, K_MU = 6, K_COUNT = 7;

@@ -17,159 +17,9 @@
 // Mixed precision: FP32 response build and contraction with double-float
 // column means, FP32 partial sums flushed to FP64 per column block, FP64
 // deviance and reductions.  FP64: everything in double.
-#include "gsn_internal.cuh"
-
-#include <math.h>
+#include "gsn_device.cuh"
 
 namespace gsn {
-
-#define DEV __device__ __forceinline__
-
-constexpr float L2E = 1.4426950408889634f;           // log2(e)
-constexpr double INV_SQRT2 = 0.70710678118654752440;
-constexpr double INV_SQRT2PI = 0.39894228040143267794;
-constexpr int FWD_WARPS = 8;
-
-// ------------------------------------------------------------------ math --
-DEV float ex2f(float x) {  // 2^x on the SFU
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// D(t) = ln(1 + t) - t with relative precision: for t in [-1/2, 1] from the
-// series ln(1+t) = 2 atanh(u), u = t/(2+t), rearranged so that no leading
-// terms cancel: D = -t u + 2 u^3 (1/3 + u^2/5 + u^4/7 + ...).
-DEV float log1pmx_f(float t) {
-    if (t >= -0.5f && t <= 1.0f) {
-        float u = __fdividef(t, 2.0f + t);
-        float v = u * u;
-        float p = fmaf(v, 1.0f / 15.0f, 1.0f / 13.0f);
-        p = fmaf(p, v, 1.0f / 11.0f);
-        p = fmaf(p, v, 1.0f / 9.0f);
-        p = fmaf(p, v, 1.0f / 7.0f);
-        p = fmaf(p, v, 1.0f / 5.0f);
-        p = fmaf(p, v, 1.0f / 3.0f);
-        return fmaf(2.0f * u * v, p, -t * u);
-    }
-    return log1pf(t) - t;
-}
-// D(t) and L1 = ln(1 + t) together; L1 directly from log1p where |t| is large
-DEV float log1pmx2_f(float t, float& L1) {
-    if (t >= -0.5f && t <= 1.0f) {
-        const float D = log1pmx_f(t);
-        L1 = D + t;
-        return D;
-    }
-    L1 = log1pf(t);
-    return L1 - t;
-}
-
-// digamma by upward recurrence and the asymptotic series (Abramowitz & Stegun 6.3.18)
-DEV double digamma_d(double x) {
-    double acc = 0.0;
-    while (x < 12.0) { acc -= 1.0 / x; x += 1.0; }
-    double ix = 1.0 / x, ix2 = ix * ix;
-    double s = ix2 * (1.0 / 12 - ix2 * (1.0 / 120 - ix2 * (1.0 / 252 - ix2 * (1.0 / 240 - ix2 * (1.0 / 132)))));
-    return acc + log(x) - 0.5 * ix - s;
-}
-DEV float digamma_f(float x) {
-    float acc = 0.0f;
-    while (x < 6.0f) { acc -= 1.0f / x; x += 1.0f; }
-    float ix = 1.0f / x, ix2 = ix * ix;
-    float s = ix2 * (1.0f / 12 - ix2 * (1.0f / 120 - ix2 * (1.0f / 252 - ix2 * (1.0f / 240))));
-    return acc + logf(x) - 0.5f * ix - s;
-}
-
-// double-float helpers (error-free products and sums)
-DEV void df_mul(float ah, float al, float bh, float bl, float& rh, float& rl) {
-    float p = ah * bh;
-    float e = fmaf(ah, bh, -p);
-    e = fmaf(ah, bl, fmaf(al, bh, e));
-    rh = p + e;
-    rl = e - (rh - p);
-}
-DEV void df_add(float ah, float al, float b, float& rh, float& rl) {
-    float s = ah + b;
-    float bb = s - ah;
-    float e = (ah - (s - bb)) + (b - bb);
-    e += al;
-    rh = s + e;
-    rl = e - (rh - s);
-}
-
-// Phi(z1) - Phi(z0) for z0 <= z1 without cancellation in the tails
-DEV double ncdf_diff(double z0, double z1) {
-    if (z0 >= 0.0) return 0.5 * (erfc(z0 * INV_SQRT2) - erfc(z1 * INV_SQRT2));
-    if (z1 <= 0.0) return 0.5 * (erfc(-z1 * INV_SQRT2) - erfc(-z0 * INV_SQRT2));
-    return 1.0 - 0.5 * (erfc(-z0 * INV_SQRT2) + erfc(z1 * INV_SQRT2));
-}
-
-template <class R> DEV R warp_sum(R v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-template <class R> DEV R warp_min(R v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-template <class R> DEV R warp_max(R v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// fixed-order block sum of one double per thread (result valid in thread 0)
-DEV double block_sum_d(double v, double* sh) {
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < nw; ++i) s += sh[i];
-    return s;
-}
-
-DEV void toy_window_union(const KArgs& a, int t, int g, int& wlo, int& whi) {
-    const int J = a.g_bins[g];
-    wlo = J; whi = 0;
-    for (int dd = 0; dd < a.g_nds[g]; ++dd) {
-        const int d = a.g_ds[g][dd];
-        int lo = a.win[t * a.win_stride + 2 * d], hi = a.win[t * a.win_stride + 2 * d + 1];
-        lo = max(lo, 0); hi = min(hi, J);
-        if (hi > lo) { wlo = min(wlo, lo); whi = max(whi, hi); }
-    }
-}
-
-template <class R> DEV R* colrec(const KArgs& a, int t, int g, int k) {
-    return reinterpret_cast<R*>(a.colbuf) + (((long long)t * a.G + g) * a.K + k) * NFP;
-}
-
-// ------------------------------------------------------- bin-at-zero -------
-// P(d, y) = e^-y sum_n y^(d+n) / Gamma(d+n+1), its d-derivative (through
-// psi(d+n+1) = psi(d+1) + sum_{m<=n} 1/(d+m)), and s^2 dP/ds = -s y^d e^-y / Gamma(d).
-template <class R> DEV void gamma_bin_zero(R d, R s, R x1, R& P, R& Pd, R& Ps2) {
-    const R y = x1 / s;
-    const R ly = log(y);
-    const R pref = exp(d * ly - y - lgamma(d + R(1)));
-    R term = 1, sum = 1, H = 0, hsum = 0;
-    const int nmax = sizeof(R) == 8 ? 80 : 40;
-    for (int n = 1; n < nmax; ++n) {
-        term *= y / (d + R(n));
-        H += R(1) / (d + R(n));
-        sum += term;
-        hsum += term * H;
-        if (term < R(sizeof(R) == 8 ? 1e-18 : 1e-9) * sum) break;
-    }
-    P = pref * sum;
-    const R psi1 = sizeof(R) == 8 ? (R)digamma_d((double)d + 1.0) : (R)digamma_f((float)d + 1.0f);
-    Pd = P * (ly - psi1) - pref * hsum;
-    Ps2 = -s * exp(d * ly - y - lgamma(d));
-}
 
 // ------------------------------------------------------------- columns -----
 template <class R, int RES>
@@ -220,20 +70,23 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
             const float Eh = a.E_hi[k], El = a.E_lo[k];
             float qh, ql;
             df_mul(Eh, El, sdf[0], sdf[1], qh, ql);
-            float Dy = 0.f, y = 0.f;
+            float Dy = 0.f, y = 0.f, Ly = 0.f;
             if (beta > 0) {
                 y = Eh * sdf[5];
-                Dy = log1pmx_f(y);
+                Dy = log1pmx2_f(y, Ly);
                 if (y < 1.0f) { qh = -sdf[4] * Dy; ql = 0.f; }
-                else df_add(qh, ql, -sdf[4] * log1pf(y), qh, ql);
+                else df_add(qh, ql, -sdf[4] * Ly, qh, ql);
             }
             float muh, mul;
             df_mul(qh, ql, sdf[2], sdf[3], muh, mul);
             f[F_MUH] = muh; f[F_MUL] = mul;
             mu = muh;
+            // dE_q/dkB = (1/alpha^2) [ s0 (beta/alpha) (2 D + y r) - s1 (D + y r) ], r = y/(1+y);
+            // for y >= 1 the same terms as 2 ln(1+y) - y (2 - r) and ln(1+y) - r (no cancellation)
             const float r1 = y / (1.0f + y);
-            // dE_q/dkB = (1/alpha^2) [ s0 (beta/alpha) (2 D + y^2/(1+y)) - s1 (D + y^2/(1+y)) ]
-            deq = beta > 0 ? sdf[7] * (sdf[6] * (2.0f * Dy + y * r1) - (float)a.s1 * (Dy + y * r1)) : (float)NAN;
+            const float ta = y < 1.0f ? fmaf(2.0f, Dy, y * r1) : fmaf(2.0f, Ly, -y * (2.0f - r1));
+            const float tb = y < 1.0f ? fmaf(y, r1, Dy) : Ly - r1;
+            deq = beta > 0 ? sdf[7] * (sdf[6] * ta - (float)a.s1 * tb) : (float)NAN;
         } else {
             const double E = a.E[k];
             double Eq = E / alpha;
@@ -290,18 +143,42 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
             } else {
                 thi = c / d;
             }
+            // for d > 1, h + cut is concave: Newton steps from these outer bounds stay outside the band
+            if (d > R(1)) {
+                for (int it = 0; it < 3; ++it) {
+                    const R L1 = log1p(thi);
+                    const R h = (d - R(1)) * (L1 - thi) - thi + c;
+                    const R hp = -(d - R(1)) * thi / (R(1) + thi) - R(1);
+                    thi = thi - h / hp;
+                }
+            }
             xmax = mu * (R(1) + thi);
             xmin = 0;
             if (d > R(1)) {
-                const R tlo = -(R(1) + sqrt(R(1) + R(2) * c * (d - R(1)))) / (d - R(1));
-                xmin = tlo > R(-1) ? mu * (R(1) + tlo) : R(0);
+                R tlo = -(R(1) + sqrt(R(1) + R(2) * c * (d - R(1)))) / (d - R(1));
+                if (tlo > R(-1)) {
+                    for (int it = 0; it < 3; ++it) {
+                        const R L1 = log1p(tlo);
+                        const R h = (d - R(1)) * (L1 - tlo) - tlo + c;
+                        const R hp = -(d - R(1)) * tlo / (R(1) + tlo) - R(1);
+                        tlo = fmax(tlo - h / hp, tlo);
+                    }
+                    xmin = mu * (R(1) + tlo);
+                }
             }
             if (a.g_zero[g]) {
                 const R x1 = (R)a.edges[a.g_edge_off[g] + 1];
                 if (xmin <= x1) {
                     R P, Pd, Ps2;
                     gamma_bin_zero<R>(d, s, x1, P, Pd, Ps2);
-                    f[F_P0] = P / Nk; f[F_P0D] = Pd / Nk; f[F_P0S] = Ps2 / Nk;
+                    f[F_P0] = P / Nk;
+                    if constexpr (sizeof(R) == 4) {
+                        // mixed adjoint: (mu/d) dP/dmu at fixed variance, s^2 dP/dvar at fixed mean
+                        f[F_P0D] = (R(2) * Pd - Ps2 / mu) / Nk;
+                        f[F_P0S] = (Ps2 / mu - Pd) / Nk;
+                    } else {
+                        f[F_P0D] = Pd; f[F_P0S] = Ps2;
+                    }
                 }
             }
         }
@@ -330,33 +207,6 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
         R* b = reinterpret_cast<R*>(a.blkbuf) + (((long long)t * a.G + g) * a.nblk + blockIdx.x) * 2;
         b[0] = mn; b[1] = mx;
     }
-}
-
-// --------------------------------------------------- response evaluators ---
-// Mixed: unnormalised bin value rho_jk = sum_n w_n exp(E_n) of a column record.
-template <int RES, int NG>
-DEV float bin_value_f(const float* c, float xc, const float* del, const float* lam, const float* wt) {
-    const float Dx = (xc - c[F_MUH]) - c[F_MUL];
-    float rho = 0.0f;
-    if constexpr (RES == 0) {
-        const float z = Dx * c[F_A];
-#pragma unroll
-        for (int n = 0; n < NG; ++n) {
-            const float zn = fmaf(del[n], c[F_A], z);
-            rho = fmaf(wt[n], ex2f(-0.5f * L2E * zn * zn), rho);
-        }
-    } else {
-        // log f(x) - log f(mu) = (d-1) D(t) - t = d D(t) - ln(1+t), t = x/mu - 1
-        const float t = Dx * c[F_A];
-        float L1;
-        const float Dt = log1pmx2_f(t, L1);
-        const float B2 = L2E * (c[F_B] - 1.0f), C2 = L2E * c[F_C];
-        const float Ec = fmaf(L2E * c[F_B], Dt, -L2E * L1);
-#pragma unroll
-        for (int n = 0; n < NG; ++n)
-            rho = fmaf(wt[n], ex2f(Ec + fmaf(C2, del[n], B2 * lam[n])), rho);
-    }
-    return rho;
 }
 
 // FP64 gamma: sum_n w_n exp((d-1) ln x_n - x_n/s - d ln s - lgamma(d))
@@ -1077,8 +927,7 @@ cudaError_t launch_columns(const KArgs& a, cudaStream_t st) {
 cudaError_t launch_forward(const KArgs& a, cudaStream_t st) {
     dim3 grid(a.ntile, a.nsplit, a.T * a.G);
     if (a.precision == 1) {
-        if (a.res == 0) k_forward<float, 0><<<grid, FWD_WARPS * 32, 0, st>>>(a);
-        else            k_forward<float, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        return launch_forward_mixed(a, st);
     } else {
         if (a.res == 0) k_forward_gauss64<<<grid, FWD_WARPS * 32, 0, st>>>(a);
         else            k_forward<double, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
@@ -1093,17 +942,12 @@ cudaError_t launch_deviance(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_backward(const KArgs& a, cudaStream_t st) {
+    if (a.precision == 1) return launch_backward_mixed(a, st);
     dim3 grid(a.nbtask, a.G, a.T);
     const int threads = a.bw_warps * 32;
-    if (a.precision == 1) {
-        const size_t sm = sizeof(float) * MAXGDS * threads + 16 + sizeof(double) * a.bw_warps * NRESP;
-        if (a.res == 0) k_backward<float, 0><<<grid, threads, sm, st>>>(a);
-        else            k_backward<float, 1><<<grid, threads, sm, st>>>(a);
-    } else {
-        const size_t sm = sizeof(double) * MAXGDS * threads + 16 + sizeof(double) * a.bw_warps * NRESP;
-        if (a.res == 0) k_backward<double, 0><<<grid, threads, sm, st>>>(a);
-        else            k_backward<double, 1><<<grid, threads, sm, st>>>(a);
-    }
+    const size_t sm = sizeof(double) * MAXGDS * threads + 16 + sizeof(double) * a.bw_warps * NRESP;
+    if (a.res == 0) k_backward<double, 0><<<grid, threads, sm, st>>>(a);
+    else            k_backward<double, 1><<<grid, threads, sm, st>>>(a);
     return cudaGetLastError();
 }
 

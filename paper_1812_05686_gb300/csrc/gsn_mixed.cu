@@ -1,0 +1,463 @@
+// Mixed-precision response kernels (FP32 response build and contraction).
+//
+// k_forward_m   lanes <-> 32 bins of one toy; the warp streams the column
+//               records of its band in batches of 32: each lane prefetches one
+//               record into registers while the warp evaluates the previous
+//               batch from a per-warp shared-memory copy, so record loads stay
+//               off the critical path.  A ballot over the batch skips columns
+//               whose band misses the warp's bins.
+// k_backward_m  lanes <-> 32 columns; the warp streams the per-bin data of its
+//               band (node offsets, weights, w_dj) the same way.  The adjoint
+//               accumulates dNLL/dmu_k at fixed variance and dNLL/dsigma_k^2 at
+//               fixed mean directly (no chain rule through shape and scale).
+// Both use the symmetric 3-point Gauss-Legendre rule of linear bins (centre
+// node without offset terms); bins below the log-spaced threshold and the bin
+// at zero take the general node table.  FP32 partial sums are folded per batch
+// into compensated (TwoSum) accumulators.
+#include "gsn_device.cuh"
+
+namespace gsn {
+
+constexpr float SQ_HALF_L2E = 0.84932180028801904f;   // sqrt(log2(e) / 2)
+
+// record fields after the per-warp transformation of the forward kernel
+//   q0 = (mu_hi, mu_lo, A, P)   q1 = (Q, R, P0, -)   q2 = (TN0, TN1, TN2, -)
+//   gamma: A = 1/mu, P = L2E d, Q = L2E (d-1), R = L2E C (C = -1/s)
+//   gauss: A = sqrt(L2E/2)/sigma
+struct RecF {
+    float4 q0, q1, q2;
+};
+
+template <int RES>
+DEV RecF transform_record(const float4 r0, const float4 r1, const float4 r2, const float4 r3) {
+    RecF o;
+    if (RES == 1) {
+        o.q0 = make_float4(r0.x, r0.y, r0.z, L2E * r0.w);
+        o.q1 = make_float4(fmaf(L2E, r0.w, -L2E), L2E * r1.x, r2.z, 0.f);
+    } else {
+        o.q0 = make_float4(r0.x, r0.y, r0.z * SQ_HALF_L2E, 0.f);
+        o.q1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    o.q2 = make_float4(r3.y, r3.z, r3.w, 0.f);
+    return o;
+}
+
+// value of one linear bin (symmetric 3-node rule) for one column
+template <int RES>
+DEV float pair_value(const RecF& c, float xc, float dl, float lp, float lm, float w0, float w1) {
+    const float Dx = (xc - c.q0.x) - c.q0.y;
+    if (RES == 1) {
+        const float tt = Dx * c.q0.z;
+        float L1;
+        const float Dt = log1pmx2_f(tt, L1);
+        const float Ec = fmaf(c.q0.w, Dt, -L2E * L1);
+        const float cd = c.q1.y * dl;
+        const float ap = fmaf(c.q1.x, lp, Ec) + cd;
+        const float am = fmaf(c.q1.x, lm, Ec) - cd;
+        return fmaf(w1, ex2f(ap) + ex2f(am), w0 * ex2f(Ec));
+    } else {
+        const float z = Dx * c.q0.z;
+        const float dz = dl * c.q0.z;
+        const float zp = z + dz, zm = z - dz;
+        return fmaf(w1, ex2f(-zp * zp) + ex2f(-zm * zm), w0 * ex2f(-z * z));
+    }
+}
+
+// ------------------------------------------------------------- forward -----
+template <int RES, int NDS>
+__global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
+    const int tile = blockIdx.x, split = blockIdx.y;
+    const int t = blockIdx.z / a.G, g = blockIdx.z % a.G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ RecF srec[FWD_WARPS][32];
+    int wlo, whi;
+    toy_window_union(a, t, g, wlo, whi);
+    const int j0 = (tile * FWD_WARPS + warp) * 32;
+    if (j0 >= whi || j0 + 32 <= wlo) return;
+    const int j = j0 + lane;
+    const bool valid = j >= wlo && j < whi;
+    const int jr = min(max(j, wlo), whi - 1);
+    const int nb = a.g_node_off[g] + jr;
+    const int jf = max(j0, wlo), jl = min(j0 + 31, whi - 1);
+    const float xlo_w = (float)a.edges[a.g_edge_off[g] + jf];
+    const float xhi_w = (float)a.edges[a.g_edge_off[g] + jl + 1];
+    const int nds = a.g_nds[g];
+    const int kchunk = (a.K + a.nsplit - 1) / a.nsplit;
+    const int k_beg = split * kchunk, k_end = min(a.K, k_beg + kchunk);
+    const float* blk = reinterpret_cast<const float*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
+
+    // column range of the band: first and last 256-column block that overlaps
+    int kfirst = k_end, klast = k_beg;
+    for (int b = k_beg / COLBLK; b * COLBLK < k_end; ++b) {
+        if (blk[2 * b + 1] < xlo_w || blk[2 * b] > xhi_w) continue;
+        kfirst = min(kfirst, max(b * COLBLK, k_beg));
+        klast = max(klast, min((b + 1) * COLBLK, k_end));
+    }
+
+    double accd[MAXGDS] = {0.0, 0.0, 0.0};
+    int ncol = 0;
+    if (j0 < a.g_jlin[g]) {
+        // warp holds bins of the general node table (log-spaced or the bin at zero)
+        const unsigned char cls = a.bclass[nb];
+        const float* nodes = a.ntab_f + (long long)nb * 3 * NGM_F;
+        const float xc = a.xc_f[nb];
+        float del[NG_LOG_F], lam[NG_LOG_F], wt[NG_LOG_F];
+#pragma unroll
+        for (int n = 0; n < NG_LOG_F; ++n) {
+            del[n] = nodes[n]; lam[n] = nodes[NGM_F + n]; wt[n] = valid ? nodes[2 * NGM_F + n] : 0.f;
+        }
+        for (int k = kfirst; k < klast; ++k) {
+            const float* c = colrec<float>(a, t, g, k);
+            if (c[F_XMAX] < xlo_w || c[F_XMIN] > xhi_w) continue;
+            ++ncol;
+            float v = bin_value_f<RES, NG_LOG_F>(c, xc, del, lam, wt);
+            if (RES == 1 && cls == BIN_ZERO) v = valid ? c[F_P0] : 0.0f;
+#pragma unroll
+            for (int dd = 0; dd < MAXGDS; ++dd)
+                if (dd < nds) accd[dd] += (double)(v * c[F_TN0 + dd]);
+        }
+    } else {
+        const float4 b0 = reinterpret_cast<const float4*>(a.btab_f)[2 * nb];
+        const float4 b1 = reinterpret_cast<const float4*>(a.btab_f)[2 * nb + 1];
+        const float xc = b0.x, dl = b0.y, lp = b0.z, lm = b0.w;
+        const float w0 = valid ? b1.x : 0.f, w1 = valid ? b1.y : 0.f;
+        float s[MAXGDS] = {0.f, 0.f, 0.f}, cc[MAXGDS] = {0.f, 0.f, 0.f};
+        const float4* rec = reinterpret_cast<const float4*>(colrec<float>(a, t, g, 0));
+        float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0, r3 = r0;
+        auto load = [&](int k) {
+            if (k < klast) {
+                const float4* p = rec + (long long)k * 4;
+                r0 = p[0]; r1 = p[1]; r2 = p[2]; r3 = p[3];
+            } else {
+                r2 = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
+            }
+        };
+        load(kfirst + lane);
+        for (int kb = kfirst; kb < klast; kb += 32) {
+            const bool hit = !(r2.y < xlo_w || r2.x > xhi_w);  // (XMIN, XMAX) of column kb + lane
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            srec[warp][lane] = transform_record<RES>(r0, r1, r2, r3);
+            __syncwarp();
+            load(kb + 32 + lane);
+            ncol += __popc(m);
+            float acc[MAXGDS] = {0.f, 0.f, 0.f};
+            auto one = [&](int cidx) {
+                const RecF c = srec[warp][cidx];
+                const float v = pair_value<RES>(c, xc, dl, lp, lm, w0, w1);
+                acc[0] = fmaf(v, c.q2.x, acc[0]);
+                if (NDS > 1) acc[1] = fmaf(v, c.q2.y, acc[1]);
+                if (NDS > 2) acc[2] = fmaf(v, c.q2.z, acc[2]);
+            };
+            if (m == 0xffffffffu) {
+                // every column of the batch reaches the warp's bins: fixed trip count, two chains in flight
+#pragma unroll 2
+                for (int cidx = 0; cidx < 32; ++cidx) one(cidx);
+            } else {
+                while (m) {
+                    const int cidx = __ffs(m) - 1;
+                    m &= m - 1;
+                    one(cidx);
+                }
+            }
+#pragma unroll
+            for (int dd = 0; dd < NDS; ++dd) two_sum_acc(s[dd], cc[dd], acc[dd]);
+            __syncwarp();
+        }
+#pragma unroll
+        for (int dd = 0; dd < MAXGDS; ++dd) accd[dd] = (double)s[dd] + (double)cc[dd];
+    }
+    if (a.work) {
+        const unsigned m = __ballot_sync(0xffffffffu, valid);
+        if (lane == 0) atomicAdd(&a.work[K_FORWARD], (unsigned long long)ncol * __popc(m));
+    }
+    if (valid) {
+        double* out = a.mubuf + ((long long)t * a.nsplit + split) * a.total_bins;
+#pragma unroll
+        for (int dd = 0; dd < MAXGDS; ++dd)
+            if (dd < nds) out[a.ds_off[a.g_ds[g][dd]] + j] = accd[dd];
+    }
+}
+
+// ------------------------------------------------------------ backward -----
+// compensated warp sum of (s, c) pairs; result in every lane
+DEV float warp_sum_comp(float s, float c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, o);
+        const float co = __shfl_xor_sync(0xffffffffu, c, o);
+        const float tsum = s + so;
+        const float bp = tsum - s;
+        c = c + co + ((s - (tsum - bp)) + (so - bp));
+        s = tsum;
+    }
+    return s + c;
+}
+
+template <int RES, int NDS>
+__global__ void __launch_bounds__(256) k_backward_m(KArgs a) {
+    const int task = blockIdx.x, g = blockIdx.y, t = blockIdx.z;
+    const int W = a.bw_warps;
+    const int cbw = task / a.bw_bsplit, bsp = task % a.bw_bsplit;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kbase = cbw * W * 32;
+    const int k = kbase + warp * 32 + lane;
+    const bool kval = k < a.K;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* sbin = reinterpret_cast<float4*>(smem_raw);                      // [W][32][3]
+    float* su = reinterpret_cast<float*>(smem_raw + sizeof(float4) * 3 * 32 * W);   // [MAXGDS][W*32]
+    double* sresp = reinterpret_cast<double*>(smem_raw + sizeof(float4) * 3 * 32 * W + sizeof(float) * MAXGDS * W * 32);
+    const int nds = a.g_nds[g];
+    const int J = a.g_bins[g];
+    const double* ed = a.edges + a.g_edge_off[g];
+    const double* prm = a.params + (long long)t * a.params_stride;
+    const double LY = prm[a.g_resp[g][0]], rb = prm[a.g_resp[g][3]], rc = prm[a.g_resp[g][4]];
+    int wlo, whi;
+    toy_window_union(a, t, g, wlo, whi);
+
+    float c[NFP];
+    {
+        const float4* cr = reinterpret_cast<const float4*>(colrec<float>(a, t, g, kval ? k : a.K - 1));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 v = cr[i];
+            c[4 * i] = v.x; c[4 * i + 1] = v.y; c[4 * i + 2] = v.z; c[4 * i + 3] = v.w;
+        }
+    }
+    const float xmn = warp_min<float>(kval ? c[F_XMIN] : INFINITY);
+    const float xmx = warp_max<float>(kval ? c[F_XMAX] : -INFINITY);
+    int ja = 0, jb = -1;
+    if (xmx >= xmn) {
+        int lo = 0, hi = J;
+        while (lo < hi) { const int m = (lo + hi) >> 1; if (ed[m + 1] <= (double)xmn) lo = m + 1; else hi = m; }
+        ja = lo;
+        lo = 0; hi = J;
+        while (lo < hi) { const int m = (lo + hi) >> 1; if (ed[m] < (double)xmx) lo = m + 1; else hi = m; }
+        jb = lo - 1;
+        ja = max(ja, wlo); jb = min(jb, whi - 1);
+        const int len = jb - ja + 1;
+        if (len > 0) {
+            const int ch = (len + a.bw_bsplit - 1) / a.bw_bsplit;
+            const int na = ja + bsp * ch;
+            jb = min(jb, na + ch - 1);
+            ja = na;
+        }
+    }
+    const float* wrow = reinterpret_cast<const float*>(a.wbuf) + (long long)t * a.total_bins;
+    const float* wv0 = wrow + a.ds_off[a.g_ds[g][0]];
+    const float* wv1 = wrow + a.ds_off[a.g_ds[g][nds > 1 ? 1 : 0]];
+    const float* wv2 = wrow + a.ds_off[a.g_ds[g][nds > 2 ? 2 : 0]];
+    const float TN0 = c[F_TN0], TN1 = NDS > 1 ? c[F_TN0 + 1] : 0.f, TN2 = NDS > 2 ? c[F_TN0 + 2] : 0.f;
+    // accumulators: U0 per dataset (rates), U1/U2 (gamma: d/dmu at fixed variance, d/dvar at fixed mean,
+    // scaled by mu/d and s^2; gauss: z- and (z^2-1)-weighted sums)
+    float sU[5] = {0, 0, 0, 0, 0}, cU[5] = {0, 0, 0, 0, 0};
+    const float A = c[F_A];
+    const float P2 = L2E * c[F_B], Q2 = fmaf(L2E, c[F_B], -L2E), R2 = L2E * c[F_C];
+    const float kap = c[F_KAPPA];
+    const float Ag = A * SQ_HALF_L2E;
+    const int jlin = a.g_jlin[g];
+    const int nbase = a.g_node_off[g];
+
+    // bins of the general node table, one at a time
+    for (int j = ja; j <= min(jb, jlin - 1); ++j) {
+        const float w[MAXGDS] = {wv0[j], NDS > 1 ? wv1[j] : 0.f, NDS > 2 ? wv2[j] : 0.f};
+        const float Wj = fmaf(w[0], TN0, fmaf(w[1], TN1, w[2] * TN2));
+        const unsigned char cls = a.bclass[nbase + j];
+        float rho = 0.f, u1 = 0.f, u2 = 0.f;
+        if (RES == 1 && cls == BIN_ZERO) {
+            rho = c[F_P0]; u1 = c[F_P0D]; u2 = c[F_P0S];
+        } else {
+            const float* nd = a.ntab_f + (long long)(nbase + j) * 3 * NGM_F;
+            const float Dx = (a.xc_f[nbase + j] - c[F_MUH]) - c[F_MUL];
+            const int NG = cls == BIN_LOG ? NG_LOG_F : NG_LIN_F;
+            if (RES == 1) {
+                const float tt = Dx * A;
+                float L1;
+                const float Dt = log1pmx2_f(tt, L1);
+                const float Ec = fmaf(P2, Dt, -L2E * L1);
+                for (int n = 0; n < NG; ++n) {
+                    const float fw = nd[2 * NGM_F + n] * ex2f(Ec + fmaf(R2, nd[n], Q2 * nd[NGM_F + n]));
+                    const float L1n = L1 + nd[NGM_F + n];
+                    const float tn = fmaf(nd[n], A, tt);
+                    rho += fw;
+                    u1 = fmaf(fw, fmaf(2.0f, L1n + kap, -tn), u1);
+                    u2 = fmaf(fw, -((L1n - tn) + kap), u2);
+                }
+            } else {
+                const float z = Dx * A;
+                for (int n = 0; n < NG; ++n) {
+                    const float zn = fmaf(nd[n], A, z);
+                    const float fw = nd[2 * NGM_F + n] * ex2f(-0.5f * L2E * zn * zn);
+                    rho += fw; u1 = fmaf(fw, zn, u1); u2 = fmaf(fw, fmaf(zn, zn, -1.0f), u2);
+                }
+            }
+        }
+        two_sum_acc(sU[3], cU[3], Wj * u1);
+        two_sum_acc(sU[4], cU[4], Wj * u2);
+#pragma unroll
+        for (int dd = 0; dd < MAXGDS; ++dd) two_sum_acc(sU[dd], cU[dd], w[dd] * rho);
+    }
+
+    // linear bins in batches of 32, staged per warp
+    const int jstart = max(ja, jlin);
+    float4 b0 = make_float4(0, 0, 0, 0), b1 = b0, b2 = b0;
+    auto load = [&](int jj) {
+        if (jj <= jb) {
+            const float4* bt = reinterpret_cast<const float4*>(a.btab_f) + 2 * (long long)(nbase + jj);
+            b0 = bt[0];
+            const float4 x = bt[1];
+            b1 = make_float4(x.x, x.y, wv0[jj], NDS > 1 ? wv1[jj] : 0.f);
+            if (NDS > 2) b2 = make_float4(wv2[jj], 0.f, 0.f, 0.f);
+        }
+    };
+    load(jstart + lane);
+    float4* my = sbin + (long long)warp * 32 * 3;
+    for (int jj0 = jstart; jj0 <= jb; jj0 += 32) {
+        my[lane * 3 + 0] = b0; my[lane * 3 + 1] = b1;
+        if (NDS > 2) my[lane * 3 + 2] = b2;
+        __syncwarp();
+        load(jj0 + 32 + lane);
+        const int nbat = min(32, jb - jj0 + 1);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll 2
+        for (int i = 0; i < nbat; ++i) {
+            const float4 q0 = my[i * 3], q1 = my[i * 3 + 1];
+            const float wd2 = NDS > 2 ? my[i * 3 + 2].x : 0.f;
+            const float xc = q0.x, dl = q0.y, lp = q0.z, lm = q0.w;
+            const float w0 = q1.x, w1 = q1.y, wd0 = q1.z, wd1 = q1.w;
+            const float Wj = fmaf(wd0, TN0, fmaf(wd1, TN1, wd2 * TN2));
+            const float Dx = (xc - c[F_MUH]) - c[F_MUL];
+            float rho, u1, u2;
+            if (RES == 1) {
+                const float tt = Dx * A;
+                float L1;
+                const float Dt = log1pmx2_f(tt, L1);
+                const float Ec = fmaf(P2, Dt, -L2E * L1);
+                const float cd = R2 * dl;
+                const float e0 = w0 * ex2f(Ec);
+                const float ep = w1 * ex2f(fmaf(Q2, lp, Ec) + cd);
+                const float em = w1 * ex2f(fmaf(Q2, lm, Ec) - cd);
+                rho = e0 + ep + em;
+                const float Ls = fmaf(ep, lp, em * lm);           // sum w f ln(x_n / x_c)
+                const float XA = (ep - em) * (dl * A);             // sum w f (x_n - x_c) / mu
+                const float cmu = fmaf(2.0f, L1 + kap, -tt);
+                u1 = fmaf(cmu, rho, fmaf(2.0f, Ls, -XA));
+                u2 = fmaf(-(Dt + kap), rho, XA - Ls);
+            } else {
+                const float z = Dx * A;
+                const float dz = dl * A;
+                const float zp = z + dz, zm = z - dz;
+                const float zg = Dx * Ag, dzg = dl * Ag;
+                const float zgp = zg + dzg, zgm = zg - dzg;
+                const float e0 = w0 * ex2f(-zg * zg);
+                const float ep = w1 * ex2f(-zgp * zgp);
+                const float em = w1 * ex2f(-zgm * zgm);
+                rho = e0 + ep + em;
+                u1 = fmaf(e0, z, fmaf(ep, zp, em * zm));
+                u2 = fmaf(e0, fmaf(z, z, -1.0f), fmaf(ep, fmaf(zp, zp, -1.0f), em * fmaf(zm, zm, -1.0f)));
+            }
+            a0 = fmaf(wd0, rho, a0);
+            if (NDS > 1) a1 = fmaf(wd1, rho, a1);
+            if (NDS > 2) a2 = fmaf(wd2, rho, a2);
+            a3 = fmaf(Wj, u1, a3);
+            a4 = fmaf(Wj, u2, a4);
+        }
+        two_sum_acc(sU[0], cU[0], a0);
+        if (NDS > 1) two_sum_acc(sU[1], cU[1], a1);
+        if (NDS > 2) two_sum_acc(sU[2], cU[2], a2);
+        two_sum_acc(sU[3], cU[3], a3);
+        two_sum_acc(sU[4], cU[4], a4);
+        __syncwarp();
+    }
+    if (a.work) {
+        const unsigned m = __ballot_sync(0xffffffffu, kval);
+        if (lane == 0 && jb >= ja) atomicAdd(&a.work[K_BACKWARD], (unsigned long long)(jb - ja + 1) * __popc(m));
+    }
+    // chain rule per column: mean and variance derivatives to (LY, kB, a, b, c)
+    float r[NRESP] = {0, 0, 0, 0, 0}, rc_[NRESP] = {0, 0, 0, 0, 0};
+    if (kval) {
+        const float U1 = sU[3] + cU[3], U2 = sU[4] + cU[4];
+        const float mu = c[F_MUH] + c[F_MUL];
+        float g_mu, g_var;
+        if (RES == 1) {
+            g_mu = U1 * (c[F_B] * A);          // (d / mu) U1
+            g_var = U2 * (c[F_C] * c[F_C]);    // U2 / s^2
+        } else {
+            g_mu = U1 * A;
+            g_var = 0.5f * U2 * A * A;
+        }
+        const float g_mt = fmaf(g_var, (float)rb + 2.0f * (float)rc * mu, g_mu);
+        r[0] = g_mt * (mu / (float)LY);
+        r[1] = g_mt * (float)LY * c[F_DEQ];
+        r[2] = g_var;
+        r[3] = g_var * mu;
+        r[4] = g_var * mu * mu;
+    }
+#pragma unroll
+    for (int i = 0; i < NRESP; ++i) {
+        const float v = warp_sum_comp(r[i], rc_[i]);
+        if (lane == 0) sresp[warp * NRESP + i] = (double)v;
+    }
+    for (int dd = 0; dd < MAXGDS; ++dd)
+        su[dd * W * 32 + warp * 32 + lane] = kval ? (sU[dd] + cU[dd]) * c[F_N] : 0.f;
+    __syncthreads();
+    double* part = a.partbuf + (((long long)t * a.G + g) * a.nbtask + task) * a.NPART;
+    if (threadIdx.x < NRESP) {
+        double s = 0.0;
+        for (int w = 0; w < W; ++w) s += sresp[w * NRESP + threadIdx.x];
+        part[threadIdx.x] = s;
+    }
+    const int ncol = min(W * 32, a.K - kbase);
+    for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
+        const int dd = i / a.S, s = i % a.S;
+        double v = 0.0;
+        if (dd < nds && a.sp_kind[s] != 2 && ((a.sp_mask[s] >> a.g_ds[g][dd]) & 1u)) {
+            const float* Srow = a.Sf + (long long)s * a.K + kbase;
+            float acc = 0.f, cmp = 0.f, part32 = 0.f;
+            for (int cc = 0; cc < ncol; ++cc) {
+                part32 = fmaf(Srow[cc], su[dd * W * 32 + cc], part32);
+                if ((cc & 31) == 31) { two_sum_acc(acc, cmp, part32); part32 = 0.f; }
+            }
+            two_sum_acc(acc, cmp, part32);
+            v = (double)acc + (double)cmp;
+        }
+        part[NRESP + i] = v;
+    }
+}
+
+template <int RES>
+static cudaError_t launch_fwd(const KArgs& a, cudaStream_t st, int nds) {
+    dim3 grid(a.ntile, a.nsplit, a.T * a.G);
+    if (nds == 1) k_forward_m<RES, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    else if (nds == 2) k_forward_m<RES, 2><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    else k_forward_m<RES, 3><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int RES>
+static cudaError_t launch_bwd(const KArgs& a, cudaStream_t st, int nds) {
+    dim3 grid(a.nbtask, a.G, a.T);
+    const int threads = a.bw_warps * 32;
+    const size_t sm = sizeof(float4) * 3 * threads + sizeof(float) * MAXGDS * threads + sizeof(double) * a.bw_warps * NRESP;
+    if (nds == 1) k_backward_m<RES, 1><<<grid, threads, sm, st>>>(a);
+    else if (nds == 2) k_backward_m<RES, 2><<<grid, threads, sm, st>>>(a);
+    else k_backward_m<RES, 3><<<grid, threads, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+static int max_group_datasets(const KArgs& a) {
+    int m = 1;
+    for (int g = 0; g < a.G; ++g) m = a.g_nds[g] > m ? a.g_nds[g] : m;
+    return m;
+}
+
+cudaError_t launch_forward_mixed(const KArgs& a, cudaStream_t st) {
+    const int nds = max_group_datasets(a);
+    return a.res == 0 ? launch_fwd<0>(a, st, nds) : launch_fwd<1>(a, st, nds);
+}
+
+cudaError_t launch_backward_mixed(const KArgs& a, cudaStream_t st) {
+    const int nds = max_group_datasets(a);
+    return a.res == 0 ? launch_bwd<0>(a, st, nds) : launch_bwd<1>(a, st, nds);
+}
+
+}  // namespace gsn
