@@ -133,6 +133,7 @@ int gsn_set_data(gsn_ctx* ctx, int n_datasets, const int* n_bins, const double* 
  *   shift          [n_species] AnaShift offset [MeV], rounded to whole fine
  *                  bins (NULL = no shifts)
  *   dataset_mask   [n_species][n_datasets] 1 where the species contributes
+ *                  (at most 8 AnaPeak species per dataset)
  * Requires gsn_set_data first (for n_datasets). */
 int gsn_set_species(gsn_ctx* ctx, int n_species, int n_fine, const double* fine_centres,
                     const double* spectra, const int* kind, const double* shift,

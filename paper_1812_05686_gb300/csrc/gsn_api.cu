@@ -619,6 +619,11 @@ int gsn_set_species(gsn_ctx* c, int n_species, int n_fine, const double* fine_ce
             if (src >= 0 && src < n_fine) Sn[(size_t)s * n_fine + k] = spectra[(size_t)s * n_fine + src] / tot;
         }
     }
+    for (int d = 0; d < c->D; ++d) {
+        int np = 0;
+        for (int s = 0; s < n_species; ++s) np += (kd[s] == GSN_ANA_PEAK && dataset_mask[(size_t)s * c->D + d]) ? 1 : 0;
+        if (np > 8) return fail(c, GSN_ERR_ARG, "at most 8 AnaPeak species per dataset");
+    }
     c->S = n_species; c->K = n_fine; c->E = E; c->Sn = Sn; c->kind = kd;
     c->mask.assign(dataset_mask, dataset_mask + (size_t)n_species * c->D);
     c->have_species = true;

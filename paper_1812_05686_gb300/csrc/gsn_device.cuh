@@ -25,7 +25,9 @@ DEV float ex2f(float x) {  // 2^x on the SFU
 // terms cancel: D = -t u + 2 u^3 (1/3 + u^2/5 + u^4/7 + ...).
 DEV float log1pmx_f(float t) {
     if (t >= -0.5f && t <= 1.0f) {
-        float u = __fdividef(t, 2.0f + t);
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(2.0f + t));
+        const float u = t * r;
         float v = u * u;
         float p = fmaf(v, 1.0f / 15.0f, 1.0f / 13.0f);
         p = fmaf(p, v, 1.0f / 11.0f);
@@ -37,6 +39,22 @@ DEV float log1pmx_f(float t) {
     }
     return log1pf(t) - t;
 }
+// D(t) without the range test, for callers that know |t/(2+t)| <= 1/3 wherever the result
+// matters: the same series, evaluated branch-free (2 D = -2 t u + u^3 (2/3 + 2 u^2/5 + ...))
+DEV float log1pmx_poly(float t) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(2.0f + t));
+    const float u = t * r;
+    const float v = u * u;
+    float p = fmaf(v, 2.0f / 15.0f, 2.0f / 13.0f);
+    p = fmaf(p, v, 2.0f / 11.0f);
+    p = fmaf(p, v, 2.0f / 9.0f);
+    p = fmaf(p, v, 2.0f / 7.0f);
+    p = fmaf(p, v, 2.0f / 5.0f);
+    p = fmaf(p, v, 2.0f / 3.0f);
+    return fmaf(u * v, p, -t * u);
+}
+
 // D(t) and L1 = ln(1 + t) together; L1 directly from log1p where |t| is large
 DEV float log1pmx2_f(float t, float& L1) {
     if (t >= -0.5f && t <= 1.0f) {

@@ -360,15 +360,51 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_gauss64(KArgs a) {
 }
 
 // ------------------------------------------------------------ deviance -----
+// bins [lo, hi) of edges ed[0..J] whose content of N(x; m, w) exceeds exp(-cut) of its peak density
+DEV void peak_bins(const double* ed, int J, double m, double w, double cut, int& lo, int& hi) {
+    const double z = sqrt(2.0 * cut);
+    const double xa = m - z * w, xb = m + z * w;
+    int l = 0, h = J;
+    while (l < h) { const int q = (l + h) >> 1; if (ed[q + 1] <= xa) l = q + 1; else h = q; }
+    lo = l;
+    l = 0; h = J;
+    while (l < h) { const int q = (l + h) >> 1; if (ed[q] < xb) l = q + 1; else h = q; }
+    hi = l;
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
     const int t = blockIdx.x;
+    constexpr int MAXPK = 8;
     __shared__ double sh[32];
+    __shared__ int spk_s[MAXD][MAXPK], spk_lo[MAXD][MAXPK], spk_hi[MAXD][MAXPK];
+    __shared__ double spk_r[MAXD][MAXPK], spk_m[MAXD][MAXPK], spk_w[MAXD][MAXPK];
+    __shared__ int snpk[MAXD];
     const double* prm = a.params + (long long)t * a.params_stride;
     const double* cnt = a.counts + (long long)t * a.counts_stride;
     R* wout = reinterpret_cast<R*>(a.wbuf) + (long long)t * a.total_bins;
     double* gdir = a.gdirect + (long long)t * a.P;
     for (int p = threadIdx.x; p < a.P; p += blockDim.x) gdir[p] = 0.0;
+    // AnaPeak species of each dataset, with the bins their profile reaches
+    if (threadIdx.x < a.D) {
+        const int d = threadIdx.x;
+        const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
+        int np = 0;
+        for (int s = 0; s < a.S && np < MAXPK; ++s) {
+            if (a.sp_kind[s] != 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
+            const int pr = a.slot_map[d * a.NSLOT + s];
+            spk_s[d][np] = s;
+            spk_r[d][np] = pr >= 0 ? prm[pr] : 0.0;
+            spk_m[d][np] = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
+            spk_w[d][np] = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
+            int lo, hi;
+            peak_bins(ed, a.ds_bins[d], spk_m[d][np], spk_w[d][np], a.cut, lo, hi);
+            spk_lo[d][np] = lo; spk_hi[d][np] = hi;
+            ++np;
+        }
+        snpk[d] = np;
+    }
+    __syncthreads();
     double part = 0.0;
     int bad_mu = 0, bad_fin = 0;
     for (int d = 0; d < a.D; ++d) {
@@ -382,13 +418,10 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
             if (j >= lo && j < hi) {
                 double mu = 0.0;
                 for (int s = 0; s < a.nsplit; ++s) mu += a.mubuf[((long long)t * a.nsplit + s) * a.total_bins + off + j];
-                for (int s = 0; s < a.S; ++s) {
-                    if (a.sp_kind[s] != 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
-                    const int pr = a.slot_map[d * a.NSLOT + s];
-                    const double r = pr >= 0 ? prm[pr] : 0.0;
-                    const double m = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
-                    const double wd = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
-                    mu += eps * r * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
+                for (int q = 0; q < snpk[d]; ++q) {
+                    if (j < spk_lo[d][q] || j >= spk_hi[d][q]) continue;
+                    const double m = spk_m[d][q], wd = spk_w[d][q];
+                    mu += eps * spk_r[d][q] * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
                 }
                 const double n = cnt[off + j];
                 double term;
@@ -407,21 +440,21 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
     }
     double nll = block_sum_d(part, sh);
     const int any_bad_mu = __syncthreads_or(bad_mu), any_bad_fin = __syncthreads_or(bad_fin);
-    // AnaPeak gradient terms: rate, position, width (closed form per bin)
+    // AnaPeak gradient terms: rate, position, width (closed form per bin of the peak's band)
     if (a.want_grad) {
         __syncthreads();  // wout visible to the block
         for (int d = 0; d < a.D; ++d) {
-            const int J = a.ds_bins[d], off = a.ds_off[d];
+            const int off = a.ds_off[d];
             const double eps = a.ds_eps[d];
             const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
-            for (int s = 0; s < a.S; ++s) {
-                if (a.sp_kind[s] != 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
+            for (int q = 0; q < snpk[d]; ++q) {
+                const int s = spk_s[d][q];
                 const int pr = a.slot_map[d * a.NSLOT + s];
                 const int pm = a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s];
                 const int pw = a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s];
-                const double r = pr >= 0 ? prm[pr] : 0.0, m = prm[pm], wd = prm[pw];
+                const double r = spk_r[d][q], m = spk_m[d][q], wd = spk_w[d][q];
                 double gr = 0.0, gm = 0.0, gw = 0.0;
-                for (int j = threadIdx.x; j < J; j += blockDim.x) {
+                for (int j = spk_lo[d][q] + threadIdx.x; j < spk_hi[d][q]; j += blockDim.x) {
                     const double wj = (double)wout[off + j];
                     if (wj == 0.0) continue;
                     const double z0 = (ed[j] - m) / wd, z1 = (ed[j + 1] - m) / wd;
