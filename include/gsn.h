@@ -47,6 +47,7 @@ extern "C" {
 #define GSN_ERR_NONFINITE        -4  /* a parameter, mu or the NLL is not finite */
 #define GSN_ERR_STATE            -5  /* set_data / set_species / set_params missing */
 #define GSN_ERR_NOMEM            -6  /* device allocation failed */
+#define GSN_ERR_TIMEOUT          -7  /* a bounded wait inside a kernel gave up (results not written) */
 
 /* precision of the response build and contraction (the deviance and the
  * NLL reduction are FP64 in both modes) */

@@ -61,6 +61,10 @@ struct gsn_ctx {
     double prof_ms[K_COUNT] = {0};
     long long prof_n[K_COUNT] = {0};
     Buf work;  // unsigned long long[K_COUNT] on the device
+    // tensor-core per-species contraction (mixed): TF32 hi / lo split of S' and their TMA maps
+    Buf s_hi, s_lo, tc_part, tc_err;
+    alignas(64) unsigned char tm_hi[128], tm_lo[128];
+    bool tc_ready = false;
 };
 
 namespace {
@@ -155,6 +159,7 @@ int finalize(gsn_ctx* c) {
         return fail(c, GSN_ERR_STATE, "gsn_set_data, gsn_set_species and gsn_set_params must all be called");
     free_owned(c);
     c->cache_valid = false;
+    c->tc_ready = false;
     const bool mixed = c->opt.precision == GSN_MIXED;
     const bool gamma = c->opt.resolution == GSN_RES_GAMMA;
     const int NSLOT = gsn_n_slots(c->S);
@@ -490,7 +495,8 @@ void gsn_destroy(gsn_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_owned(c);
     for (Buf* b : {&c->colbuf, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->params, &c->counts_b,
-                   &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf})
+                   &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf, &c->s_hi, &c->s_lo,
+                   &c->tc_part, &c->tc_err})
         if (b->p) cudaFree(b->p);
     if (c->work.p) cudaFree(c->work.p);
     for (auto& p : c->pending) { c->event_pool.push_back(p.e0); c->event_pool.push_back(p.e1); }
@@ -688,6 +694,41 @@ int gsn_eval_grad(gsn_ctx* c, const double* params, double* nll, double* grad) {
     return status_message(c, st, 0);
 }
 
+// round to the nearest TF32 value (10 explicit mantissa bits, ties to even)
+static float tf32_round(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    b = (b + 0xFFFu + ((b >> 13) & 1u)) & ~0x1FFFu;
+    float y;
+    std::memcpy(&y, &b, 4);
+    return y;
+}
+
+// TF32 hi / lo split of S' (rows padded to 16 species, columns to 32) and the TMA maps over them
+static int prepare_tensor_core(gsn_ctx* c) {
+    if (c->tc_ready) return GSN_OK;
+    const int Spad = (c->S + 15) / 16 * 16, Kpad = (c->K + 31) / 32 * 32;
+    std::vector<float> hi((size_t)Spad * Kpad, 0.f), lo((size_t)Spad * Kpad, 0.f);
+    for (int s = 0; s < c->S; ++s)
+        for (int k = 0; k < c->K; ++k) {
+            const float v = (float)c->Sn[(size_t)s * c->K + k];
+            const float h = tf32_round(v);
+            hi[(size_t)s * Kpad + k] = h;
+            lo[(size_t)s * Kpad + k] = v - h;
+        }
+    int rc;
+    if ((rc = ensure(c, c->s_hi, hi.size() * sizeof(float)))) return rc;
+    if ((rc = ensure(c, c->s_lo, lo.size() * sizeof(float)))) return rc;
+    CUDA_TRY(c, cudaMemcpy(c->s_hi.p, hi.data(), hi.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->s_lo.p, lo.data(), lo.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (make_species_tensor_map(c->tm_hi, (const float*)c->s_hi.p, Spad, Kpad) ||
+        make_species_tensor_map(c->tm_lo, (const float*)c->s_lo.p, Spad, Kpad))
+        return fail(c, GSN_ERR_CUDA, "cuTensorMapEncodeTiled failed for the species tiles");
+    if ((rc = ensure(c, c->tc_err, sizeof(int)))) return rc;
+    c->tc_ready = true;
+    return GSN_OK;
+}
+
 // per-species expected shapes M[g][s][j] at the response parameters of params (T = 1)
 static int compute_species(gsn_ctx* c, const double* params_dev) {
     int rc;
@@ -700,7 +741,31 @@ static int compute_species(gsn_ctx* c, const double* params_dev) {
     a.Mbuf = (double*)c->Mbuf.p;
     a.sp_first = 0; a.sp_count = c->S;
     if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
-    if ((rc = launch(c, K_SPECIES, a, launch_species))) return rc;
+    if (c->opt.precision == GSN_MIXED) {
+        if ((rc = prepare_tensor_core(c))) return rc;
+        const int tiles = (c->Jmax + 127) / 128 * c->G * ((c->S + 15) / 16);
+        a.tc_nsplit = std::max(1, std::min(64, (3 * c->nsm + tiles - 1) / tiles));
+        if ((rc = ensure(c, c->tc_part, (size_t)a.tc_nsplit * c->G * c->S * c->Jmax * sizeof(double)))) return rc;
+        a.tc_part = (double*)c->tc_part.p;
+        a.tc_error = (int*)c->tc_err.p;
+        CUDA_TRY(c, cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+        auto fn = [c](const KArgs& x, cudaStream_t st) { return launch_species_tc(x, c->tm_hi, c->tm_lo, st); };
+        if ((rc = launch(c, K_SPECIES, a, fn))) return rc;
+    } else {
+        if ((rc = launch(c, K_SPECIES, a, launch_species))) return rc;
+    }
+    return GSN_OK;
+}
+
+// GSN_ERR_TIMEOUT if a tensor-core CTA gave up waiting (call after the stream is synchronised)
+static int species_status(gsn_ctx* c) {
+    if (c->opt.precision != GSN_MIXED || !c->tc_err.p) return GSN_OK;
+    int e = 0;
+    CUDA_TRY(c, cudaMemcpy(&e, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        c->cache_valid = false;
+        return fail(c, GSN_ERR_TIMEOUT, "a tensor-core wait timed out in the per-species contraction");
+    }
     return GSN_OK;
 }
 
@@ -739,6 +804,7 @@ int gsn_eval(gsn_ctx* c, const double* params, double* nll) {
     CUDA_TRY(c, cudaMemcpyAsync(nll, c->nll_b.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(&st, c->status_b.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (!hit && (rc = species_status(c))) return rc;
     return status_message(c, st, 0);
 }
 
@@ -763,7 +829,7 @@ int gsn_expected(gsn_ctx* c, const double* params, int dataset, double* mu_per_s
     if ((rc = launch(c, K_SPECIES, a, launch_expected_out))) return rc;
     CUDA_TRY(c, cudaMemcpyAsync(mu_per_species, c->outbuf.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    return GSN_OK;
+    return species_status(c);
 }
 
 int gsn_eval_grad_batch_dev(gsn_ctx* c, int n_toys, const double* params_dev, const double* toy_counts_dev,

@@ -98,6 +98,10 @@ struct KArgs {
     int out_dataset;
     // statistics: evaluated (bin, column) pairs per kernel class (NULL = off)
     unsigned long long* work;
+    // tensor-core per-species contraction
+    int tc_nsplit;         // column ranges per bin tile
+    double* tc_part;       // [tc_nsplit][G][S][Jmax] partial sums
+    int* tc_error;         // set to 1 by a CTA whose bounded wait timed out
 };
 
 // launchers (gsn_kernels.cu); return cudaError_t of the launches
@@ -111,6 +115,9 @@ cudaError_t launch_mu_from_species(const KArgs& a, cudaStream_t st);
 cudaError_t launch_expected_out(const KArgs& a, cudaStream_t st);
 cudaError_t run_probe(int which, int nsm, double* ops_per_second);
 cudaError_t launch_forward_mixed(const KArgs& a, cudaStream_t st);
+size_t species_tc_smem_bytes();
+cudaError_t launch_species_tc(const KArgs& a, const void* tm_hi, const void* tm_lo, cudaStream_t st);
+int make_species_tensor_map(void* out, const float* dev, int rows, int cols_pad);
 cudaError_t launch_backward_mixed(const KArgs& a, cudaStream_t st);
 
 constexpr int K_COLUMNS = 0, K_FORWARD = 1, K_DEVIANCE = 2, K_BACKWARD = 3, K_GRADFINAL = 4,
