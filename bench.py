@@ -35,11 +35,14 @@ UNIT = "evals/s"
 WORKLOAD = "borexino_like toys: 2 datasets x 1200-bin domain, 16 species x 20000 fine points, gamma response, 23 params"
 
 # Algorithmic FP32 floating-point operations per evaluated (bin, column) pair of
-# the mixed generalized-gamma kernels (FMA = 2, SFU exponential = 1), counted from
-# the arithmetic each pair needs: window offset and t (3), ln(1+t)-t (21),
-# ln(1+t) (1), centre exponent (3), 3 Gauss-Legendre nodes (forward 7 each,
-# adjoint 11 each), contraction with 2 datasets (forward 4; adjoint 4 + 12).
-FLOP_PER_PAIR = {"forward": 53, "backward": 78}
+# the mixed generalized-gamma kernels on their branch-free path (shape d >= 50,
+# 94% of the columns), FMA = 2, SFU reciprocal / exponential = 1:
+#   forward  44 = offset and t (3) + ln(1+t)-t series (20) + centre exponent (3)
+#                 + 3 Gauss-Legendre nodes and their weighted sum (14) + 2-dataset contraction (4)
+#   backward 70 = dataset weight (3) + offset and t (3) + series (20) + ln(1+t) (1) + exponent (3)
+#                 + nodes (15) + value / ln / offset-weighted sums (8) + mean / variance
+#                 coefficients (11) + four accumulations (8)
+FLOP_PER_PAIR = {"forward": 44, "backward": 70}
 FP32_LANES_PER_SM = 128
 
 

@@ -88,13 +88,14 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
     __shared__ RecF srec[FWD_WARPS][32];
     int wlo, whi;
     toy_window_union(a, t, g, wlo, whi);
-    const int j0 = (tile * FWD_WARPS + warp) * 32;
-    if (j0 >= whi || j0 + 32 <= wlo) return;
+    // warps tile the toy's window from its first bin, so no warp starts outside it
+    const int j0 = wlo + (tile * FWD_WARPS + warp) * 32;
+    if (j0 >= whi) return;
     const int j = j0 + lane;
-    const bool valid = j >= wlo && j < whi;
-    const int jr = min(max(j, wlo), whi - 1);
+    const bool valid = j < whi;
+    const int jr = min(j, whi - 1);
     const int nb = a.g_node_off[g] + jr;
-    const int jf = max(j0, wlo), jl = min(j0 + 31, whi - 1);
+    const int jf = j0, jl = min(j0 + 31, whi - 1);
     const float xlo_w = (float)a.edges[a.g_edge_off[g] + jf];
     const float xhi_w = (float)a.edges[a.g_edge_off[g] + jl + 1];
     const int nds = a.g_nds[g];
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
 
     double accd[MAXGDS] = {0.0, 0.0, 0.0};
     int ncol = 0;
-    if (j0 < a.g_jlin[g]) {
+    if (j0 < a.g_jlin[g]) {  // the warp holds bins below the first linear bin
         // warp holds bins of the general node table (log-spaced or the bin at zero)
         const unsigned char cls = a.bclass[nb];
         const float* nodes = a.ntab_f + (long long)nb * 3 * NGM_F;
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
                 if (NDS > 2) acc[2] = fmaf(v, c.q2.z, acc[2]);
             };
             if (m == 0xffffffffu && poly) {
-                // dense batch of wide columns: branch-free evaluation, two chains in flight
-#pragma unroll 2
+                // dense batch of wide columns: branch-free evaluation, several chains in flight
+#pragma unroll 4
                 for (int cidx = 0; cidx < 32; ++cidx) {
                     const RecF c = srec[warp][cidx];
                     const float v = pair_value_poly(c, xc, dl, lp, lm, w0, w1);
@@ -350,14 +351,7 @@ __global__ void __launch_bounds__(256) k_backward_m(KArgs a) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
 #pragma unroll 2
         for (int i = 0; i < nbat; ++i) {
-            if (i == 8 || i == 16 || i == 24) {
-                // fold the partial sums every 8 bins (bounds the FP32 error of the plain sums)
-                two_sum_acc(sU[0], cU[0], a0); a0 = 0.f;
-                if (NDS > 1) { two_sum_acc(sU[1], cU[1], a1); a1 = 0.f; }
-                if (NDS > 2) { two_sum_acc(sU[2], cU[2], a2); a2 = 0.f; }
-                two_sum_acc(sU[3], cU[3], a3); a3 = 0.f;
-                two_sum_acc(sU[4], cU[4], a4); a4 = 0.f;
-            }
+
             const float4 q0 = my[i * 3], q1 = my[i * 3 + 1];
             const float wd2 = NDS > 2 ? my[i * 3 + 2].x : 0.f;
             const float xc = q0.x, dl = q0.y, lp = q0.z, lm = q0.w;
