@@ -15,19 +15,9 @@ constexpr int FWD_WARPS = 8;
 
 // ------------------------------------------------------------------ math --
 DEV float ex2f(float x) {  // 2^x on the SFU
-#ifdef GSN_EXP2_SOFTWARE
-    if (x < -126.0f) return 0.0f;
-    const float n = rintf(x);
-    const float g = (x - n) * 0.693147180559945f;
-    float p = 1.0f / 5040.0f;
-    p = fmaf(p, g, 1.0f / 720.0f); p = fmaf(p, g, 1.0f / 120.0f); p = fmaf(p, g, 1.0f / 24.0f);
-    p = fmaf(p, g, 1.0f / 6.0f); p = fmaf(p, g, 0.5f); p = fmaf(p, g, 1.0f); p = fmaf(p, g, 1.0f);
-    return p * __int_as_float(((int)n + 127) << 23);
-#else
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-#endif
 }
 
 // D(t) = ln(1 + t) - t with relative precision: for t in [-1/2, 1] from the

@@ -275,6 +275,8 @@ __global__ void __launch_bounds__(TC_ROWS) k_species_tc(const __grid_constant__ 
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    if (a.work && tid == 0 && c_end > c_beg)
+        atomicAdd(&a.work[K_SPECIES], (unsigned long long)min(TC_ROWS, J - j0) * (unsigned long long)(c_end - c_beg) * TC_KC);
     if (valid && ok) {
         double* out = a.tc_part + ((long long)split * a.G + g) * (long long)a.S * a.Jmax;
         for (int i = 0; i < TC_N && sp0 + i < a.S; ++i)
