@@ -126,19 +126,60 @@ def ncu_traffic(kernel):
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    m = re.search(r"csrc_sha256:\s*([0-9a-f]+)", txt)
+    m = re.search(r"kernel_sources_sha256:\s*([0-9a-f]+)", txt)
     t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
     if not (m and t):
         return None
-    return float(t.group(1)) if m.group(1) == csrc_sha() else None
+    return float(t.group(1)) if m.group(1) == kernel_sha() else None
 
 
-def csrc_sha():
+KERNEL_SOURCES = ("gsn_mixed.cu", "gsn_device.cuh", "gsn_internal.cuh")
+
+
+def kernel_sha():
+    """Hash of the sources of the mixed-precision forward and adjoint kernels."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1812_05686_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------ gradient scale -----
+def fisher_diagonal(ctx64, w, theta):
+    """F_ii = sum_dj (d mu_dj / d theta_i)^2 / mu_dj at theta over the whole histograms.
+
+    The statistical scale of each gradient component: sqrt(F_ii) is the spread of dNLL/dtheta_i
+    from Poisson fluctuations of the counts.  Derivatives by central differences of the FP64
+    GPU path's expected counts (gsn_expected), steps 1e-4 relative.
+    """
+    import numpy as np
+    D = len(w["edges"])
+    mu = [ctx64.expected(theta, d).sum(axis=1) for d in range(D)]
+    F = np.zeros(len(theta))
+    for i in range(len(theta)):
+        h = 1e-4 * max(abs(theta[i]), 1e-6)
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        for d in range(D):
+            dm = (ctx64.expected(tp, d).sum(axis=1) - ctx64.expected(tm, d).sum(axis=1)) / (2 * h)
+            ok = mu[d] > 0
+            F[i] += float(np.sum(dm[ok] ** 2 / mu[d][ok]))
+    return F
+
+
+def gradient_errors(gm, g64, F):
+    """Mixed-vs-FP64 gradient errors per toy: normwise and per component on the Fisher scale."""
+    import numpy as np
+    norm = np.max(np.abs(gm - g64), axis=1) / np.maximum(np.max(np.abs(g64), axis=1), 1.0)
+    fish = np.max(np.abs(gm - g64) / (np.abs(g64) + np.sqrt(F)[None, :]), axis=1)
+    return {"normwise_max": float(norm.max()), "normwise_median": float(np.median(norm)),
+            "normwise_p99": float(np.percentile(norm, 99)), "toys_normwise_above_1e-5": int(np.sum(norm >= 1e-5)),
+            "fisher_scaled_max": float(fish.max()), "fisher_scaled_median": float(np.median(fish)),
+            "toys_fisher_scaled_above_1e-5": int(np.sum(fish >= 1e-5)),
+            "definition": "normwise: ||g - g64||_inf / max(||g64||_inf, 1); fisher_scaled: "
+                          "max_i |g_i - g64_i| / (|g64_i| + sqrt(F_ii)), F the Fisher diagonal at theta0"}
 
 
 # ------------------------------------------------------------- oracle ------
@@ -266,7 +307,19 @@ def run_ours(args, rank, world, local_rank):
     dnll = float(np.max(np.abs(nll64.cpu().numpy() - nll_mixed[:nf])))
     g64 = grad64.cpu().numpy()
     gm = grad[:nf].cpu().numpy()
-    gerr = float(np.max(np.max(np.abs(gm - g64), axis=1) / np.maximum(np.max(np.abs(g64), axis=1), 1.0)))
+    gerrs = gradient_errors(gm, g64, fisher_diagonal(ctx64, w, w["theta0"]))
+
+    # the same step replayed from a CUDA graph (tracing off: no events between the kernels)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize(dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        step()
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    graph_ms = g0.elapsed_time(g1) / args.steps
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -310,7 +363,12 @@ def run_ours(args, rank, world, local_rank):
                            "species": 16, "precision": "mixed",
                            "l2": "inputs and scratch per step (GBs) exceed the 129 MB L2"},
                 "fp64_path": {"value": fp64_value, "unit": UNIT, "toys": nf, "speedup_mixed_over_fp64": value / world / fp64_value,
-                              "max_abs_dnll_mixed_vs_fp64": dnll, "grad_normwise_err_mixed_vs_fp64": gerr},
+                              "max_abs_dnll_mixed_vs_fp64": dnll, "grad_normwise_err_mixed_vs_fp64": gerrs["normwise_max"],
+                              "grad_err_mixed_vs_fp64": gerrs},
+                "graph_replay": {"value": world * T / (graph_ms * 1e-3), "unit": UNIT, "ms_per_step": graph_ms,
+                                 "note": "same step replayed from one CUDA graph with tracing off; the headline "
+                                         "value is the traced run (events around every launch)"},
+                "plan": ctx.plan_info(min(T, 4096), True),
                 "status_nonzero_toys": int(np.count_nonzero(st)),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "kernels": {k: {"ms_total": v[0], "launches": v[1], "pairs": v[2]} for k, v in prof.items() if v[1]}}
@@ -333,17 +391,29 @@ def run_single(args):
         counts = [rng.poisson(50.0, len(e) - 1).astype(np.float64) for e in work["edges"]]
         pts = I.perturbed_points(work["theta0"], 64, 2)
         for prec, label in ((gsn.GSN_MIXED, "mixed"), (gsn.GSN_FP64, "fp64")):
-            ctx = gsn.context_from_workload(work, prec, counts=counts)
-            for p in pts[:4]:
-                ctx.eval_grad(p)
             n = 64 if prec == gsn.GSN_MIXED else 16
-            t0 = time.perf_counter()
-            for i in range(n):
-                rc, v, g = ctx.eval_grad(pts[i % len(pts)])
-            dt = (time.perf_counter() - t0) / n
-            out.append({"workload": name, "precision": label, "calls": n, "ms_per_call": dt * 1e3,
-                        "evals_per_s": 1.0 / dt})
-            ctx.close()
+            rec = {"workload": name, "precision": label, "calls": n}
+            for graphs in (1, 0):
+                ctx = gsn.context_from_workload(work, prec, counts=counts, use_graphs=graphs)
+                for p in pts[:4]:
+                    ctx.eval_grad(p)
+                t0 = time.perf_counter()
+                for i in range(n):
+                    rc, v, g = ctx.eval_grad(pts[i % len(pts)])
+                dt = (time.perf_counter() - t0) / n
+                if graphs:
+                    rec.update({"ms_per_call": dt * 1e3, "evals_per_s": 1.0 / dt, "plan": ctx.plan_info(1, True)})
+                    # per-kernel event times of the same calls (tracing on: plain launches)
+                    ctx.profile(True)
+                    for i in range(n):
+                        ctx.eval_grad(pts[i % len(pts)])
+                    prof = ctx.profile_read()
+                    ctx.profile(False)
+                    rec["kernel_us_per_call"] = {k: 1e3 * v[0] / n for k, v in prof.items() if v[1]}
+                else:
+                    rec["ms_per_call_without_graphs"] = dt * 1e3
+                ctx.close()
+            out.append(rec)
     print(json.dumps({"metric": "sequential NLL+grad calls (gsn_eval_grad, host buffers)", "unit": "evals/s",
                       "data": "synthetic", "results": out}), flush=True)
 

@@ -93,9 +93,22 @@ typedef struct gsn_options {
     void*  stream;         /* cudaStream_t for all work of the context; NULL = a
                               stream created and owned by the context */
     int    max_toys_per_launch; /* batch chunk bounding scratch memory (<= 0: 4096) */
+    int    use_graphs;     /* 1: gsn_eval_grad and the batch calls record their kernel
+                              launches into a CUDA graph on first use and replay it when a
+                              call repeats with the same sizes and buffers; 0: plain launches.
+                              Skipped while tracing is on or while the stream is being
+                              captured by the caller. */
+    int    autotune;       /* 1: on the first launch of each toy count whose occupancy
+                              heuristic splits the work (small batches, single points),
+                              time candidate work decompositions on the call's own inputs
+                              and keep the fastest for the context; 0: the heuristic plan.
+                              Decompositions sum the same terms in another fixed order, so
+                              mixed-precision results may differ between contexts in the
+                              last FP32 bits; with 0 they are bitwise reproducible. */
 } gsn_options;
 
-/* Fill *opt with the defaults described above (FP64, Gaussian, device 0). */
+/* Fill *opt with the defaults described above (FP64, Gaussian, device 0,
+ * graphs and autotuning on). */
 int gsn_default_options(gsn_options* opt);
 
 /* Create a context.  Errors: GSN_ERR_ARG (bad option), GSN_ERR_CUDA. */
@@ -211,6 +224,13 @@ void* gsn_stream(gsn_ctx* ctx);
 int gsn_eval_grad_noalloc(gsn_ctx* ctx, const double* params_dev, double* nll_dev, double* grad_dev,
                           int* status_dev);
 
+/* Work decomposition of a launch of n_toys toys (n_toys >= 1; grad 0/1: without / with the
+ * adjoint): the autotuner's choice once it has run for this (n_toys, grad), else the occupancy
+ * heuristic.  out[0] fine-column splits of the forward, out[1] warps per adjoint block,
+ * out[2] bin splits of the adjoint, out[3] deviance blocks per toy, out[4] 1 if tuned.
+ * Puts the problem on the device if needed.  Errors: GSN_ERR_ARG, GSN_ERR_STATE. */
+int gsn_plan_info(gsn_ctx* ctx, int n_toys, int grad, int* out5);
+
 /* ----------------------------------------------------------- tracing ----
  * Per-kernel statistics.  While enabled, each kernel launch of the context is
  * bracketed by CUDA events recorded on the context's stream, and the response
@@ -218,12 +238,13 @@ int gsn_eval_grad_noalloc(gsn_ctx* ctx, const double* params_dev, double* nll_de
  * paper's method: measurement support for the roofline of each kernel. */
 #define GSN_K_COLUMNS    0   /* column prologue: means, resolution, band, T_dk */
 #define GSN_K_FORWARD    1   /* response build + contraction -> mu */
-#define GSN_K_DEVIANCE   2   /* FP64 deviance, NLL reduction, w = 1 - n/mu */
+#define GSN_K_DEVIANCE   2   /* FP64 deviance over bin ranges, w = 1 - n/mu */
 #define GSN_K_BACKWARD   3   /* adjoint over the band */
 #define GSN_K_GRADFINAL  4   /* partial-gradient reduction and slot-map scatter */
 #define GSN_K_SPECIES    5   /* per-species contraction (gsn_eval, gsn_expected) */
 #define GSN_K_MU         6   /* rate-weighted sum of cached per-species shapes */
-#define GSN_K_COUNT      7
+#define GSN_K_DEVFINAL   7   /* NLL reduction of the deviance partials, pulls, AnaPeak gradient */
+#define GSN_K_COUNT      8
 
 /* enable = 1 resets the statistics and starts recording; 0 stops. */
 int gsn_profile(gsn_ctx* ctx, int enable);

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -49,7 +50,15 @@ struct gsn_ctx {
     // persistent device buffers
     std::vector<Buf> owned;
     // scratch
-    Buf colbuf, blkbuf, mubuf, wbuf, partbuf, gdirect, params, counts_b, win_b, nll_b, grad_b, status_b, Mbuf, outbuf;
+    Buf colbuf, blkbuf, mubuf, wbuf, partbuf, gdirect, devbuf, params, counts_b, win_b, nll_b, grad_b, status_b, Mbuf,
+        outbuf;
+    unsigned long long scratch_gen = 0;  // bumped whenever a buffer is (re)allocated
+    // launch plans chosen by the autotuner, per (toys in a launch, gradient wanted)
+    struct PlanRec { int nsplit, ntile, bw_warps, bw_bsplit, nbtask, dev_chunks; };
+    std::map<std::pair<int, int>, PlanRec> tuned;
+    // CUDA graphs of recent launch sequences, replayed when the same sequence repeats
+    struct GraphRec { std::vector<long long> key; cudaGraphExec_t exec; };
+    std::vector<GraphRec> graphs;
     // response cache of gsn_eval (section 2.5: values are reused while the response parameters do not change)
     std::vector<double> cache_key;
     bool cache_valid = false;
@@ -92,6 +101,7 @@ int ensure(gsn_ctx* c, Buf& b, size_t bytes) {
         return fail(c, GSN_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     }
     b.n = bytes;
+    ++c->scratch_gen;
     return GSN_OK;
 }
 
@@ -133,30 +143,51 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
     }
 }
 
-struct Plan {
-    int nsplit, ntile, bw_warps, bw_bsplit, nbtask;
-};
+using Plan = gsn_ctx::PlanRec;
 
-Plan make_plan(const gsn_ctx* c, int T) {
+// Work decomposition of one launch of T toys.  nsplit: fine-column ranges per forward tile
+// (partial mu rows, summed by the deviance); bw_warps x 32: columns per adjoint block;
+// bw_bsplit: bin ranges per adjoint column block; dev_chunks: deviance blocks per toy.
+Plan plan_with(const gsn_ctx* c, int T, int nsplit, int bw_warps, int bsplit) {
     Plan p{};
     const bool e64g = c->opt.precision == GSN_FP64 && c->opt.resolution == GSN_RES_GAUSS;
     const int bins_per_tile = 8 * (e64g ? 31 : 32);
     p.ntile = (c->Jmax + bins_per_tile - 1) / bins_per_tile;
-    const long long target = 4LL * c->nsm;
-    const long long fw = (long long)T * c->G * p.ntile;
-    p.nsplit = (int)std::min<long long>(std::max<long long>(1, (target + fw - 1) / fw), std::max(1, c->K / 256));
-    p.bw_warps = 8;
+    p.nsplit = std::max(1, std::min(nsplit, std::max(1, c->K / 256)));
+    p.bw_warps = bw_warps;
+    p.bw_bsplit = std::max(1, std::min(bsplit, 16));
     const int ncb = (c->K + p.bw_warps * 32 - 1) / (p.bw_warps * 32);
-    const long long bw = (long long)T * c->G * ncb;
-    p.bw_bsplit = (int)std::min<long long>(std::max<long long>(1, (target + bw - 1) / bw), 16);
     p.nbtask = ncb * p.bw_bsplit;
+    const long long dc = (2LL * c->nsm + T - 1) / T;
+    p.dev_chunks = (int)std::max<long long>(1, std::min<long long>(dc, (c->total_bins + 127) / 128));
     return p;
+}
+
+// occupancy heuristic: about 4 blocks per SM in the forward and the adjoint
+Plan heuristic_plan(const gsn_ctx* c, int T) {
+    const long long target = 4LL * c->nsm;
+    const Plan p0 = plan_with(c, T, 1, 8, 1);
+    const long long fw = (long long)T * c->G * p0.ntile;
+    const int nsplit = (int)std::min<long long>((target + fw - 1) / fw, 1 << 20);
+    const long long bw = (long long)T * c->G * p0.nbtask;
+    const int bsplit = (int)std::min<long long>((target + bw - 1) / bw, 16);
+    return plan_with(c, T, nsplit, 8, bsplit);
+}
+
+Plan make_plan(const gsn_ctx* c, int T) { return heuristic_plan(c, T); }
+
+void drop_graphs(gsn_ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
 }
 
 int finalize(gsn_ctx* c) {
     if (c->ready) return GSN_OK;
     if (!c->have_data || !c->have_species || !c->have_params)
         return fail(c, GSN_ERR_STATE, "gsn_set_data, gsn_set_species and gsn_set_params must all be called");
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    c->tuned.clear();
     free_owned(c);
     c->cache_valid = false;
     c->tc_ready = false;
@@ -326,22 +357,38 @@ int finalize(gsn_ctx* c) {
     return GSN_OK;
 }
 
-// allocate scratch for T toys under plan p and fill the launch fields of a
-int prepare(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
-    a.work = nullptr;
+// allocate (or grow) the scratch buffers for T toys under plan p
+int reserve(gsn_ctx* c, int T, const Plan& p) {
     const size_t rs = c->opt.precision == GSN_MIXED ? sizeof(float) : sizeof(double);
+    const int nblk = (c->K + COLBLK - 1) / COLBLK;
+    const int npart = NRESP + MAXGDS * c->S;
     int rc;
     if ((rc = ensure(c, c->colbuf, (size_t)T * c->G * c->K * NFP * rs))) return rc;
-    if ((rc = ensure(c, c->blkbuf, (size_t)T * c->G * a.nblk * 2 * rs))) return rc;
+    if ((rc = ensure(c, c->blkbuf, (size_t)T * c->G * nblk * 2 * rs))) return rc;
     if ((rc = ensure(c, c->mubuf, (size_t)T * p.nsplit * c->total_bins * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->wbuf, (size_t)T * c->total_bins * rs))) return rc;
-    if ((rc = ensure(c, c->partbuf, (size_t)T * c->G * p.nbtask * a.NPART * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->partbuf, (size_t)T * c->G * p.nbtask * npart * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->gdirect, (size_t)T * c->P * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->devbuf, (size_t)T * p.dev_chunks * 2 * sizeof(double)))) return rc;
+    return GSN_OK;
+}
+
+// fill the plan and scratch fields of a (buffers reserved for at least T toys under p)
+void fill(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
+    a.work = nullptr;
     a.T = T;
     a.nsplit = p.nsplit; a.ntile = p.ntile;
     a.bw_warps = p.bw_warps; a.bw_bsplit = p.bw_bsplit; a.nbtask = p.nbtask;
+    a.dev_chunks = p.dev_chunks;
     a.colbuf = c->colbuf.p; a.blkbuf = c->blkbuf.p; a.mubuf = (double*)c->mubuf.p;
     a.wbuf = c->wbuf.p; a.partbuf = (double*)c->partbuf.p; a.gdirect = (double*)c->gdirect.p;
+    a.devpart = (double*)c->devbuf.p;
+}
+
+int prepare(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
+    int rc;
+    if ((rc = reserve(c, T, p))) return rc;
+    fill(c, T, p, a);
     return GSN_OK;
 }
 
@@ -394,10 +441,136 @@ int run_step(gsn_ctx* c, KArgs& a, bool grad) {
     if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
     if ((rc = launch(c, K_FORWARD, a, launch_forward))) return rc;
     if ((rc = launch(c, K_DEVIANCE, a, launch_deviance))) return rc;
+    if ((rc = launch(c, K_DEVFINAL, a, launch_devfinal))) return rc;
     if (grad) {
         if ((rc = launch(c, K_BACKWARD, a, launch_backward))) return rc;
         if ((rc = launch(c, K_GRADFINAL, a, launch_gradfinal))) return rc;
     }
+    return GSN_OK;
+}
+
+bool stream_capturing(gsn_ctx* c) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess) { cudaGetLastError(); return false; }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// best of `reps` runs of a launch sequence on the context's stream [ms]
+template <class F>
+int time_best(gsn_ctx* c, int reps, F body, float& best) {
+    cudaEvent_t e0 = take_event(c), e1 = take_event(c);
+    cudaError_t e = cudaSuccess;
+    best = 3.0e38f;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) e = body();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess) best = std::min(best, ms);
+    }
+    c->event_pool.push_back(e0);
+    c->event_pool.push_back(e1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GSN_ERR_CUDA, std::string("autotuner: ") + cudaGetErrorString(e));
+    }
+    return GSN_OK;
+}
+
+// Plan of a launch of T toys.  With autotuning on, the first launch of each (T, gradient) pair
+// whose heuristic plan splits the work times candidate decompositions on the caller's own
+// inputs (a holds them and the outputs) and keeps the fastest.  The candidates differ only in
+// how the sums are split, so each computes the same quantities in another fixed order.
+int choose_plan(gsn_ctx* c, int T, KArgs a, bool grad, Plan& out) {
+    const auto key = std::make_pair(T, grad ? 1 : 0);
+    const auto it = c->tuned.find(key);
+    if (it != c->tuned.end()) { out = it->second; return GSN_OK; }
+    const Plan h = heuristic_plan(c, T);
+    out = h;
+    if (stream_capturing(c)) return GSN_OK;  // no timing inside a caller's capture
+    if (!c->opt.autotune || (h.nsplit == 1 && h.bw_bsplit == 1)) { c->tuned[key] = h; return GSN_OK; }
+    const cudaStream_t st = c->stream;
+    int rc;
+    if ((rc = prepare(c, T, h, a))) return rc;
+    CUDA_TRY(c, launch_columns(a, st));  // the column prologue does not depend on the plan
+    auto fwd = [&]() {
+        cudaError_t e = launch_forward(a, st);
+        if (e == cudaSuccess) e = launch_deviance(a, st);
+        if (e == cudaSuccess) e = launch_devfinal(a, st);
+        return e;
+    };
+    Plan best = h;
+    float tbest = 3.0e38f;
+    int last = -1;
+    for (int ns : {1, h.nsplit / 4, h.nsplit / 2, h.nsplit, 2 * h.nsplit}) {
+        const Plan p = plan_with(c, T, std::max(ns, 1), h.bw_warps, h.bw_bsplit);
+        if (p.nsplit == last) continue;
+        last = p.nsplit;
+        if ((rc = prepare(c, T, p, a))) return rc;
+        float ms;
+        if ((rc = time_best(c, 3, fwd, ms))) return rc;
+        if (ms < tbest) { tbest = ms; best = p; }
+    }
+    if (grad) {
+        if ((rc = prepare(c, T, best, a))) return rc;
+        CUDA_TRY(c, fwd());  // mu and w for the adjoint candidates
+        auto bwd = [&]() {
+            cudaError_t e = launch_backward(a, st);
+            if (e == cudaSuccess) e = launch_gradfinal(a, st);
+            return e;
+        };
+        const Plan f = best;
+        tbest = 3.0e38f;
+        for (int wp : {4, 8})
+            for (int bs : {1, 2, 4, 8, 16}) {
+                const Plan p = plan_with(c, T, f.nsplit, wp, bs);
+                if ((rc = prepare(c, T, p, a))) return rc;
+                float ms;
+                if ((rc = time_best(c, 3, bwd, ms))) return rc;
+                if (ms < tbest) { tbest = ms; best = p; }
+            }
+    }
+    c->tuned[key] = best;
+    out = best;
+    return GSN_OK;
+}
+
+// Run a launch sequence, through a CUDA graph when graphs are on: the first call with a given
+// key captures the sequence, later calls with the same key replay it.  The key holds every
+// pointer and size the sequence bakes in, plus the scratch generation (a reallocation changes it).
+template <class F>
+int replay(gsn_ctx* c, std::vector<long long> key, F body) {
+    if (!c->opt.use_graphs || c->prof || stream_capturing(c)) return body();
+    key.push_back((long long)c->scratch_gen);
+    for (auto& g : c->graphs)
+        if (g.key == key) {
+            CUDA_TRY(c, cudaGraphLaunch(g.exec, c->stream));
+            return GSN_OK;
+        }
+    CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = body();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (rc || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc ? rc : fail(c, GSN_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GSN_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+    }
+    if (c->graphs.size() >= 8) {
+        cudaGraphExecDestroy(c->graphs.front().exec);
+        c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back({key, exec});
+    CUDA_TRY(c, cudaGraphLaunch(exec, c->stream));
     return GSN_OK;
 }
 
@@ -424,21 +597,40 @@ int batch_device(gsn_ctx* c, int n_toys, const double* params, const double* cou
     int rc;
     if ((rc = finalize(c))) return rc;
     const int chunk = std::max(1, c->opt.max_toys_per_launch);
+    const bool g = grad != nullptr;
+    std::vector<KArgs> args;
+    std::vector<Plan> plans;
+    std::vector<int> Ts;
     for (int t0 = 0; t0 < n_toys; t0 += chunk) {
         const int T = std::min(chunk, n_toys - t0);
         KArgs a = c->base;
-        const Plan p = make_plan(c, T);
-        if ((rc = prepare(c, T, p, a))) return rc;
         a.params = params + (size_t)t0 * c->P; a.params_stride = c->P;
         a.counts = counts + (size_t)t0 * c->total_bins; a.counts_stride = c->total_bins;
         a.win = win + (size_t)t0 * c->D * 2; a.win_stride = 2 * c->D;
         a.nll = nll + t0;
         a.grad = grad ? grad + (size_t)t0 * c->P : nullptr;
         a.status = status ? status + t0 : nullptr;
-        a.want_grad = grad ? 1 : 0;
-        if ((rc = run_step(c, a, grad != nullptr))) return rc;
+        a.want_grad = g ? 1 : 0;
+        Plan p;
+        if ((rc = choose_plan(c, T, a, g, p))) return rc;
+        args.push_back(a); plans.push_back(p); Ts.push_back(T);
     }
-    return GSN_OK;
+    // every buffer is sized before any launch is recorded, so a captured graph sees final pointers
+    for (size_t i = 0; i < args.size(); ++i)
+        if ((rc = reserve(c, Ts[i], plans[i]))) return rc;
+    std::vector<long long> key = {1, n_toys, chunk, g ? 1 : 0, (long long)params, (long long)counts, (long long)win,
+                                  (long long)nll, (long long)grad, (long long)status};
+    for (size_t i = 0; i < args.size(); ++i) {
+        fill(c, Ts[i], plans[i], args[i]);
+        key.insert(key.end(), {plans[i].nsplit, plans[i].bw_warps, plans[i].bw_bsplit, plans[i].dev_chunks});
+    }
+    return replay(c, key, [&]() {
+        for (auto& a : args) {
+            const int r = run_step(c, a, g);
+            if (r) return r;
+        }
+        return (int)GSN_OK;
+    });
 }
 
 }  // namespace
@@ -457,6 +649,8 @@ int gsn_default_options(gsn_options* o) {
     o->device = 0;
     o->stream = nullptr;
     o->max_toys_per_launch = 4096;
+    o->use_graphs = 1;
+    o->autotune = 1;
     return GSN_OK;
 }
 
@@ -493,8 +687,9 @@ void gsn_destroy(gsn_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
     free_owned(c);
-    for (Buf* b : {&c->colbuf, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->params, &c->counts_b,
+    for (Buf* b : {&c->colbuf, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
                    &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf, &c->s_hi, &c->s_lo,
                    &c->tc_part, &c->tc_err})
         if (b->p) cudaFree(b->p);
@@ -533,8 +728,22 @@ int gsn_profile_read(gsn_ctx* c, int kernel, double* total_ms, long long* launch
     return GSN_OK;
 }
 
+int gsn_plan_info(gsn_ctx* c, int n_toys, int grad, int* out) {
+    if (!c) return GSN_ERR_ARG;
+    if (n_toys < 1 || !out) return fail(c, GSN_ERR_ARG, "n_toys must be >= 1 and out non-NULL");
+    int rc;
+    if ((rc = finalize(c))) return rc;
+    const auto it = c->tuned.find(std::make_pair(n_toys, grad ? 1 : 0));
+    const bool tuned = it != c->tuned.end();
+    const Plan p = tuned ? it->second : heuristic_plan(c, n_toys);
+    out[0] = p.nsplit; out[1] = p.bw_warps; out[2] = p.bw_bsplit; out[3] = p.dev_chunks;
+    out[4] = tuned && c->opt.autotune ? 1 : 0;
+    return GSN_OK;
+}
+
 const char* gsn_kernel_name(int kernel) {
-    static const char* names[K_COUNT] = {"columns", "forward", "deviance", "backward", "gradfinal", "species", "mu"};
+    static const char* names[K_COUNT] = {"columns", "forward", "deviance", "backward", "gradfinal", "species", "mu",
+                                         "devfinal"};
     return (kernel >= 0 && kernel < K_COUNT) ? names[kernel] : "";
 }
 
@@ -679,13 +888,15 @@ int gsn_eval_grad(gsn_ctx* c, const double* params, double* nll, double* grad) {
     if ((rc = ensure(c, c->status_b, sizeof(int)))) return rc;
     CUDA_TRY(c, cudaMemcpyAsync(c->params.p, params, c->P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     KArgs a = c->base;
-    const Plan p = make_plan(c, 1);
-    if ((rc = prepare(c, 1, p, a))) return rc;
     a.params = (const double*)c->params.p; a.params_stride = c->P;
     a.counts_stride = 0; a.win_stride = 0;
     a.nll = (double*)c->nll_b.p; a.grad = grad ? (double*)c->grad_b.p : nullptr; a.status = (int*)c->status_b.p;
     a.want_grad = grad ? 1 : 0;
-    if ((rc = run_step(c, a, grad != nullptr))) return rc;
+    Plan p;
+    if ((rc = choose_plan(c, 1, a, grad != nullptr, p))) return rc;
+    if ((rc = prepare(c, 1, p, a))) return rc;
+    const std::vector<long long> key = {2, grad ? 1 : 0, p.nsplit, p.bw_warps, p.bw_bsplit, p.dev_chunks};
+    if ((rc = replay(c, key, [&]() { return run_step(c, a, grad != nullptr); }))) return rc;
     int st = 0;
     CUDA_TRY(c, cudaMemcpyAsync(nll, c->nll_b.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (grad) CUDA_TRY(c, cudaMemcpyAsync(grad, c->grad_b.p, c->P * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -800,6 +1011,7 @@ int gsn_eval(gsn_ctx* c, const double* params, double* nll) {
     a.want_grad = 0;
     if ((rc = launch(c, K_MU, a, launch_mu_from_species))) return rc;
     if ((rc = launch(c, K_DEVIANCE, a, launch_deviance))) return rc;
+    if ((rc = launch(c, K_DEVFINAL, a, launch_devfinal))) return rc;
     int st = 0;
     CUDA_TRY(c, cudaMemcpyAsync(nll, c->nll_b.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(&st, c->status_b.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -924,15 +1136,16 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     KArgs a = c->base;
     const Plan p = make_plan(c, 1);
     const size_t rs = c->opt.precision == GSN_MIXED ? sizeof(float) : sizeof(double);
-    const size_t sizes[6] = {
+    const size_t sizes[7] = {
         (size_t)c->G * c->K * NFP * rs,                         // column records
         (size_t)c->G * a.nblk * 2 * rs,                         // band summaries
         (size_t)p.nsplit * c->total_bins * sizeof(double),      // partial mu
         (size_t)c->total_bins * rs,                             // w
         (size_t)c->G * p.nbtask * a.NPART * sizeof(double),     // partial gradients
-        (size_t)c->P * sizeof(double)};                         // direct gradient terms
-    size_t off[6], total = 0;
-    for (int i = 0; i < 6; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
+        (size_t)c->P * sizeof(double),                          // direct gradient terms
+        (size_t)p.dev_chunks * 2 * sizeof(double)};             // deviance partials
+    size_t off[7], total = 0;
+    for (int i = 0; i < 7; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
     if (total > GSN_NOALLOC_SCRATCH_BYTES)
         return fail(c, GSN_ERR_ARG, "this problem needs " + std::to_string(total) + " bytes of scratch; the "
                     "no-allocation entry point holds " + std::to_string((size_t)GSN_NOALLOC_SCRATCH_BYTES));
@@ -941,6 +1154,7 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     a.bw_warps = p.bw_warps; a.bw_bsplit = p.bw_bsplit; a.nbtask = p.nbtask;
     a.colbuf = base + off[0]; a.blkbuf = base + off[1]; a.mubuf = (double*)(base + off[2]);
     a.wbuf = base + off[3]; a.partbuf = (double*)(base + off[4]); a.gdirect = (double*)(base + off[5]);
+    a.dev_chunks = p.dev_chunks; a.devpart = (double*)(base + off[6]);
     a.params = params_dev; a.params_stride = c->P;
     a.counts_stride = 0; a.win_stride = 0;
     a.nll = nll_dev; a.grad = grad_dev; a.status = status_dev;
@@ -949,6 +1163,7 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     CUDA_TRY(c, launch_columns(a, c->stream));
     CUDA_TRY(c, launch_forward(a, c->stream));
     CUDA_TRY(c, launch_deviance(a, c->stream));
+    CUDA_TRY(c, launch_devfinal(a, c->stream));
     CUDA_TRY(c, launch_backward(a, c->stream));
     CUDA_TRY(c, launch_gradfinal(a, c->stream));
     return GSN_OK;

@@ -85,6 +85,8 @@ struct KArgs {
     int nblk;
     int nbtask, bw_warps, bw_bsplit, NPART;
     int ntile;             // forward tiles per group (max over groups)
+    int dev_chunks;        // deviance blocks per toy
+    double* devpart;       // [T][dev_chunks][2]: partial deviance sum, status flags
     // outputs
     double* nll;
     double* grad;
@@ -108,6 +110,7 @@ struct KArgs {
 cudaError_t launch_columns(const KArgs& a, cudaStream_t st);
 cudaError_t launch_forward(const KArgs& a, cudaStream_t st);
 cudaError_t launch_deviance(const KArgs& a, cudaStream_t st);
+cudaError_t launch_devfinal(const KArgs& a, cudaStream_t st);
 cudaError_t launch_backward(const KArgs& a, cudaStream_t st);
 cudaError_t launch_gradfinal(const KArgs& a, cudaStream_t st);
 cudaError_t launch_species(const KArgs& a, cudaStream_t st);
@@ -121,6 +124,6 @@ int make_species_tensor_map(void* out, const float* dev, int rows, int cols_pad)
 cudaError_t launch_backward_mixed(const KArgs& a, cudaStream_t st);
 
 constexpr int K_COLUMNS = 0, K_FORWARD = 1, K_DEVIANCE = 2, K_BACKWARD = 3, K_GRADFINAL = 4,
-              K_SPECIES = 5, K_MU = 6, K_COUNT = 7;
+              K_SPECIES = 5, K_MU = 6, K_DEVFINAL = 7, K_COUNT = 8;
 
 }  // namespace gsn

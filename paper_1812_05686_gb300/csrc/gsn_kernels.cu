@@ -7,8 +7,10 @@
 //   k_forward   mu_dj = sum_k R_jk T_dk: the response bin integrals R_jk are
 //               generated in registers and contracted at once (the
 //               "response mesh" and "smearing convolution" of section 2.5 fused)
-//   k_deviance  FP64 Poisson deviance of Eq. (LL), pulls, fixed-order reduction,
-//               w_dj = 1 - n_dj / mu_dj for the adjoint, AnaPeak terms
+//   k_deviance  FP64 Poisson deviance of Eq. (LL) over a range of bins per block
+//               (AnaPeak profiles added to mu), w_dj = 1 - n_dj / mu_dj for the adjoint
+//   k_devfinal  fixed-order sum of the deviance partials, pulls, status, and the
+//               closed-form AnaPeak gradient terms
 //   k_backward  adjoint: per column, sums over the band of w-weighted response
 //               values and their derivatives, then the chain rule to
 //               (LY, kB, a, b, c) and S'^T u for the rates
@@ -372,20 +374,14 @@ DEV void peak_bins(const double* ed, int J, double m, double w, double cut, int&
     hi = l;
 }
 
-template <class R>
-__global__ void __launch_bounds__(256) k_deviance(KArgs a) {
-    const int t = blockIdx.x;
-    constexpr int MAXPK = 8;
-    __shared__ double sh[32];
-    __shared__ int spk_s[MAXD][MAXPK], spk_lo[MAXD][MAXPK], spk_hi[MAXD][MAXPK];
-    __shared__ double spk_r[MAXD][MAXPK], spk_m[MAXD][MAXPK], spk_w[MAXD][MAXPK];
-    __shared__ int snpk[MAXD];
-    const double* prm = a.params + (long long)t * a.params_stride;
-    const double* cnt = a.counts + (long long)t * a.counts_stride;
-    R* wout = reinterpret_cast<R*>(a.wbuf) + (long long)t * a.total_bins;
-    double* gdir = a.gdirect + (long long)t * a.P;
-    for (int p = threadIdx.x; p < a.P; p += blockDim.x) gdir[p] = 0.0;
-    // AnaPeak species of each dataset, with the bins their profile reaches
+// AnaPeak species of each dataset (at most MAXPK per dataset), with the bins their profile reaches
+constexpr int MAXPK = 8;
+struct PeakInfo {
+    int s[MAXD][MAXPK], lo[MAXD][MAXPK], hi[MAXD][MAXPK], n[MAXD];
+    double r[MAXD][MAXPK], m[MAXD][MAXPK], w[MAXD][MAXPK];
+};
+
+DEV void load_peaks(const KArgs& a, const double* prm, PeakInfo& pk) {
     if (threadIdx.x < a.D) {
         const int d = threadIdx.x;
         const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
@@ -393,35 +389,66 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
         for (int s = 0; s < a.S && np < MAXPK; ++s) {
             if (a.sp_kind[s] != 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
             const int pr = a.slot_map[d * a.NSLOT + s];
-            spk_s[d][np] = s;
-            spk_r[d][np] = pr >= 0 ? prm[pr] : 0.0;
-            spk_m[d][np] = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
-            spk_w[d][np] = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
+            pk.s[d][np] = s;
+            pk.r[d][np] = pr >= 0 ? prm[pr] : 0.0;
+            pk.m[d][np] = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
+            pk.w[d][np] = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
             int lo, hi;
-            peak_bins(ed, a.ds_bins[d], spk_m[d][np], spk_w[d][np], a.cut, lo, hi);
-            spk_lo[d][np] = lo; spk_hi[d][np] = hi;
+            peak_bins(ed, a.ds_bins[d], pk.m[d][np], pk.w[d][np], a.cut, lo, hi);
+            pk.lo[d][np] = lo; pk.hi[d][np] = hi;
             ++np;
         }
-        snpk[d] = np;
+        pk.n[d] = np;
     }
     __syncthreads();
+}
+
+// sum of the nsplit partial mu rows of one bin, in a fixed order (four interleaved accumulators)
+DEV double sum_splits(const double* p, long long stride, int n) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = 0;
+    for (; i + 4 <= n; i += 4) {
+        s0 += p[i * stride]; s1 += p[(i + 1) * stride];
+        s2 += p[(i + 2) * stride]; s3 += p[(i + 3) * stride];
+    }
+    for (; i < n; ++i) s0 += p[i * stride];
+    return (s0 + s1) + (s2 + s3);
+}
+
+// Stage 1 of the deviance, grid (T, dev_chunks): every block takes one contiguous range of the
+// concatenated bins of a toy, completes mu (split sum + AnaPeak profiles), writes
+// w = 1 - n/mu for the adjoint and the block's partial sum of the Eq. (LL) terms and status flags.
+template <class R>
+__global__ void __launch_bounds__(256) k_deviance(KArgs a) {
+    const int t = blockIdx.x, c = blockIdx.y;
+    __shared__ double sh[32];
+    __shared__ PeakInfo pk;
+    const double* prm = a.params + (long long)t * a.params_stride;
+    const double* cnt = a.counts + (long long)t * a.counts_stride;
+    R* wout = reinterpret_cast<R*>(a.wbuf) + (long long)t * a.total_bins;
+    load_peaks(a, prm, pk);
+    const int chunk = (a.total_bins + a.dev_chunks - 1) / a.dev_chunks;
+    const int b0 = c * chunk, b1 = min(a.total_bins, b0 + chunk);
+    const long long sstride = a.total_bins;
+    const double* mrow = a.mubuf + (long long)t * a.nsplit * a.total_bins;
     double part = 0.0;
     int bad_mu = 0, bad_fin = 0;
     for (int d = 0; d < a.D; ++d) {
         const int J = a.ds_bins[d], off = a.ds_off[d];
+        const int j0 = max(0, b0 - off), j1 = min(J, b1 - off);
+        if (j0 >= j1) continue;
         int lo = a.win[t * a.win_stride + 2 * d], hi = a.win[t * a.win_stride + 2 * d + 1];
         lo = max(lo, 0); hi = min(hi, J);
         const double eps = a.ds_eps[d];
         const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
-        for (int j = threadIdx.x; j < J; j += blockDim.x) {
+        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             double w = 0.0;
             if (j >= lo && j < hi) {
-                double mu = 0.0;
-                for (int s = 0; s < a.nsplit; ++s) mu += a.mubuf[((long long)t * a.nsplit + s) * a.total_bins + off + j];
-                for (int q = 0; q < snpk[d]; ++q) {
-                    if (j < spk_lo[d][q] || j >= spk_hi[d][q]) continue;
-                    const double m = spk_m[d][q], wd = spk_w[d][q];
-                    mu += eps * spk_r[d][q] * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
+                double mu = sum_splits(mrow + off + j, sstride, a.nsplit);
+                for (int q = 0; q < pk.n[d]; ++q) {
+                    if (j < pk.lo[d][q] || j >= pk.hi[d][q]) continue;
+                    const double m = pk.m[d][q], wd = pk.w[d][q];
+                    mu += eps * pk.r[d][q] * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
                 }
                 const double n = cnt[off + j];
                 double term;
@@ -438,24 +465,42 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
             wout[off + j] = (R)w;
         }
     }
-    double nll = block_sum_d(part, sh);
+    const double sum = block_sum_d(part, sh);
     const int any_bad_mu = __syncthreads_or(bad_mu), any_bad_fin = __syncthreads_or(bad_fin);
-    // AnaPeak gradient terms: rate, position, width (closed form per bin of the peak's band)
+    if (threadIdx.x == 0) {
+        double* o = a.devpart + ((long long)t * a.dev_chunks + c) * 2;
+        o[0] = sum;
+        o[1] = (double)(any_bad_mu | (any_bad_fin << 1));
+    }
+}
+
+// Stage 2, one block per toy: fixed-order sum of the stage-1 partials, pull terms, status, and
+// the direct gradient terms (AnaPeak rate / position / width in closed form, pulls).
+__global__ void __launch_bounds__(256) k_devfinal(KArgs a) {
+    const int t = blockIdx.x;
+    __shared__ double sh[32];
+    __shared__ PeakInfo pk;
+    const double* prm = a.params + (long long)t * a.params_stride;
+    double* gdir = a.gdirect + (long long)t * a.P;
+    if (a.want_grad)
+        for (int p = threadIdx.x; p < a.P; p += blockDim.x) gdir[p] = 0.0;
+    load_peaks(a, prm, pk);
     if (a.want_grad) {
-        __syncthreads();  // wout visible to the block
+        const float* wf = reinterpret_cast<const float*>(a.wbuf) + (long long)t * a.total_bins;
+        const double* wd64 = reinterpret_cast<const double*>(a.wbuf) + (long long)t * a.total_bins;
         for (int d = 0; d < a.D; ++d) {
             const int off = a.ds_off[d];
             const double eps = a.ds_eps[d];
             const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
-            for (int q = 0; q < snpk[d]; ++q) {
-                const int s = spk_s[d][q];
+            for (int q = 0; q < pk.n[d]; ++q) {
+                const int s = pk.s[d][q];
                 const int pr = a.slot_map[d * a.NSLOT + s];
                 const int pm = a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s];
                 const int pw = a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s];
-                const double r = spk_r[d][q], m = spk_m[d][q], wd = spk_w[d][q];
+                const double r = pk.r[d][q], m = pk.m[d][q], wd = pk.w[d][q];
                 double gr = 0.0, gm = 0.0, gw = 0.0;
-                for (int j = spk_lo[d][q] + threadIdx.x; j < spk_hi[d][q]; j += blockDim.x) {
-                    const double wj = (double)wout[off + j];
+                for (int j = pk.lo[d][q] + threadIdx.x; j < pk.hi[d][q]; j += blockDim.x) {
+                    const double wj = a.precision == 1 ? (double)wf[off + j] : wd64[off + j];
                     if (wj == 0.0) continue;
                     const double z0 = (ed[j] - m) / wd, z1 = (ed[j + 1] - m) / wd;
                     const double p0 = exp(-0.5 * z0 * z0) * INV_SQRT2PI, p1 = exp(-0.5 * z1 * z1) * INV_SQRT2PI;
@@ -475,6 +520,10 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
         }
     }
     if (threadIdx.x == 0) {
+        const double* dp = a.devpart + (long long)t * a.dev_chunks * 2;
+        double nll = 0.0;
+        int flags = 0;
+        for (int c = 0; c < a.dev_chunks; ++c) { nll += dp[2 * c]; flags |= (int)dp[2 * c + 1]; }
         for (int i = 0; i < a.n_pulls; ++i) {
             const int p = a.pull_param[i];
             const double z = (prm[p] - a.pull_c[i]) / a.pull_w[i];
@@ -482,8 +531,8 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
             if (a.want_grad) gdir[p] += z / a.pull_w[i];
         }
         int st = 0;
-        if (any_bad_mu) { st = -3; nll = INFINITY; }
-        else if (any_bad_fin || !isfinite(nll)) st = -4;
+        if (flags & 1) { st = -3; nll = INFINITY; }
+        else if ((flags & 2) || !isfinite(nll)) st = -4;
         a.nll[t] = nll;
         if (a.status) a.status[t] = st;
     }
@@ -969,8 +1018,14 @@ cudaError_t launch_forward(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_deviance(const KArgs& a, cudaStream_t st) {
-    if (a.precision == 1) k_deviance<float><<<a.T, 256, 0, st>>>(a);
-    else                  k_deviance<double><<<a.T, 256, 0, st>>>(a);
+    dim3 grid(a.T, a.dev_chunks);
+    if (a.precision == 1) k_deviance<float><<<grid, 256, 0, st>>>(a);
+    else                  k_deviance<double><<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_devfinal(const KArgs& a, cudaStream_t st) {
+    k_devfinal<<<a.T, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

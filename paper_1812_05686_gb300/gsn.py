@@ -26,7 +26,8 @@ GSN_ANA, GSN_ANA_SHIFT, GSN_ANA_PEAK = 0, 1, 2
 class gsn_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("resolution", C.c_int), ("band_cut", C.c_double),
                 ("birks_s0", C.c_double), ("birks_s1", C.c_double), ("device", C.c_int),
-                ("stream", C.c_void_p), ("max_toys_per_launch", C.c_int)]
+                ("stream", C.c_void_p), ("max_toys_per_launch", C.c_int), ("use_graphs", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class GsnError(RuntimeError):
@@ -70,6 +71,7 @@ def load_library(path: str = LIB_PATH):
         "gsn_kernel_name": (C.c_char_p, [C.c_int]),
         "gsn_peak_probe": (C.c_int, [C.c_int, C.c_int, _DP]),
         "gsn_eval_grad_noalloc": (C.c_int, [vp, vp, vp, vp, vp]),
+        "gsn_plan_info": (C.c_int, [vp, C.c_int, C.c_int, _IP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -84,10 +86,11 @@ def exported_symbols():
     return ["gsn_default_options", "gsn_create", "gsn_destroy", "gsn_last_error", "gsn_n_slots",
             "gsn_set_data", "gsn_set_species", "gsn_set_params", "gsn_eval", "gsn_eval_grad",
             "gsn_eval_grad_batch", "gsn_eval_grad_batch_dev", "gsn_expected", "gsn_stream",
-            "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe", "gsn_eval_grad_noalloc"]
+            "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe", "gsn_eval_grad_noalloc",
+            "gsn_plan_info"]
 
 
-GSN_K_COUNT = 7
+GSN_K_COUNT = 8
 GSN_PROBE_FFMA, GSN_PROBE_EX2, GSN_PROBE_DFMA, GSN_PROBE_NODE = 0, 1, 2, 3
 
 
@@ -115,7 +118,7 @@ class Context:
     """One gsn_ctx: a problem (data, species, parameter map) on one device and stream."""
 
     def __init__(self, precision=GSN_FP64, resolution=GSN_RES_GAUSS, band_cut=0.0, device=0, stream=None,
-                 birks_s0=1.55, birks_s1=0.155, max_toys_per_launch=0):
+                 birks_s0=1.55, birks_s1=0.155, max_toys_per_launch=0, use_graphs=1, autotune=1):
         self.lib = load_library()
         o = gsn_options()
         self.lib.gsn_default_options(C.byref(o))
@@ -123,6 +126,7 @@ class Context:
         o.birks_s0, o.birks_s1, o.device = birks_s0, birks_s1, device
         o.stream = stream
         o.max_toys_per_launch = max_toys_per_launch
+        o.use_graphs, o.autotune = use_graphs, autotune
         h = C.c_void_p()
         rc = self.lib.gsn_create(C.byref(h), C.byref(o))
         if rc != GSN_OK:
@@ -227,6 +231,13 @@ class Context:
 
     def stream(self):
         return self.lib.gsn_stream(self.h)
+
+    def plan_info(self, n_toys=1, grad=True):
+        """Work decomposition of a launch of n_toys toys (gsn_plan_info)."""
+        out = (C.c_int * 5)()
+        self._check(self.lib.gsn_plan_info(self.h, int(n_toys), int(grad), C.cast(out, _IP)))
+        keys = ("nsplit", "bw_warps", "bw_bsplit", "dev_chunks", "tuned")
+        return dict(zip(keys, list(out)))
 
     def profile(self, enable=True):
         self._check(self.lib.gsn_profile(self.h, int(enable)))
