@@ -287,9 +287,12 @@ int finalize(gsn_ctx* c) {
                 // symmetric 3-node rule of linear bins: centre and +-offset
                 const float xcf = (float)xc;
                 const double off = 0.5 * (hi - lo) * std::sqrt(0.6);
+                // weights 4/9 h and 5/18 h rounded so that centre + 2 sides = h: independent roundings
+                // would bias every bin integral of every column by the same ~3e-8
+                const float wside = (float)(0.5 * (hi - lo) * 5.0 / 9.0);
+                const float wcen = (float)((hi - lo) - 2.0 * (double)wside);
                 float bt[8] = {xcf, (float)(xc + off - (double)xcf), (float)std::log1p(off / xc),
-                               (float)std::log1p(-off / xc), (float)(0.5 * (hi - lo) * 8.0 / 9.0),
-                               (float)(0.5 * (hi - lo) * 5.0 / 9.0), 0.f, 0.f};
+                               (float)std::log1p(-off / xc), wcen, wside, 0.f, 0.f};
                 if (cls != BIN_LIN) for (int q = 1; q < 8; ++q) bt[q] = 0.f;
                 btab_f.insert(btab_f.end(), bt, bt + 8);
             }

@@ -11,6 +11,10 @@ namespace gsn {
 constexpr float L2E = 1.4426950408889634f;           // log2(e)
 constexpr double INV_SQRT2 = 0.70710678118654752440;
 constexpr double INV_SQRT2PI = 0.39894228040143267794;
+// 1/sqrt(2 pi) as an FP32 pair (hi + lo): the column normalisations use it with one FMA, so the
+// FP32 rounding of the constant does not scale every column by the same factor
+constexpr float ISQ2PI_HI = (float)INV_SQRT2PI;
+constexpr float ISQ2PI_LO = (float)(INV_SQRT2PI - (double)ISQ2PI_HI);
 constexpr int FWD_WARPS = 8;
 
 // ------------------------------------------------------------------ math --

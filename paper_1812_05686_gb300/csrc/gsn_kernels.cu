@@ -29,22 +29,25 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
     const int t = blockIdx.z, g = blockIdx.y;
     const int k = blockIdx.x * COLBLK + threadIdx.x;
     __shared__ double sres[NRESP];
-    __shared__ R srate[MAXGDS][MAXS];
+    // eps_d r_s as an unevaluated pair (hi + lo): one rounding of eps_d r_s to FP32 would be
+    // shared by every column and bin of the toy, a coherent bias of mu that does not average out
+    __shared__ R srate[MAXGDS][MAXS], srate_lo[MAXGDS][MAXS];
     __shared__ float sdf[8];      // per-toy double-float constants (mixed)
     __shared__ R sred[2][COLBLK / 32];
     const double* prm = a.params + (long long)t * a.params_stride;
     if (threadIdx.x < NRESP) sres[threadIdx.x] = prm[a.g_resp[g][threadIdx.x]];
     for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
         const int dd = i / a.S, s = i % a.S;
-        R v = 0;
+        double v = 0.0;
         if (dd < a.g_nds[g]) {
             const int d = a.g_ds[g][dd];
             if (a.sp_kind[s] != 2 && ((a.sp_mask[s] >> d) & 1u)) {
                 const int p = a.slot_map[d * a.NSLOT + s];
-                if (p >= 0) v = (R)(a.ds_eps[d] * prm[p]);
+                if (p >= 0) v = a.ds_eps[d] * prm[p];
             }
         }
-        srate[dd][s] = v;
+        srate[dd][s] = (R)v;
+        srate_lo[dd][s] = (R)(v - (double)(R)v);
     }
     __syncthreads();
     const double LY = sres[0], kB = sres[1], ra = sres[2], rb = sres[3], rc = sres[4];
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
         if constexpr (RES == 0) {
             const R sig = sqrt(var), isg = R(1) / sig;
             f[F_A] = isg;
-            if constexpr (sizeof(R) == 4) Nk = isg * (R)INV_SQRT2PI;
+            if constexpr (sizeof(R) == 4) Nk = fmaf(isg, ISQ2PI_LO, isg * ISQ2PI_HI);
             const R zc = sqrt(R(2) * (R)a.cut);
             xmin = mu - zc * sig;
             xmax = mu + zc * sig;
@@ -123,7 +126,8 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
                     // density at the mean: exp(-corr(d)) / (sigma sqrt(2 pi)), corr = Stirling remainder
                     const float id = 1.0f / d, id2 = id * id;
                     const float corr = id * (1.0f / 12 - id2 * (1.0f / 360 - id2 * (1.0f / 1260 - id2 * (1.0f / 1680))));
-                    Nk = expf(-corr) * rsqrtf(var) * (float)INV_SQRT2PI;
+                    const float nq = expf(-corr) * rsqrtf(var);
+                    Nk = fmaf(nq, ISQ2PI_LO, nq * ISQ2PI_HI);
                     f[F_KAPPA] = 0.5f * id + id2 * (1.0f / 12 - id2 * (1.0f / 120 - id2 * (1.0f / 252 - id2 * (1.0f / 240))));
                 } else {
                     const double dd = (double)mu * (double)mu / (double)var, sd = (double)var / (double)mu;
@@ -190,7 +194,13 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
         for (int dd = 0; dd < a.g_nds[g]; ++dd) {
             R T = 0;
             if constexpr (sizeof(R) == 4) {
-                for (int s = 0; s < a.S; ++s) T = fmaf(srate[dd][s], a.Sf[(long long)s * a.K + k], T);
+                float Tl = 0.f;
+                for (int s = 0; s < a.S; ++s) {
+                    const float sv = a.Sf[(long long)s * a.K + k];
+                    T = fmaf(srate[dd][s], sv, T);
+                    Tl = fmaf(srate_lo[dd][s], sv, Tl);
+                }
+                T += Tl;
             } else {
                 for (int s = 0; s < a.S; ++s) T = fma(srate[dd][s], a.Sd[(long long)s * a.K + k], T);
             }
