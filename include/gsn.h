@@ -263,11 +263,15 @@ const char* gsn_kernel_name(int kernel);
  *   GSN_PROBE_FFMA  FP32 fused multiply-adds
  *   GSN_PROBE_EX2   SFU base-2 exponentials
  *   GSN_PROBE_DFMA  FP64 fused multiply-adds
- *   GSN_PROBE_NODE  one mixed-precision quadrature node: 2 FFMA + EX2 + FFMA */
+ *   GSN_PROBE_NODE  one mixed-precision quadrature node: 2 FFMA + EX2 + FFMA
+ *   GSN_PROBE_EX2_BIAS  not a rate: the mean relative error of the SFU exponential over
+ *                   the exponents of a Gaussian profile, weighted by the profile (the
+ *                   bias the mixed-precision column normalisation divides out) */
 #define GSN_PROBE_FFMA 0
 #define GSN_PROBE_EX2  1
 #define GSN_PROBE_DFMA 2
 #define GSN_PROBE_NODE 3
+#define GSN_PROBE_EX2_BIAS 4
 int gsn_peak_probe(int device, int which, double* ops_per_second);
 
 #ifdef __cplusplus

@@ -751,7 +751,7 @@ const char* gsn_kernel_name(int kernel) {
 }
 
 int gsn_peak_probe(int device, int which, double* ops) {
-    if (!ops || which < 0 || which > 3) return GSN_ERR_ARG;
+    if (!ops || which < 0 || which > 4) return GSN_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return GSN_ERR_CUDA; }
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);

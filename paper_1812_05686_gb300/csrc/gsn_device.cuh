@@ -9,12 +9,21 @@ namespace gsn {
 #define DEV __device__ __forceinline__
 
 constexpr float L2E = 1.4426950408889634f;           // log2(e)
+constexpr float L2E_LO = (float)(1.4426950408889634 - (double)L2E);
+constexpr float HALF_L2E_LO = (float)(0.72134752044448170 - 0.5 * (double)L2E);
 constexpr double INV_SQRT2 = 0.70710678118654752440;
 constexpr double INV_SQRT2PI = 0.39894228040143267794;
-// 1/sqrt(2 pi) as an FP32 pair (hi + lo): the column normalisations use it with one FMA, so the
-// FP32 rounding of the constant does not scale every column by the same factor
-constexpr float ISQ2PI_HI = (float)INV_SQRT2PI;
-constexpr float ISQ2PI_LO = (float)(INV_SQRT2PI - (double)ISQ2PI_HI);
+// Mean relative error of the SFU exponential ex2.approx.ftz.f32 over the arguments of a Gaussian
+// profile, weighted by the profile (gsn_peak_probe(GSN_PROBE_EX2_BIAS) measures it).  Every
+// mixed-precision response value is N_k times a sum of such exponentials, so a bias of the SFU
+// would scale all expected counts alike; the column normalisation divides it out.
+constexpr double EX2_MEAN_REL_ERR = -2.749454e-8;  // measured on GB300 (sm_103a)
+// Column normalisation constant 1/(sqrt(2 pi) (1 + bias)) as an FP32 pair, applied as
+// fmaf(x, NORM_HI, x * NORM_LO): the exact product enters the single rounding, so the FP32
+// rounding of the constant does not scale every column by the same factor
+constexpr double NORM_D = INV_SQRT2PI / (1.0 + EX2_MEAN_REL_ERR);
+constexpr float NORM_HI = (float)NORM_D;
+constexpr float NORM_LO = (float)(NORM_D - (double)NORM_HI);
 constexpr int FWD_WARPS = 8;
 
 // ------------------------------------------------------------------ math --
@@ -185,6 +194,10 @@ DEV void two_sum_acc(float& s, float& c, float x) {
     s = t;
 }
 
+// log2(e) x with the exact product inside one rounding: per-column constants made with the FP32
+// log2(e) alone would carry its rounding (1.3e-8) into the exponent of every column
+DEV float mul_l2e(float x) { return fmaf(L2E, x, x * L2E_LO); }
+
 // --------------------------------------------------- response evaluators ---
 // Mixed: unnormalised bin value rho_jk = sum_n w_n exp(E_n) of a column record.
 template <int RES, int NG>
@@ -196,15 +209,16 @@ DEV float bin_value_f(const float* c, float xc, const float* del, const float* l
 #pragma unroll
         for (int n = 0; n < NG; ++n) {
             const float zn = fmaf(del[n], c[F_A], z);
-            rho = fmaf(wt[n], ex2f(-0.5f * L2E * zn * zn), rho);
+            const float q = zn * zn;
+            rho = fmaf(wt[n], ex2f(-fmaf(0.5f * L2E, q, q * HALF_L2E_LO)), rho);
         }
     } else {
         // log f(x) - log f(mu) = (d-1) D(t) - t = d D(t) - ln(1+t), t = x/mu - 1
         const float t = Dx * c[F_A];
         float L1;
         const float Dt = log1pmx2_f(t, L1);
-        const float B2 = L2E * (c[F_B] - 1.0f), C2 = L2E * c[F_C];
-        const float Ec = fmaf(L2E * c[F_B], Dt, -L2E * L1);
+        const float B2 = fmaf(L2E, c[F_B], fmaf(L2E_LO, c[F_B] - 1.0f, -L2E)), C2 = mul_l2e(c[F_C]);
+        const float Ec = fmaf(mul_l2e(c[F_B]), Dt, -L2E * L1);
 #pragma unroll
         for (int n = 0; n < NG; ++n)
             rho = fmaf(wt[n], ex2f(Ec + fmaf(C2, del[n], B2 * lam[n])), rho);

@@ -106,13 +106,14 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
             const double D = L - y, r1 = y / (1.0 + y);
             deq = beta > 0 ? (a.s0 * (beta / alpha) * (2.0 * D + y * r1) - a.s1 * (D + y * r1)) / (alpha * alpha) : NAN;
         }
-        var = (R)ra + mu * ((R)rb + (R)rc * mu);
+        // in FP64 and rounded once: FP32 copies of a, b, c would scale every column's variance alike
+        var = (R)fma((double)mu, fma(rc, (double)mu, rb), ra);
         f[F_DEQ] = deq;
         R Nk = 1;
         if constexpr (RES == 0) {
             const R sig = sqrt(var), isg = R(1) / sig;
             f[F_A] = isg;
-            if constexpr (sizeof(R) == 4) Nk = fmaf(isg, ISQ2PI_LO, isg * ISQ2PI_HI);
+            if constexpr (sizeof(R) == 4) Nk = fmaf(isg, NORM_HI, isg * NORM_LO);
             const R zc = sqrt(R(2) * (R)a.cut);
             xmin = mu - zc * sig;
             xmax = mu + zc * sig;
@@ -127,11 +128,12 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
                     const float id = 1.0f / d, id2 = id * id;
                     const float corr = id * (1.0f / 12 - id2 * (1.0f / 360 - id2 * (1.0f / 1260 - id2 * (1.0f / 1680))));
                     const float nq = expf(-corr) * rsqrtf(var);
-                    Nk = fmaf(nq, ISQ2PI_LO, nq * ISQ2PI_HI);
+                    Nk = fmaf(nq, NORM_HI, nq * NORM_LO);
                     f[F_KAPPA] = 0.5f * id + id2 * (1.0f / 12 - id2 * (1.0f / 120 - id2 * (1.0f / 252 - id2 * (1.0f / 240))));
                 } else {
                     const double dd = (double)mu * (double)mu / (double)var, sd = (double)var / (double)mu;
-                    Nk = (float)exp((dd - 1.0) * log((double)mu) - (double)mu / sd - dd * log(sd) - lgamma(dd));
+                    Nk = (float)(exp((dd - 1.0) * log((double)mu) - (double)mu / sd - dd * log(sd) - lgamma(dd)) /
+                                 (1.0 + EX2_MEAN_REL_ERR));
                     f[F_KAPPA] = (float)(log(dd) - digamma_d(dd));
                 }
             } else {
@@ -194,13 +196,10 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
         for (int dd = 0; dd < a.g_nds[g]; ++dd) {
             R T = 0;
             if constexpr (sizeof(R) == 4) {
-                float Tl = 0.f;
-                for (int s = 0; s < a.S; ++s) {
-                    const float sv = a.Sf[(long long)s * a.K + k];
-                    T = fmaf(srate[dd][s], sv, T);
-                    Tl = fmaf(srate_lo[dd][s], sv, Tl);
-                }
-                T += Tl;
+                // the lo parts first: the hi products then enter exactly into the running sum, so
+                // the correction survives the roundings (added last, it would be below half an ulp)
+                for (int s = 0; s < a.S; ++s) T = fmaf(srate_lo[dd][s], a.Sf[(long long)s * a.K + k], T);
+                for (int s = 0; s < a.S; ++s) T = fmaf(srate[dd][s], a.Sf[(long long)s * a.K + k], T);
             } else {
                 for (int s = 0; s < a.S; ++s) T = fma(srate[dd][s], a.Sd[(long long)s * a.K + k], T);
             }
@@ -965,7 +964,38 @@ __global__ void __launch_bounds__(256) k_probe(float* sink, double* sinkd, float
     if (sd == 12345.678) sinkd[threadIdx.x] = sd;
 }
 
+// Mean relative error of ex2f over the exponents of a unit Gaussian profile, -(log2 e / 2) z^2 on
+// a uniform grid of z in [-6.5, 6.5], each weighted by the profile value; FP64 exp2 is the reference.
+__global__ void __launch_bounds__(256) k_ex2_bias(long long n, double* acc) {
+    __shared__ double sh[32];
+    double se = 0.0, sw = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double z = -6.5 + 13.0 * (i + 0.5) / n;
+        const float x = (float)(-0.72134752044448170 * z * z);
+        const double ref = exp2((double)x);
+        se += ((double)ex2f(x) - ref);
+        sw += ref;
+    }
+    se = block_sum_d(se, sh);
+    sw = block_sum_d(sw, sh);
+    if (threadIdx.x == 0) { atomicAdd(acc, se); atomicAdd(acc + 1, sw); }
+}
+
+cudaError_t run_ex2_bias(double* bias) {
+    double* acc = nullptr;
+    cudaError_t err;
+    if ((err = cudaMalloc(&acc, 2 * sizeof(double)))) return err;
+    double h[2] = {0.0, 0.0};
+    err = cudaMemcpy(acc, h, sizeof h, cudaMemcpyHostToDevice);
+    if (!err) { k_ex2_bias<<<1024, 256>>>(1LL << 26, acc); err = cudaGetLastError(); }
+    if (!err) err = cudaMemcpy(h, acc, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(acc);
+    *bias = h[1] > 0 ? h[0] / h[1] : 0.0;
+    return err;
+}
+
 cudaError_t run_probe(int which, int nsm, double* ops) {
+    if (which == 4) return run_ex2_bias(ops);
     float* sink = nullptr;
     double* sinkd = nullptr;
     cudaStream_t st;

@@ -19,6 +19,7 @@
 namespace gsn {
 
 constexpr float SQ_HALF_L2E = 0.84932180028801904f;   // sqrt(log2(e) / 2)
+constexpr float SQ_HALF_L2E_LO = (float)(0.84932180028801904 - (double)SQ_HALF_L2E);
 // Columns of shape d >= D_POLY take the branch-free series for ln(1+t) - t: inside their band
 // every point with density above ~1e-8 of the peak has |t/(2+t)| <= 1/3, and the truncated
 // series stays finite and far below the cut elsewhere.
@@ -36,10 +37,10 @@ template <int RES>
 DEV RecF transform_record(const float4 r0, const float4 r1, const float4 r2, const float4 r3) {
     RecF o;
     if (RES == 1) {
-        o.q0 = make_float4(r0.x, r0.y, r0.z, L2E * r0.w);
-        o.q1 = make_float4(fmaf(L2E, r0.w, -L2E), L2E * r1.x, r2.z, -L2E * r0.z);
+        o.q0 = make_float4(r0.x, r0.y, r0.z, mul_l2e(r0.w));
+        o.q1 = make_float4(fmaf(L2E, r0.w, fmaf(L2E_LO, r0.w - 1.0f, -L2E)), mul_l2e(r1.x), r2.z, -mul_l2e(r0.z));
     } else {
-        o.q0 = make_float4(r0.x, r0.y, r0.z * SQ_HALF_L2E, 0.f);
+        o.q0 = make_float4(r0.x, r0.y, fmaf(SQ_HALF_L2E, r0.z, r0.z * SQ_HALF_L2E_LO), 0.f);
         o.q1 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     o.q2 = make_float4(r3.y, r3.z, r3.w, 0.f);
@@ -280,10 +281,11 @@ __global__ void __launch_bounds__(256) k_backward_m(KArgs a) {
     // scaled by mu/d and s^2; gauss: z- and (z^2-1)-weighted sums)
     float sU[5] = {0, 0, 0, 0, 0}, cU[5] = {0, 0, 0, 0, 0};
     const float A = c[F_A];
-    const float P2 = L2E * c[F_B], Q2 = fmaf(L2E, c[F_B], -L2E), R2 = L2E * c[F_C];
+    const float P2 = mul_l2e(c[F_B]), Q2 = fmaf(L2E, c[F_B], fmaf(L2E_LO, c[F_B] - 1.0f, -L2E)),
+                R2 = mul_l2e(c[F_C]);
     const float kap = c[F_KAPPA];
-    const float Ag = A * SQ_HALF_L2E;
-    const float mL2EA = -L2E * A;
+    const float Ag = fmaf(SQ_HALF_L2E, A, A * SQ_HALF_L2E_LO);
+    const float mL2EA = -mul_l2e(A);
     const bool wpoly = RES == 1 && __all_sync(0xffffffffu, !kval || c[F_B] >= D_POLY);
     const int jlin = a.g_jlin[g];
     const int nbase = a.g_node_off[g];
@@ -317,7 +319,8 @@ __global__ void __launch_bounds__(256) k_backward_m(KArgs a) {
                 const float z = Dx * A;
                 for (int n = 0; n < NG; ++n) {
                     const float zn = fmaf(nd[n], A, z);
-                    const float fw = nd[2 * NGM_F + n] * ex2f(-0.5f * L2E * zn * zn);
+                    const float q = zn * zn;
+                    const float fw = nd[2 * NGM_F + n] * ex2f(-fmaf(0.5f * L2E, q, q * HALF_L2E_LO));
                     rho += fw; u1 = fmaf(fw, zn, u1); u2 = fmaf(fw, fmaf(zn, zn, -1.0f), u2);
                 }
             }

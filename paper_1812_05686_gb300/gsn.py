@@ -91,7 +91,7 @@ def exported_symbols():
 
 
 GSN_K_COUNT = 8
-GSN_PROBE_FFMA, GSN_PROBE_EX2, GSN_PROBE_DFMA, GSN_PROBE_NODE = 0, 1, 2, 3
+GSN_PROBE_FFMA, GSN_PROBE_EX2, GSN_PROBE_DFMA, GSN_PROBE_NODE, GSN_PROBE_EX2_BIAS = 0, 1, 2, 3, 4
 
 
 def peak_probe(which, device=0):
