@@ -300,10 +300,21 @@ int finalize(gsn_ctx* c) {
                 const float xcf = (float)xc;
                 xc_f.push_back(xcf);
                 float t[3 * NGM_F] = {0};
+                double wsum = 0.0, fsum = 0.0;
+                int nmax = 0;
                 for (int n = 0; n < ng; ++n) {
                     t[n] = (float)(nx[n] - (double)xcf);
                     t[NGM_F + n] = (float)(nx[n] > 0 ? std::log(nx[n] / (double)xcf) : 0.0);
                     t[2 * NGM_F + n] = (float)nw[n];
+                    wsum += nw[n];
+                    fsum += (double)t[2 * NGM_F + n];
+                    if (nw[n] > nw[nmax]) nmax = n;
+                }
+                // the largest weight absorbs the rounding residual of the others, so that the FP32
+                // weights of a bin sum to its rule's total (independent roundings bias every column)
+                if (ng > 0) {
+                    const double others = fsum - (double)t[2 * NGM_F + nmax];
+                    t[2 * NGM_F + nmax] = (float)(wsum - others);
                 }
                 ntab_f.insert(ntab_f.end(), t, t + 3 * NGM_F);
             } else {

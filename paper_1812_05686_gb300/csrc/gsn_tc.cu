@@ -11,11 +11,16 @@
 //     32 columns) with TMA (128-byte swizzle) onto an mbarrier;
 //   - the same thread issues, per k-step of 8 columns, the three products
 //     A_hi B_hi + A_hi B_lo + A_lo B_hi (tcgen05.mma kind::tf32, M = 128,
-//     N = 16) into an FP32 accumulator in tensor memory and commits them to a
+//     N = 16) into FP32 accumulators in tensor memory and commits them to a
 //     second mbarrier.
-// Every 64 columns the accumulator is read back (tcgen05.ld) and folded into
-// compensated FP32 sums; the partial sums of each column range are written
-// in FP64 and reduced over the ranges in a fixed order.
+// The tensor-core accumulation does not round to nearest: every accumulating
+// MMA loses a fraction of an ulp of its accumulator, always the same way, which
+// adds up to a coherent bias of the contraction.  So the A_hi B_hi products of
+// each pair of k-steps get an accumulator of their own (two per chunk), the
+// small cross terms a third, and all three are read back (tcgen05.ld) after
+// every chunk of 32 columns and folded into compensated FP32 sums; the partial
+// sums of each column range are written in FP64 and reduced over the ranges in
+// a fixed order.
 // Every wait is bounded: a CTA that times out sets an error flag, waits
 // (bounded) for its own operations in flight, frees its tensor memory and
 // returns.
@@ -31,8 +36,7 @@ namespace {
 constexpr int TC_ROWS = 128;     // bins per CTA = MMA M = TMEM lanes
 constexpr int TC_N = 16;         // species per CTA = MMA N
 constexpr int TC_KC = 32;        // columns per chunk (one 128-byte swizzle row of S')
-constexpr int TC_FLUSH = 2;      // chunks per accumulator read-back
-constexpr uint32_t TC_TMEM_COLS = 32;
+constexpr uint32_t TC_TMEM_COLS = 64;  // accumulators: hi*hi of k-steps 0-1 | 2-3 | cross terms
 constexpr long long WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
 
 DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -192,7 +196,6 @@ __global__ void __launch_bounds__(TC_ROWS) k_species_tc(const __grid_constant__ 
     for (int i = 0; i < TC_N; ++i) { accs[i] = 0.f; accc[i] = 0.f; }
     uint32_t ph_tma = 0, ph_mma = 0;
     bool ok = true, tma_pending = false, mma_pending = false;
-    int in_group = 0;
     const uint32_t sa_hi = smem_u32(sm.ahi), sa_lo = smem_u32(sm.alo);
     const uint32_t sb_hi = smem_u32(sm.bhi), sb_lo = smem_u32(sm.blo);
 
@@ -245,24 +248,23 @@ __global__ void __launch_bounds__(TC_ROWS) k_species_tc(const __grid_constant__ 
                 const uint64_t al = smem_desc(sa_lo + 256u * s, 128, 1024, 0);
                 const uint64_t bh = smem_desc(sb_hi + 32u * s, 16, 1024, 2);
                 const uint64_t bl = smem_desc(sb_lo + 32u * s, 16, 1024, 2);
-                umma_tf32(tmem, ah, bh, (in_group > 0 || s > 0) ? 1u : 0u);
-                umma_tf32(tmem, ah, bl, 1u);
-                umma_tf32(tmem, al, bh, 1u);
+                umma_tf32(tmem + (uint32_t)(TC_N * (s >> 1)), ah, bh, (uint32_t)(s & 1));
+                umma_tf32(tmem + 2u * TC_N, ah, bl, s > 0 ? 1u : 0u);
+                umma_tf32(tmem + 2u * TC_N, al, bh, 1u);
             }
             umma_commit(bar_mma);
         }
         if (__syncthreads_or(!mbar_wait(bar_mma, ph_mma))) { ok = false; mma_pending = true; break; }
         ph_mma ^= 1u;
         tc_fence_after();
-        ++in_group;
-        if (in_group == TC_FLUSH || cc + 1 == c_end) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
             float v[16];
-            tmem_ld16(taddr, v);
+            tmem_ld16(taddr + (uint32_t)(TC_N * r), v);
 #pragma unroll
             for (int i = 0; i < TC_N; ++i) two_sum_acc(accs[i], accc[i], v[i]);
-            tc_fence_before();
-            in_group = 0;
         }
+        tc_fence_before();
         __syncthreads();
     }
     if (!ok) {
