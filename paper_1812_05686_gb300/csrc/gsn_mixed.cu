@@ -10,6 +10,12 @@
 //               band (node offsets, weights, w_dj) the same way.  The adjoint
 //               accumulates dNLL/dmu_k at fixed variance and dNLL/dsigma_k^2 at
 //               fixed mean directly (no chain rule through shape and scale).
+//               Its common case (gamma columns of shape >= D_POLY) evaluates two
+//               bins per instruction with the packed FP32 operations of sm_100+
+//               (fma / add / mul .rn.f32x2): the adjoint is FP32-issue bound, and
+//               the packed form halves its instruction count.  (The forward stays
+//               scalar: its chains are short between SFU operations, and packing
+//               two columns into one chain left it latency bound and slower.)
 // Both use the symmetric 3-point Gauss-Legendre rule of linear bins (centre
 // node without offset terms); bins below the log-spaced threshold and the bin
 // at zero take the general node table.  FP32 partial sums are folded per batch
@@ -45,6 +51,31 @@ DEV RecF transform_record(const float4 r0, const float4 r1, const float4 r2, con
     }
     o.q2 = make_float4(r3.y, r3.z, r3.w, 0.f);
     return o;
+}
+
+// ---- packed FP32 (two lanes of work per instruction: fma / add / mul .rn.f32x2 on sm_100+) ----
+DEV float2 f2(float x) { return make_float2(x, x); }
+DEV float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+DEV float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+DEV float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+DEV float2 ex2f2(float2 x) { return make_float2(ex2f(x.x), ex2f(x.y)); }
+DEV float2 rcp2(float2 x) {
+    float2 r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(x.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(x.y));
+    return r;
+}
+// D(t) = ln(1 + t) - t of log1pmx_poly for two arguments; nt = -t
+DEV float2 log1pmx_poly2(float2 t, float2 nt) {
+    const float2 u = mul2(t, rcp2(add2(t, f2(2.0f))));
+    const float2 v = mul2(u, u);
+    float2 p = fma2(v, f2(2.0f / 15.0f), f2(2.0f / 13.0f));
+    p = fma2(p, v, f2(2.0f / 11.0f));
+    p = fma2(p, v, f2(2.0f / 9.0f));
+    p = fma2(p, v, f2(2.0f / 7.0f));
+    p = fma2(p, v, f2(2.0f / 5.0f));
+    p = fma2(p, v, f2(2.0f / 3.0f));
+    return mul2(u, fma2(v, p, nt));  // u (v p - t)
 }
 
 // value of one linear bin for a column of shape d >= D_POLY:
@@ -223,8 +254,13 @@ DEV float warp_sum_comp(float s, float c) {
     return s + c;
 }
 
+// resident 256-thread blocks per SM the adjoint's register budget is sized for
+#ifndef GSN_BW_MINBLOCKS
+#define GSN_BW_MINBLOCKS 4
+#endif
+
 template <int RES, int NDS>
-__global__ void __launch_bounds__(256) k_backward_m(KArgs a) {
+__global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
     const int task = blockIdx.x, g = blockIdx.y, t = blockIdx.z;
     const int W = a.bw_warps;
     const int cbw = task / a.bw_bsplit, bsp = task % a.bw_bsplit;
@@ -233,7 +269,7 @@ __global__ void __launch_bounds__(256) k_backward_m(KArgs a) {
     const int k = kbase + warp * 32 + lane;
     const bool kval = k < a.K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* sbin = reinterpret_cast<float4*>(smem_raw);                      // [W][32][3]
+    float4* sbin = reinterpret_cast<float4*>(smem_raw);                      // per warp 384 floats of bin data
     float* su = reinterpret_cast<float*>(smem_raw + sizeof(float4) * 3 * 32 * W);   // [MAXGDS][W*32]
     double* sresp = reinterpret_cast<double*>(smem_raw + sizeof(float4) * 3 * 32 * W + sizeof(float) * MAXGDS * W * 32);
     const int nds = a.g_nds[g];
@@ -331,90 +367,151 @@ __global__ void __launch_bounds__(256) k_backward_m(KArgs a) {
         for (int dd = 0; dd < MAXGDS; ++dd) two_sum_acc(sU[dd], cU[dd], w[dd] * rho);
     }
 
-    // linear bins in batches of 32, staged per warp
+    // linear bins in batches of 32, staged per warp as interleaved pairs (bins 2p, 2p+1): each float4
+    // holds one quantity of both bins, so the packed FP32 path reads its float2 operands directly.
+    //   pair p: (xc, xc', dl, dl') (lp, lp', lm, lm') (w0, w0', w1, w1') (wd0, wd0', wd1, wd1') (wd2, wd2', -, -)
     const int jstart = max(ja, jlin);
-    float4 b0 = make_float4(0, 0, 0, 0), b1 = b0, b2 = b0;
-    auto load = [&](int jj) {
-        if (jj <= jb) {
-            const float4* bt = reinterpret_cast<const float4*>(a.btab_f) + 2 * (long long)(nbase + jj);
+    if (jstart <= jb) {
+        float4 b0 = make_float4(0, 0, 0, 0), b1 = b0;
+        float bw2 = 0.f;
+        auto load = [&](int jj) {
+            // bins past jb pad the last pair: the geometry of bin jb with zero weights
+            const float4* bt = reinterpret_cast<const float4*>(a.btab_f) + 2 * (long long)(nbase + min(jj, jb));
             b0 = bt[0];
-            const float4 x = bt[1];
-            b1 = make_float4(x.x, x.y, wv0[jj], NDS > 1 ? wv1[jj] : 0.f);
-            if (NDS > 2) b2 = make_float4(wv2[jj], 0.f, 0.f, 0.f);
-        }
-    };
-    load(jstart + lane);
-    float4* my = sbin + (long long)warp * 32 * 3;
-    for (int jj0 = jstart; jj0 <= jb; jj0 += 32) {
-        my[lane * 3 + 0] = b0; my[lane * 3 + 1] = b1;
-        if (NDS > 2) my[lane * 3 + 2] = b2;
-        __syncwarp();
-        load(jj0 + 32 + lane);
-        const int nbat = min(32, jb - jj0 + 1);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
-#pragma unroll 2
-        for (int i = 0; i < nbat; ++i) {
-
-            const float4 q0 = my[i * 3], q1 = my[i * 3 + 1];
-            const float wd2 = NDS > 2 ? my[i * 3 + 2].x : 0.f;
-            const float xc = q0.x, dl = q0.y, lp = q0.z, lm = q0.w;
-            const float w0 = q1.x, w1 = q1.y, wd0 = q1.z, wd1 = q1.w;
-            const float Wj = fmaf(wd0, TN0, fmaf(wd1, TN1, wd2 * TN2));
-            const float Dx = (xc - c[F_MUH]) - c[F_MUL];
-            float rho, u1, u2;
-            if (RES == 1) {
-                const float tt = Dx * A;
-                float L1, Dt, Ec;
-                if (wpoly) {
-                    // shape >= D_POLY: branch-free series, exponent (d-1) D - t
-                    Dt = log1pmx_poly(tt);
-                    L1 = Dt + tt;
-                    Ec = fmaf(Q2, Dt, Dx * mL2EA);
-                } else {
-                    Dt = log1pmx2_f(tt, L1);
-                    Ec = fmaf(P2, Dt, -L2E * L1);
-                }
-                const float cd = R2 * dl;
-                const float e0 = w0 * ex2f(Ec);
-                const float ep = w1 * ex2f(fmaf(Q2, lp, Ec) + cd);
-                const float em = w1 * ex2f(fmaf(Q2, lm, Ec) - cd);
-                rho = e0 + ep + em;
-                const float Ls = fmaf(ep, lp, em * lm);           // sum w f ln(x_n / x_c)
-                const float XA = (ep - em) * (dl * A);             // sum w f (x_n - x_c) / mu
-                const float cmu = fmaf(2.0f, L1 + kap, -tt);
-                u1 = fmaf(cmu, rho, fmaf(2.0f, Ls, -XA));
-                u2 = fmaf(-(Dt + kap), rho, XA - Ls);
+            if (jj <= jb) {
+                const float4 x = bt[1];
+                b1 = make_float4(x.x, x.y, wv0[jj], NDS > 1 ? wv1[jj] : 0.f);
+                bw2 = NDS > 2 ? wv2[jj] : 0.f;
             } else {
-                const float z = Dx * A;
-                const float dz = dl * A;
-                const float zp = z + dz, zm = z - dz;
-                const float zg = Dx * Ag, dzg = dl * Ag;
-                const float zgp = zg + dzg, zgm = zg - dzg;
-                const float e0 = w0 * ex2f(-zg * zg);
-                const float ep = w1 * ex2f(-zgp * zgp);
-                const float em = w1 * ex2f(-zgm * zgm);
-                rho = e0 + ep + em;
-                u1 = fmaf(e0, z, fmaf(ep, zp, em * zm));
-                u2 = fmaf(e0, fmaf(z, z, -1.0f), fmaf(ep, fmaf(zp, zp, -1.0f), em * fmaf(zm, zm, -1.0f)));
+                b1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                bw2 = 0.f;
             }
-            a0 = fmaf(wd0, rho, a0);
-            if (NDS > 1) a1 = fmaf(wd1, rho, a1);
-            if (NDS > 2) a2 = fmaf(wd2, rho, a2);
-            a3 = fmaf(Wj, u1, a3);
-            a4 = fmaf(Wj, u2, a4);
+        };
+        load(jstart + lane);
+        float* my = reinterpret_cast<float*>(sbin) + (long long)warp * 32 * 12;   // 16 pairs x 20 floats
+        const float4* P = reinterpret_cast<const float4*>(my);
+        // per-column constants of the packed path
+        const float2 Av = f2(A), nAv = f2(-A), nmuhv = f2(-c[F_MUH]), nmulv = f2(-c[F_MUL]);
+        const float2 Q2v = f2(Q2), R2v = f2(R2), nR2v = f2(-R2), mL2EAv = f2(mL2EA);
+        const float2 kapv = f2(kap), twokapv = f2(2.0f * kap);
+        const float2 TN0v = f2(TN0), TN1v = f2(TN1), TN2v = f2(TN2);
+        for (int jj0 = jstart; jj0 <= jb; jj0 += 32) {
+            {
+                float* q = my + (lane >> 1) * 20 + (lane & 1);
+                q[0] = b0.x; q[2] = b0.y; q[4] = b0.z; q[6] = b0.w;
+                q[8] = b1.x; q[10] = b1.y; q[12] = b1.z; q[14] = b1.w;
+                if (NDS > 2) q[16] = bw2;
+            }
+            __syncwarp();
+            load(jj0 + 32 + lane);
+            const int nbat = min(32, jb - jj0 + 1);
+            const int npair = (nbat + 1) >> 1;
+            // a4 accumulates -u2
+            float2 a0 = f2(0.f), a1 = a0, a2 = a0, a3 = a0, a4 = a0;
+            if (RES == 1 && wpoly) {
+                // shape >= D_POLY: branch-free series, exponent (d-1) D - t; two bins per instruction
+#pragma unroll 2
+                for (int p = 0; p < npair; ++p) {
+                    const float4 X0 = P[p * 5], X1 = P[p * 5 + 1], X2 = P[p * 5 + 2], X3 = P[p * 5 + 3];
+                    const float2 xc = make_float2(X0.x, X0.y), dl = make_float2(X0.z, X0.w);
+                    const float2 lp = make_float2(X1.x, X1.y), lm = make_float2(X1.z, X1.w);
+                    const float2 w0 = make_float2(X2.x, X2.y), w1 = make_float2(X2.z, X2.w);
+                    const float2 wd0 = make_float2(X3.x, X3.y), wd1 = make_float2(X3.z, X3.w);
+                    float2 wd2 = f2(0.f);
+                    float2 Wj = mul2(wd0, TN0v);
+                    if (NDS > 1) Wj = fma2(wd1, TN1v, Wj);
+                    if (NDS > 2) {
+                        const float4 X4 = P[p * 5 + 4];
+                        wd2 = make_float2(X4.x, X4.y);
+                        Wj = fma2(wd2, TN2v, Wj);
+                    }
+                    const float2 Dx = add2(add2(xc, nmuhv), nmulv);
+                    const float2 tt = mul2(Dx, Av);
+                    const float2 Dt = log1pmx_poly2(tt, mul2(Dx, nAv));
+                    const float2 Ec = fma2(Q2v, Dt, mul2(Dx, mL2EAv));
+                    const float2 ap = fma2(R2v, dl, fma2(Q2v, lp, Ec));
+                    const float2 am = fma2(nR2v, dl, fma2(Q2v, lm, Ec));
+                    const float2 e0 = mul2(w0, ex2f2(Ec));
+                    const float2 ep = mul2(w1, ex2f2(ap));
+                    const float2 em = mul2(w1, ex2f2(am));
+                    const float2 rho = add2(add2(e0, ep), em);
+                    const float2 Ls = fma2(ep, lp, mul2(em, lm));                  // sum w f ln(x_n / x_c)
+                    const float2 XAn = mul2(fma2(ep, f2(-1.f), em), mul2(dl, Av));  // -sum w f (x_n - x_c) / mu
+                    const float2 cmu = fma2(f2(2.f), Dt, add2(tt, twokapv));        // 2 (ln(1+t) + kappa) - t
+                    const float2 u1 = fma2(cmu, rho, fma2(f2(2.f), Ls, XAn));
+                    const float2 nu2 = fma2(add2(Dt, kapv), rho, add2(XAn, Ls));
+                    a0 = fma2(wd0, rho, a0);
+                    if (NDS > 1) a1 = fma2(wd1, rho, a1);
+                    if (NDS > 2) a2 = fma2(wd2, rho, a2);
+                    a3 = fma2(Wj, u1, a3);
+                    a4 = fma2(Wj, nu2, a4);
+                }
+            } else {
+                for (int i = 0; i < nbat; ++i) {
+                    const float* Q = my + (i >> 1) * 20 + (i & 1);
+                    const float xc = Q[0], dl = Q[2], lp = Q[4], lm = Q[6];
+                    const float w0 = Q[8], w1 = Q[10], wd0 = Q[12], wd1 = Q[14];
+                    const float wd2 = NDS > 2 ? Q[16] : 0.f;
+                    const float Wj = fmaf(wd0, TN0, fmaf(wd1, TN1, wd2 * TN2));
+                    const float Dx = (xc - c[F_MUH]) - c[F_MUL];
+                    float rho, u1, u2;
+                    if (RES == 1) {
+                        const float tt = Dx * A;
+                        float L1;
+                        const float Dt = log1pmx2_f(tt, L1);
+                        const float Ec = fmaf(P2, Dt, -L2E * L1);
+                        const float cd = R2 * dl;
+                        const float e0 = w0 * ex2f(Ec);
+                        const float ep = w1 * ex2f(fmaf(Q2, lp, Ec) + cd);
+                        const float em = w1 * ex2f(fmaf(Q2, lm, Ec) - cd);
+                        rho = e0 + ep + em;
+                        const float Ls = fmaf(ep, lp, em * lm);           // sum w f ln(x_n / x_c)
+                        const float XA = (ep - em) * (dl * A);             // sum w f (x_n - x_c) / mu
+                        const float cmu = fmaf(2.0f, L1 + kap, -tt);
+                        u1 = fmaf(cmu, rho, fmaf(2.0f, Ls, -XA));
+                        u2 = fmaf(-(Dt + kap), rho, XA - Ls);
+                    } else {
+                        const float z = Dx * A;
+                        const float dz = dl * A;
+                        const float zp = z + dz, zm = z - dz;
+                        const float zg = Dx * Ag, dzg = dl * Ag;
+                        const float zgp = zg + dzg, zgm = zg - dzg;
+                        const float e0 = w0 * ex2f(-zg * zg);
+                        const float ep = w1 * ex2f(-zgp * zgp);
+                        const float em = w1 * ex2f(-zgm * zgm);
+                        rho = e0 + ep + em;
+                        u1 = fmaf(e0, z, fmaf(ep, zp, em * zm));
+                        u2 = fmaf(e0, fmaf(z, z, -1.0f), fmaf(ep, fmaf(zp, zp, -1.0f), em * fmaf(zm, zm, -1.0f)));
+                    }
+                    a0.x = fmaf(wd0, rho, a0.x);
+                    if (NDS > 1) a1.x = fmaf(wd1, rho, a1.x);
+                    if (NDS > 2) a2.x = fmaf(wd2, rho, a2.x);
+                    a3.x = fmaf(Wj, u1, a3.x);
+                    a4.x = fmaf(Wj, -u2, a4.x);
+                }
+            }
+            two_sum_acc(sU[0], cU[0], a0.x + a0.y);
+            if (NDS > 1) two_sum_acc(sU[1], cU[1], a1.x + a1.y);
+            if (NDS > 2) two_sum_acc(sU[2], cU[2], a2.x + a2.y);
+            two_sum_acc(sU[3], cU[3], a3.x + a3.y);
+            two_sum_acc(sU[4], cU[4], -(a4.x + a4.y));
+            __syncwarp();
         }
-        two_sum_acc(sU[0], cU[0], a0);
-        if (NDS > 1) two_sum_acc(sU[1], cU[1], a1);
-        if (NDS > 2) two_sum_acc(sU[2], cU[2], a2);
-        two_sum_acc(sU[3], cU[3], a3);
-        two_sum_acc(sU[4], cU[4], a4);
-        __syncwarp();
     }
     if (a.work) {
         const unsigned m = __ballot_sync(0xffffffffu, kval);
         if (lane == 0 && jb >= ja) atomicAdd(&a.work[K_BACKWARD], (unsigned long long)(jb - ja + 1) * __popc(m));
     }
-    // chain rule per column: mean and variance derivatives to (LY, kB, a, b, c)
+    // chain rule per column: mean and variance derivatives to (LY, kB, a, b, c); the record is read
+    // again (an L2 hit) rather than kept in registers through the bin loops
+    {
+        const float4* cr = reinterpret_cast<const float4*>(colrec<float>(a, t, g, kval ? k : a.K - 1));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 v = cr[i];
+            c[4 * i] = v.x; c[4 * i + 1] = v.y; c[4 * i + 2] = v.z; c[4 * i + 3] = v.w;
+        }
+    }
     float r[NRESP] = {0, 0, 0, 0, 0}, rc_[NRESP] = {0, 0, 0, 0, 0};
     if (kval) {
         const float U1 = sU[3] + cU[3], U2 = sU[4] + cU[4];
