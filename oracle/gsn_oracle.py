@@ -16,7 +16,13 @@ the method computes, written from the GooStats paper (arXiv:1812.05686):
 * section 4.3: species types Ana (smeared fine spectrum), AnaShift (shifted in
   true energy, then smeared) and AnaPeak (a peak with free position and width);
 * section 2.2: parameter synchronisation across datasets, expressed as a slot
-  map from per-dataset slots to global parameters.
+  map from per-dataset slots to global parameters;
+* section 2.4 (multivariate fit): a second observable splits a dataset into
+  slices, each a histogram of its own with fixed per-slice factors -- a
+  multiplier of each response parameter (LY, kB, a, b, c) and a fraction of
+  each species' rate -- expressed here as per-dataset factors: dataset d uses
+  resp_scale[d][i] * (slot value) for the response and eps_d f_ds r_s for the
+  rates (the workload keys "resp_scale" and "rate_factor"; both default to 1).
 
 Readings (the paper gives no formula for them):
 * quenching: Birks' law E_q(E) = int_0^E dE' / (1 + kB S(E')) with the
@@ -172,6 +178,16 @@ def dataset_values(work, params, d):
     return vals
 
 
+def dataset_factors(work, d):
+    """Fixed factors of dataset d (section 2.4 slices): response multipliers (5,) and rate fractions (S,)."""
+    S = np.asarray(work["spectra"]).shape[0]
+    rs = work.get("resp_scale")
+    rf = work.get("rate_factor")
+    scale = np.ones(5) if rs is None else np.asarray(rs, np.float64)[d]
+    frac = np.ones(S) if rf is None else np.asarray(rf, np.float64)[d]
+    return scale, frac
+
+
 def _unpack(work, vals):
     S = np.asarray(work["spectra"]).shape[0]
     rates = vals[:S]
@@ -203,11 +219,14 @@ def response_matrix(work, edges, resp):
 def expected_per_species(work, params, d):
     """Expected counts per bin and species of dataset d, shape (J, S) (section 3.1 validation quantity).
 
-    Column s holds eps_d r_s sum_k R[j,k] S'[s,k] for Ana/AnaShift species and
-    eps_d r_s * peak_j(m_s, w_s) for AnaPeak species; zero where mask[s, d] = 0.
+    Column s holds eps_d f_ds r_s sum_k R[j,k] S'[s,k] for Ana/AnaShift species and
+    eps_d f_ds r_s * peak_j(m_s, w_s) for AnaPeak species; zero where mask[s, d] = 0.
+    R is built from the response slots times the dataset's response multipliers.
     """
     vals = dataset_values(work, params, d)
     rates, resp, peaks = _unpack(work, vals)
+    scale, frac = dataset_factors(work, d)
+    resp = {k: resp[k] * scale[i] for i, k in enumerate(_RESP)}
     edges = np.asarray(work["edges"][d], np.float64)
     eps = float(work["exposure"][d])
     Sp = species_spectra(work)
@@ -218,9 +237,9 @@ def expected_per_species(work, params, d):
         if not work["mask"][s][d]:
             continue
         if int(work["kind"][s]) == KIND_ANA_PEAK:
-            out[:, s] = eps * rates[s] * peak_profile(edges, peaks[s, 0], peaks[s, 1])
+            out[:, s] = eps * frac[s] * rates[s] * peak_profile(edges, peaks[s, 0], peaks[s, 1])
         else:
-            out[:, s] = eps * rates[s] * (R @ Sp[s])
+            out[:, s] = eps * frac[s] * rates[s] * (R @ Sp[s])
     return out
 
 
@@ -298,6 +317,8 @@ def nll_grad(work, params, counts, windows=None):
             continue
         vals = dataset_values(work, params, d)
         rates, resp, peaks = _unpack(work, vals)
+        scale, frac = dataset_factors(work, d)
+        resp = {k: resp[k] * scale[i] for i, k in enumerate(_RESP)}
         edges = np.asarray(work["edges"][d], np.float64)
         eps = float(work["exposure"][d])
         mask = np.asarray(work["mask"])[:, d].astype(bool)
@@ -309,11 +330,11 @@ def nll_grad(work, params, counts, windows=None):
         # smeared species
         Eq, mu_k, var_k = column_mean_var(work, resp)
         smeared = mask & (np.asarray(work["kind"]) != KIND_ANA_PEAK)
-        T = eps * (rates[smeared][:, None] * Sp[smeared]).sum(axis=0) if smeared.any() else np.zeros(E.size)
+        T = eps * ((frac * rates)[smeared][:, None] * Sp[smeared]).sum(axis=0) if smeared.any() else np.zeros(E.size)
         R = response_matrix(work, edges, resp)
         u = w @ R  # u_k = sum_j w_j R_jk
         for s in np.nonzero(smeared)[0]:
-            gs[s] += eps * float(Sp[s] @ u)
+            gs[s] += eps * frac[s] * float(Sp[s] @ u)
         # response parameters through (mu_k, var_k)
         x = edges[:, None]
         if int(work["resolution"]) == RES_GAUSS:
@@ -344,15 +365,17 @@ def nll_grad(work, params, counts, windows=None):
         gs[base + 2] += float(g_var.sum())
         gs[base + 3] += float(g_var @ mu_k)
         gs[base + 4] += float(g_var @ (mu_k * mu_k))
+        # the slots hold the unscaled parameters: d(scale_i p_i)/dp_i = scale_i
+        gs[base:base + 5] *= scale
         # peak species
         for s in np.nonzero(mask & (np.asarray(work["kind"]) == KIND_ANA_PEAK))[0]:
             m, wd = peaks[s]
             zz = (edges - m) / wd
             ph = np.exp(-0.5 * zz * zz) / math.sqrt(2.0 * math.pi)
             prof = _norm_cdf_diff(zz[:-1], zz[1:])
-            gs[s] += eps * float(w @ prof)
-            gs[base + 5 + 2 * s] += eps * rates[s] * float(w @ (-(ph[1:] - ph[:-1]) / wd))
-            gs[base + 5 + 2 * s + 1] += eps * rates[s] * float(w @ (-(zz[1:] * ph[1:] - zz[:-1] * ph[:-1]) / wd))
+            gs[s] += eps * frac[s] * float(w @ prof)
+            gs[base + 5 + 2 * s] += eps * frac[s] * rates[s] * float(w @ (-(ph[1:] - ph[:-1]) / wd))
+            gs[base + 5 + 2 * s + 1] += eps * frac[s] * rates[s] * float(w @ (-(zz[1:] * ph[1:] - zz[:-1] * ph[:-1]) / wd))
         sm = np.asarray(work["slot_map"])[d]
         for slot, pidx in enumerate(sm):
             if pidx >= 0:

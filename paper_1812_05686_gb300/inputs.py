@@ -32,6 +32,10 @@ slot_map     (D, 3S+5)   global parameter index of each per-dataset slot:
 pull_param/pull_centre/pull_width   Gaussian pull terms (section 4.1, Eq. LL)
 theta0       (P,)        generating parameter point
 param_names  list[str]
+resp_scale   (D, 5)      optional fixed multipliers of the response slots (LY, kB, a, b, c)
+                         of each dataset (section 2.4 slices; default 1)
+rate_factor  (D, S)      optional fixed fraction of each species' rate in each dataset
+                         (section 2.4 slices; default 1)
 """
 from __future__ import annotations
 
@@ -204,6 +208,63 @@ def borexino_like(seed: int = 2, n_bins: int = 1000, n_fine: int = 20000, e_max:
         pull_centre=np.array([0.011, m0]), pull_width=np.array([0.002, 2.0]),
         theta0=theta0,
         param_names=[f"r_{n}" for n in names] + ["LY", "kB", "a", "b", "c", "m_alpha", "w_alpha"],
+    )
+
+
+def multivariate_like(seed: int = 5, n_datasets: int = 4, n_slices: int = 64, n_bins: int = 1000,
+                      n_fine: int = 50000, n_species: int = 32, e_max: float = 2.0) -> dict:
+    """Two-dimensional workload: energy x a second observable (radial / pulse-shape slices).
+
+    Each of n_datasets histograms is split into n_slices slices along the second
+    observable (section 2.4); slice q of dataset d is dataset index d * n_slices + q,
+    with n_bins energy bins of 1 p.e.  Every species has a seeded slice-fraction
+    template f_s(q) (positive, summing to 1 over the slices: a random walk in log
+    space, so neighbouring slices are alike), and every slice fixed multipliers of
+    the light yield (lambda_q, U[0.95, 1.05]) and of the resolution constant term
+    (alpha_q, U[0.8, 1.2]); the free parameters are global.  n_species species on
+    a 2 MeV grid of n_fine points (betas, lines, shoulders, exponentials, flats in
+    turn), gamma resolution a = 10, b = 1.1, c = 2e-4, exposures 1, 0.8, 0.6, 0.4, ...
+    Parameters: n_species rates, LY, kB, a, b, c; a pull on kB.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    E = fine_grid(n_fine, e_max)
+    rows, names = [], []
+    makers = (lambda: shape_beta(E, rng.uniform(0.3, 2.0)), lambda: shape_line(E, rng.uniform(0.2, 1.6)),
+              lambda: shape_shoulder(E, rng.uniform(0.3, 1.4)), lambda: shape_expo(E, rng.uniform(0.1, 1.0)),
+              lambda: shape_flat(E))
+    tags = ("beta", "line", "shoulder", "expo", "flat")
+    for i in range(n_species):
+        rows.append(makers[i % 5]())
+        names.append(f"{tags[i % 5]}{i // 5}")
+    S = n_species
+    D = n_datasets * n_slices
+    frac = np.empty((S, n_slices))
+    for s_ in range(S):
+        walk = np.cumsum(rng.normal(0.0, 0.15, size=n_slices))
+        f = np.exp(walk - walk.max())
+        frac[s_] = f / f.sum()
+    lam = rng.uniform(0.95, 1.05, size=n_slices)
+    alp = rng.uniform(0.8, 1.2, size=n_slices)
+    resp_scale = np.ones((D, 5))
+    rate_factor = np.empty((D, S))
+    for d in range(n_datasets):
+        for q in range(n_slices):
+            resp_scale[d * n_slices + q, 0] = lam[q]
+            resp_scale[d * n_slices + q, 2] = alp[q]
+            rate_factor[d * n_slices + q] = frac[:, q]
+    exposure = np.repeat(1.0 - 0.2 * (np.arange(n_datasets) % 5), n_slices)
+    rates = 10.0 ** rng.uniform(3.0, 6.0, size=S)
+    theta0 = np.concatenate([rates, [500.0, 0.011, 10.0, 1.1, 2e-4]])
+    return dict(
+        name=f"multivariate_like_{n_datasets}x{n_slices}x{n_bins}x{n_fine}",
+        fine_centres=E, spectra=np.array(rows), kind=np.zeros(S, np.int32), shift=np.zeros(S),
+        mask=np.ones((S, D), np.uint8), edges=[unit_edges(n_bins) for _ in range(D)], exposure=exposure,
+        win_lo=np.zeros(D, np.int32), win_hi=np.full(D, n_bins, np.int32),
+        resolution=RES_GAMMA, birks_s0=BIRKS_S0, birks_s1=BIRKS_S1,
+        n_params=S + 5, slot_map=_slot_map_shared(S, D),
+        pull_param=np.array([S + 1], np.int32), pull_centre=np.array([0.011]), pull_width=np.array([0.002]),
+        theta0=theta0, param_names=[f"r_{n}" for n in names] + ["LY", "kB", "a", "b", "c"],
+        resp_scale=resp_scale, rate_factor=rate_factor, n_slices=n_slices,
     )
 
 

@@ -323,3 +323,87 @@ def test_planted_mistake_is_caught(monkeypatch, name):
     except Exception:
         caught.append(True)
     assert any(caught), f"no pin caught the planted mistake '{name}'"
+
+
+# ------------------------------------------- multivariate slices (section 2.4) --------
+def _mv_small(unit_response=False):
+    w = I.multivariate_like(seed=5, n_datasets=2, n_slices=3, n_bins=90, n_fine=900, n_species=5)
+    if unit_response:
+        w = dict(w, resp_scale=np.ones_like(w["resp_scale"]))
+    return w
+
+
+def _unsplit(w):
+    """The same histograms without the second observable: one dataset per slice group, no factors."""
+    Q = w["n_slices"]
+    D = len(w["edges"]) // Q
+    S = w["spectra"].shape[0]
+    one = {k: v for k, v in w.items() if k not in ("resp_scale", "rate_factor")}
+    one.update(edges=w["edges"][::Q], exposure=w["exposure"][::Q], mask=np.ones((S, D), np.uint8),
+               win_lo=w["win_lo"][::Q], win_hi=w["win_hi"][::Q], slot_map=w["slot_map"][::Q])
+    return one
+
+
+def pin_slices_sum_to_unsplit():
+    """Slices with unit response multipliers and rate fractions summing to 1 add up to the unsplit histogram."""
+    w = _mv_small(unit_response=True)
+    one = _unsplit(w)
+    Q = w["n_slices"]
+    p = I.perturbed_points(w["theta0"], 1, 7)[0]
+    worst = 0.0
+    for d in range(len(one["edges"])):
+        tot = sum(O.expected_counts(w, p, d * Q + q) for q in range(Q))
+        ref = O.expected_counts(one, p, d)
+        worst = max(worst, float(np.max(np.abs(tot - ref)) / ref.max()))
+    return worst
+
+
+def pin_multipliers_are_scaled_parameters():
+    """A slice's factors act as the scaled parameters would: LY x lambda, a x alpha, rate x fraction."""
+    w = _mv_small()
+    plain = {k: v for k, v in w.items() if k not in ("resp_scale", "rate_factor")}
+    S = w["spectra"].shape[0]
+    p = I.perturbed_points(w["theta0"], 1, 8)[0]
+    worst = 0.0
+    for d in (1, 4):
+        q = p.copy()
+        q[S] *= w["resp_scale"][d, 0]
+        q[S + 2] *= w["resp_scale"][d, 2]
+        q[:S] *= w["rate_factor"][d]
+        got, ref = O.expected_counts(w, p, d), O.expected_counts(plain, q, d)
+        worst = max(worst, float(np.max(np.abs(got - ref)) / ref.max()))
+    return worst
+
+
+def test_slices_sum_to_unsplit_histogram():
+    assert pin_slices_sum_to_unsplit() < 1e-12
+
+
+def test_slice_multipliers_act_as_scaled_parameters():
+    assert pin_multipliers_are_scaled_parameters() < 1e-12
+
+
+def test_multivariate_gradient_matches_finite_differences():
+    """Chain rule through the slice multipliers and fractions against Richardson differences."""
+    w = _mv_small()
+    mu = np.concatenate([O.expected_counts(w, w["theta0"], d) for d in range(len(w["edges"]))])
+    n = I.poisson_counts(mu, 23)
+    p = I.perturbed_points(w["theta0"], 1, 24, rel=0.02)[0]
+    g = O.nll_grad(w, p, n)
+    gf = O.nll_grad_fd(w, p, n, rel=1e-4)
+    scale = np.abs(g) + 1e-3 * np.max(np.abs(g))
+    assert np.max(np.abs(g - gf) / scale) < 2e-6
+
+
+_factors = O.dataset_factors
+FACTOR_MUTANTS = {
+    "response multipliers dropped": lambda w, d: (np.ones(5), _factors(w, d)[1]),
+    "rate fractions dropped": lambda w, d: (_factors(w, d)[0], np.ones_like(_factors(w, d)[1])),
+    "multipliers on the wrong slot": lambda w, d: (np.roll(_factors(w, d)[0], 1), _factors(w, d)[1]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FACTOR_MUTANTS))
+def test_planted_factor_mistake_is_caught(monkeypatch, name):
+    monkeypatch.setattr(O, "dataset_factors", FACTOR_MUTANTS[name])
+    assert pin_slices_sum_to_unsplit() > 1e-6 or pin_multipliers_are_scaled_parameters() > 1e-6
