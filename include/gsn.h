@@ -8,14 +8,17 @@
  *   NLL(theta) = sum_d sum_{j in window_d} [ mu_dj - n_dj + n_dj ln(n_dj / mu_dj) ]
  *                + 1/2 sum_p ((theta_p - c_p) / sigma_p)^2
  *
- *   mu_dj = eps_d [ sum_{s smeared} r_s sum_k R_jk(theta) S'_sk
- *                   + sum_{s peak} r_s int_{bin j} N(x; m_s, w_s) dx ]
+ *   mu_dj = eps_d [ sum_{s smeared} f_ds r_s sum_k R_jk(theta) S'_sk
+ *                   + sum_{s peak} f_ds r_s int_{bin j} N(x; m_s, w_s) dx ]
  *
  * with R_jk the bin integral of the analytic detector response of fine
  * true-energy column k (section 2.3): visible mean mu_k = LY * E_q(E_k; kB)
  * (Birks quenching with stopping power S(E) = s0 + s1/E), variance
  * sigma_k^2 = a + b mu_k + c mu_k^2, and either a Gaussian or the
- * moment-matched gamma ("generalized gamma") resolution.  n = 0 bins
+ * moment-matched gamma ("generalized gamma") resolution.  f_ds (default 1)
+ * and fixed multipliers of the response parameters of each dataset describe
+ * the slices of a multivariate fit (section 2.4, gsn_set_dataset_factors).
+ * n = 0 bins
  * contribute mu.  The data-only constant of -ln L is dropped, so NLL = 0 for
  * data equal to the model and an increase of 0.5 is one standard deviation.
  *
@@ -76,8 +79,10 @@ extern "C" {
 #define GSN_SLOT_M(S, s)  ((S) + 5 + 2 * (s))
 #define GSN_SLOT_W(S, s)  ((S) + 6 + 2 * (s))
 
-#define GSN_MAX_DATASETS  8
+#define GSN_MAX_DATASETS  512  /* histograms, or slices of histograms (section 2.4) */
 #define GSN_MAX_SPECIES   64
+#define GSN_MAX_GROUPS    256  /* distinct (edges, response slots, response multipliers);
+                                  at most 3 datasets share one response evaluation */
 
 typedef struct gsn_ctx gsn_ctx;
 
@@ -162,6 +167,24 @@ int gsn_set_species(gsn_ctx* ctx, int n_species, int n_fine, const double* fine_
  * Requires gsn_set_species first. */
 int gsn_set_params(gsn_ctx* ctx, int n_params, const int* slot_map, int n_pulls,
                    const int* pull_param, const double* pull_centre, const double* pull_width);
+
+/* Fixed per-dataset factors of a multivariate fit (section 2.4): a second
+ * observable (radial position, pulse shape, ...) splits each histogram into
+ * slices, passed to gsn_set_data as datasets of their own; every slice scales
+ * the response parameters and takes a fraction of each species' rate.
+ *   resp_scale   [n_datasets][5] multipliers of (LY, kB, a, b, c): dataset d
+ *                evaluates its response at resp_scale[d][i] * (slot value); > 0,
+ *                finite.  NULL: all 1.
+ *   rate_factor  [n_datasets][n_species] f_ds >= 0, finite: species s enters
+ *                dataset d as eps_d f_ds r_s (on top of the species mask).
+ *                NULL: all 1.
+ * Call after gsn_set_data and gsn_set_species; n_datasets and n_species must
+ * match them.  The factors stay until a later gsn_set_data or gsn_set_species
+ * changes the number of datasets or species (then they return to 1).  The
+ * gradient is with respect to the unscaled global parameters.
+ * Errors: GSN_ERR_ARG (sizes, values), GSN_ERR_STATE (data or species missing). */
+int gsn_set_dataset_factors(gsn_ctx* ctx, int n_datasets, int n_species, const double* resp_scale,
+                            const double* rate_factor);
 
 /* NLL at params[n_params] with the counts and windows of gsn_set_data.
  * Errors: GSN_ERR_NONPOSITIVE_MU (nll = +inf), GSN_ERR_NONFINITE. */

@@ -41,12 +41,15 @@ struct gsn_ctx {
     std::vector<unsigned char> mask;  // [S][D]
     int P = 0;
     std::vector<int> slot_map;
+    std::vector<double> rscale;       // [D][5] response multipliers of each dataset (section 2.4 slices)
+    std::vector<double> rfrac;        // [D][S] rate fraction of each species in each dataset
     std::vector<int> pull_p;
     std::vector<double> pull_c, pull_w;
     bool have_data = false, have_species = false, have_params = false, ready = false;
     // derived
     int G = 0, total_bins = 0, Jmax = 0;
     KArgs base{};
+    Tables tab{};                     // host copy of the device problem tables
     // persistent device buffers
     std::vector<Buf> owned;
     // scratch
@@ -202,38 +205,50 @@ int finalize(gsn_ctx* c) {
     a.cut = c->opt.band_cut;
     a.s0 = c->opt.birks_s0; a.s1 = c->opt.birks_s1;
     a.n_pulls = (int)c->pull_p.size();
-    // species
-    for (int s = 0; s < c->S; ++s) {
-        a.sp_kind[s] = c->kind[s];
-        unsigned m = 0;
-        for (int d = 0; d < c->D; ++d) if (c->mask[s * c->D + d]) m |= 1u << d;
-        a.sp_mask[s] = m;
-    }
-    // response groups: identical edges and identical response slots
-    std::vector<int> gfirst;
+    if (c->rscale.size() != (size_t)c->D * NRESP) c->rscale.assign((size_t)c->D * NRESP, 1.0);
+    if (c->rfrac.size() != (size_t)c->D * c->S) c->rfrac.assign((size_t)c->D * c->S, 1.0);
+    Tables& tb = c->tab;
+    tb = Tables{};
+    // species; rate coefficient eps_d f_ds of every (dataset, species), 0 where absent
+    for (int s = 0; s < c->S; ++s) tb.sp_kind[s] = c->kind[s];
+    std::vector<double> rfac((size_t)c->D * c->S, 0.0);
+    for (int d = 0; d < c->D; ++d)
+        for (int s = 0; s < c->S; ++s) {
+            if (!c->mask[s * c->D + d]) continue;
+            rfac[(size_t)d * c->S + s] = c->eps[d] * c->rfrac[(size_t)d * c->S + s];
+            if (c->kind[s] == GSN_ANA_PEAK && rfac[(size_t)d * c->S + s] != 0.0) ++tb.ds_npk[d];
+        }
+    // response groups: identical edges, response slots and response multipliers (at most MAXGDS each)
     c->G = 0;
     int off = 0;
+    a.max_nds = 1;
     for (int d = 0; d < c->D; ++d) {
-        a.ds_bins[d] = c->nb[d]; a.ds_off[d] = off; a.ds_eps[d] = c->eps[d];
+        tb.ds_bins[d] = c->nb[d]; tb.ds_off[d] = off;
         off += c->nb[d];
         int gsel = -1;
         for (int g = 0; g < c->G && gsel < 0; ++g) {
-            const int d0 = a.g_ds[g][0];
-            if (a.g_nds[g] >= MAXGDS || c->edges[d0] != c->edges[d]) continue;
+            const int d0 = tb.g_ds[g][0];
+            if (tb.g_nds[g] >= MAXGDS || c->edges[d0] != c->edges[d]) continue;
             bool same = true;
             for (int i = 0; i < NRESP; ++i)
-                same = same && c->slot_map[d0 * NSLOT + c->S + i] == c->slot_map[d * NSLOT + c->S + i];
+                same = same && c->slot_map[d0 * NSLOT + c->S + i] == c->slot_map[d * NSLOT + c->S + i] &&
+                       c->rscale[d0 * NRESP + i] == c->rscale[d * NRESP + i];
             if (same) gsel = g;
         }
         if (gsel < 0) {
-            if (c->G >= MAXG) return fail(c, GSN_ERR_ARG, "too many distinct response groups");
+            if (c->G >= MAXG)
+                return fail(c, GSN_ERR_ARG, "more than " + std::to_string(MAXG) + " distinct response groups");
             gsel = c->G++;
-            a.g_nds[gsel] = 0;
-            for (int i = 0; i < NRESP; ++i) a.g_resp[gsel][i] = c->slot_map[d * NSLOT + c->S + i];
+            tb.g_nds[gsel] = 0;
+            for (int i = 0; i < NRESP; ++i) {
+                tb.g_resp[gsel][i] = c->slot_map[d * NSLOT + c->S + i];
+                tb.g_rscale[gsel][i] = c->rscale[d * NRESP + i];
+            }
         }
-        a.ds_group[d] = gsel;
-        a.ds_in_group[d] = a.g_nds[gsel];
-        a.g_ds[gsel][a.g_nds[gsel]++] = d;
+        tb.ds_group[d] = gsel;
+        tb.ds_in_group[d] = tb.g_nds[gsel];
+        tb.g_ds[gsel][tb.g_nds[gsel]++] = d;
+        a.max_nds = std::max(a.max_nds, tb.g_nds[gsel]);
     }
     c->total_bins = off;
     a.total_bins = off;
@@ -251,15 +266,15 @@ int finalize(gsn_ctx* c) {
     c->Jmax = 0;
     int noff = 0;
     for (int g = 0; g < c->G; ++g) {
-        const std::vector<double>& x = c->edges[a.g_ds[g][0]];
+        const std::vector<double>& x = c->edges[tb.g_ds[g][0]];
         const int J = (int)x.size() - 1;
-        a.g_bins[g] = J;
-        a.g_edge_off[g] = (int)edges_all.size();
-        a.g_node_off[g] = noff;
-        a.g_zero[g] = (gamma && x[0] == 0.0) ? 1 : 0;
-        a.g_jlin[g] = 0;
+        tb.g_bins[g] = J;
+        tb.g_edge_off[g] = (int)edges_all.size();
+        tb.g_node_off[g] = noff;
+        tb.g_zero[g] = (gamma && x[0] == 0.0) ? 1 : 0;
+        tb.g_jlin[g] = 0;
         if (gamma)
-            while (a.g_jlin[g] < J && !(x[a.g_jlin[g]] >= xlog && x[a.g_jlin[g]] > 0.0)) ++a.g_jlin[g];
+            while (tb.g_jlin[g] < J && !(x[tb.g_jlin[g]] >= xlog && x[tb.g_jlin[g]] > 0.0)) ++tb.g_jlin[g];
         c->Jmax = std::max(c->Jmax, J);
         edges_all.insert(edges_all.end(), x.begin(), x.end());
         for (int j = 0; j < J; ++j) {
@@ -331,7 +346,25 @@ int finalize(gsn_ctx* c) {
         noff += J;
     }
     a.Jmax = c->Jmax;
+    // kernel-parameter copy of the first groups and datasets
+    a.fast = (c->G <= FASTG && c->D <= FASTD) ? 1 : 0;
+    for (int g = 0; g < std::min(c->G, FASTG); ++g) {
+        a.ft.g_nds[g] = tb.g_nds[g];
+        for (int i = 0; i < MAXGDS; ++i) a.ft.g_ds[g][i] = tb.g_ds[g][i];
+        a.ft.g_bins[g] = tb.g_bins[g]; a.ft.g_edge_off[g] = tb.g_edge_off[g]; a.ft.g_node_off[g] = tb.g_node_off[g];
+        a.ft.g_jlin[g] = tb.g_jlin[g]; a.ft.g_zero[g] = tb.g_zero[g];
+        for (int i = 0; i < NRESP; ++i) { a.ft.g_resp[g][i] = tb.g_resp[g][i]; a.ft.g_rscale[g][i] = tb.g_rscale[g][i]; }
+    }
+    for (int s = 0; s < c->S; ++s) a.ft.sp_kind[s] = tb.sp_kind[s];
+    for (int d = 0; d < std::min(c->D, FASTD); ++d) {
+        a.ft.ds_off[d] = tb.ds_off[d]; a.ft.ds_bins[d] = tb.ds_bins[d]; a.ft.ds_group[d] = tb.ds_group[d];
+    }
     int rc;
+    {
+        const std::vector<Tables> tv(1, tb);
+        if ((rc = upload(c, tv, &a.tb))) return rc;
+    }
+    if ((rc = upload(c, rfac, &a.rfac))) return rc;
     if ((rc = upload(c, edges_all, &a.edges))) return rc;
     if ((rc = upload(c, bcls, &a.bclass))) return rc;
     if (mixed) {
@@ -610,7 +643,12 @@ int batch_device(gsn_ctx* c, int n_toys, const double* params, const double* cou
                  double* nll, double* grad, int* status) {
     int rc;
     if ((rc = finalize(c))) return rc;
-    const int chunk = std::max(1, c->opt.max_toys_per_launch);
+    // toys per launch: the option, the grid limit of the forward (toys x groups <= 65535) and a
+    // 32 GiB bound on the column records (16 words per toy, group and fine column)
+    const size_t rec = (size_t)c->G * c->K * NFP * (c->opt.precision == GSN_MIXED ? sizeof(float) : sizeof(double));
+    const long long mem_cap = std::max<long long>(1, (long long)((size_t)32 << 30) / (long long)std::max<size_t>(rec, 1));
+    const int chunk = (int)std::max<long long>(1, std::min<long long>({(long long)c->opt.max_toys_per_launch,
+                                                                        65535LL / std::max(1, c->G), mem_cap}));
     const bool g = grad != nullptr;
     std::vector<KArgs> args;
     std::vector<Plan> plans;
@@ -682,7 +720,7 @@ int gsn_create(gsn_ctx** out, const gsn_options* opt) {
     if (!(o.birks_s0 > 0)) o.birks_s0 = 1.55;
     if (o.birks_s1 < 0) o.birks_s1 = 0.155;
     if (o.max_toys_per_launch <= 0) o.max_toys_per_launch = 4096;
-    o.max_toys_per_launch = std::min(o.max_toys_per_launch, 65535 / MAXG);
+    o.max_toys_per_launch = std::min(o.max_toys_per_launch, 65535);
     c->dev = o.device;
     if (cudaSetDevice(c->dev) != cudaSuccess) { cudaGetLastError(); delete c; return GSN_ERR_CUDA; }
     if (o.stream) {
@@ -805,6 +843,7 @@ int gsn_set_data(gsn_ctx* c, int n_datasets, const int* n_bins, const double* co
         lo[d] = win_lo[d]; hi[d] = win_hi[d];
     }
     if (c->have_species && n_datasets != c->D) c->have_species = c->have_params = false;
+    if (n_datasets != c->D) { c->rscale.clear(); c->rfrac.clear(); }
     c->D = n_datasets; c->nb = nb; c->edges = ed; c->counts = cn; c->eps = ex; c->wlo = lo; c->whi = hi;
     c->have_data = true;
     c->ready = false;
@@ -853,6 +892,7 @@ int gsn_set_species(gsn_ctx* c, int n_species, int n_fine, const double* fine_ce
         for (int s = 0; s < n_species; ++s) np += (kd[s] == GSN_ANA_PEAK && dataset_mask[(size_t)s * c->D + d]) ? 1 : 0;
         if (np > 8) return fail(c, GSN_ERR_ARG, "at most 8 AnaPeak species per dataset");
     }
+    if (n_species != c->S) c->rfrac.clear();
     c->S = n_species; c->K = n_fine; c->E = E; c->Sn = Sn; c->kind = kd;
     c->mask.assign(dataset_mask, dataset_mask + (size_t)n_species * c->D);
     c->have_species = true;
@@ -886,6 +926,30 @@ int gsn_set_params(gsn_ctx* c, int n_params, const int* slot_map, int n_pulls, c
         if (pp[i] < 0 || pp[i] >= n_params || !(pw[i] > 0)) return fail(c, GSN_ERR_ARG, "bad pull term");
     c->P = n_params; c->slot_map = sm; c->pull_p = pp; c->pull_c = pc; c->pull_w = pw;
     c->have_params = true;
+    c->ready = false;
+    return GSN_OK;
+}
+
+int gsn_set_dataset_factors(gsn_ctx* c, int n_datasets, int n_species, const double* resp_scale,
+                            const double* rate_factor) {
+    if (!c) return GSN_ERR_ARG;
+    if (!c->have_data || !c->have_species)
+        return fail(c, GSN_ERR_STATE, "gsn_set_data and gsn_set_species must come before the dataset factors");
+    if (n_datasets != c->D || n_species != c->S)
+        return fail(c, GSN_ERR_ARG, "n_datasets / n_species differ from gsn_set_data / gsn_set_species");
+    std::vector<double> rs((size_t)c->D * NRESP, 1.0), rf((size_t)c->D * c->S, 1.0);
+    if (resp_scale) {
+        rs.assign(resp_scale, resp_scale + rs.size());
+        for (double v : rs)
+            if (!(v > 0.0) || !std::isfinite(v)) return fail(c, GSN_ERR_ARG, "resp_scale must be finite and > 0");
+    }
+    if (rate_factor) {
+        rf.assign(rate_factor, rate_factor + rf.size());
+        for (double v : rf)
+            if (!(v >= 0.0) || !std::isfinite(v)) return fail(c, GSN_ERR_ARG, "rate_factor must be finite and >= 0");
+    }
+    c->rscale = rs;
+    c->rfrac = rf;
     c->ready = false;
     return GSN_OK;
 }
@@ -1006,7 +1070,7 @@ int gsn_eval(gsn_ctx* c, const double* params, double* nll) {
     CUDA_TRY(c, cudaMemcpyAsync(c->params.p, params, c->P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     std::vector<double> key;
     for (int g = 0; g < c->G; ++g)
-        for (int i = 0; i < NRESP; ++i) key.push_back(params[c->base.g_resp[g][i]]);
+        for (int i = 0; i < NRESP; ++i) key.push_back(params[c->tab.g_resp[g][i]]);
     const bool hit = c->cache_valid && key.size() == c->cache_key.size() &&
                      std::memcmp(key.data(), c->cache_key.data(), key.size() * sizeof(double)) == 0;
     if (!hit) {
@@ -1052,6 +1116,7 @@ int gsn_expected(gsn_ctx* c, const double* params, int dataset, double* mu_per_s
     a.Mbuf = (double*)c->Mbuf.p;
     a.out_species = (double*)c->outbuf.p;
     a.out_dataset = dataset;
+    a.out_bins = c->nb[dataset];
     if ((rc = launch(c, K_SPECIES, a, launch_expected_out))) return rc;
     CUDA_TRY(c, cudaMemcpyAsync(mu_per_species, c->outbuf.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));

@@ -26,6 +26,21 @@ constexpr float NORM_HI = (float)NORM_D;
 constexpr float NORM_LO = (float)(NORM_D - (double)NORM_HI);
 constexpr int FWD_WARPS = 8;
 
+// problem-table reads: the kernel-parameter copy for the first groups / datasets, else device memory;
+// FAST = true (problems of at most FASTG groups and FASTD datasets) reads the copy unconditionally
+template <bool FAST = false> DEV int tb_g_nds(const KArgs& a, int g) { return (FAST || g < FASTG) ? a.ft.g_nds[g] : a.tb->g_nds[g]; }
+template <bool FAST = false> DEV int tb_g_ds(const KArgs& a, int g, int i) { return (FAST || g < FASTG) ? a.ft.g_ds[g][i] : a.tb->g_ds[g][i]; }
+template <bool FAST = false> DEV int tb_g_bins(const KArgs& a, int g) { return (FAST || g < FASTG) ? a.ft.g_bins[g] : a.tb->g_bins[g]; }
+template <bool FAST = false> DEV int tb_g_edge_off(const KArgs& a, int g) { return (FAST || g < FASTG) ? a.ft.g_edge_off[g] : a.tb->g_edge_off[g]; }
+template <bool FAST = false> DEV int tb_g_node_off(const KArgs& a, int g) { return (FAST || g < FASTG) ? a.ft.g_node_off[g] : a.tb->g_node_off[g]; }
+template <bool FAST = false> DEV int tb_g_jlin(const KArgs& a, int g) { return (FAST || g < FASTG) ? a.ft.g_jlin[g] : a.tb->g_jlin[g]; }
+template <bool FAST = false> DEV int tb_g_zero(const KArgs& a, int g) { return (FAST || g < FASTG) ? a.ft.g_zero[g] : a.tb->g_zero[g]; }
+template <bool FAST = false> DEV int tb_g_resp(const KArgs& a, int g, int i) { return (FAST || g < FASTG) ? a.ft.g_resp[g][i] : a.tb->g_resp[g][i]; }
+template <bool FAST = false> DEV double tb_g_rscale(const KArgs& a, int g, int i) { return (FAST || g < FASTG) ? a.ft.g_rscale[g][i] : a.tb->g_rscale[g][i]; }
+template <bool FAST = false> DEV int tb_ds_off(const KArgs& a, int d) { return (FAST || d < FASTD) ? a.ft.ds_off[d] : a.tb->ds_off[d]; }
+template <bool FAST = false> DEV int tb_ds_bins(const KArgs& a, int d) { return (FAST || d < FASTD) ? a.ft.ds_bins[d] : a.tb->ds_bins[d]; }
+template <bool FAST = false> DEV int tb_ds_group(const KArgs& a, int d) { return (FAST || d < FASTD) ? a.ft.ds_group[d] : a.tb->ds_group[d]; }
+
 // ------------------------------------------------------------------ math --
 DEV float ex2f(float x) {  // 2^x on the SFU
     float y;
@@ -148,11 +163,12 @@ DEV double block_sum_d(double v, double* sh) {
     return s;
 }
 
+template <bool FAST = false>
 DEV void toy_window_union(const KArgs& a, int t, int g, int& wlo, int& whi) {
-    const int J = a.g_bins[g];
+    const int J = tb_g_bins<FAST>(a, g);
     wlo = J; whi = 0;
-    for (int dd = 0; dd < a.g_nds[g]; ++dd) {
-        const int d = a.g_ds[g][dd];
+    for (int dd = 0; dd < tb_g_nds<FAST>(a, g); ++dd) {
+        const int d = tb_g_ds<FAST>(a, g, dd);
         int lo = a.win[t * a.win_stride + 2 * d], hi = a.win[t * a.win_stride + 2 * d + 1];
         lo = max(lo, 0); hi = min(hi, J);
         if (hi > lo) { wlo = min(wlo, lo); whi = max(whi, hi); }

@@ -5,9 +5,9 @@
 
 namespace gsn {
 
-constexpr int MAXD = 8;      // datasets
+constexpr int MAXD = 512;    // datasets (histograms, or slices of histograms along a second observable)
 constexpr int MAXS = 64;     // species
-constexpr int MAXG = 8;      // response groups
+constexpr int MAXG = 256;    // response groups
 constexpr int MAXGDS = 3;    // datasets sharing one response group
 
 // Gauss-Legendre nodes per bin.  Mixed: 3 linear nodes, 6 log-spaced nodes for
@@ -39,6 +39,30 @@ static_assert(F_TN0 + MAXGDS <= NFP, "column record too small");
 
 constexpr int NRESP = 5;  // LY, kB, a, b, c
 
+// Problem tables, in device memory (uploaded once per problem, read by every kernel).
+struct Tables {
+    int ds_bins[MAXD], ds_off[MAXD], ds_group[MAXD], ds_in_group[MAXD];
+    int ds_npk[MAXD];           // AnaPeak species present in the dataset
+    int g_nds[MAXG], g_ds[MAXG][MAXGDS], g_bins[MAXG], g_edge_off[MAXG], g_node_off[MAXG];
+    int g_resp[MAXG][NRESP];    // global parameter of each response slot
+    int g_zero[MAXG];           // first edge of the group is 0 (gamma bin-at-zero)
+    int g_jlin[MAXG];           // first bin of the group from which every bin is linear
+    double g_rscale[MAXG][NRESP];  // fixed multipliers of the response parameters (section 2.4 slices)
+    int sp_kind[MAXS];
+};
+
+// Copy of the first FASTG groups and FASTD datasets of Tables, carried in the kernel parameters
+// (constant bank): the prologues of the response kernels read these values before their first
+// memory access, and problems of up to 8 datasets then need no device-table round trip.
+constexpr int FASTG = 8, FASTD = 8;
+struct FastTables {
+    int g_nds[FASTG], g_ds[FASTG][MAXGDS], g_bins[FASTG], g_edge_off[FASTG], g_node_off[FASTG];
+    int g_jlin[FASTG], g_zero[FASTG], g_resp[FASTG][NRESP];
+    double g_rscale[FASTG][NRESP];
+    int ds_off[FASTD], ds_bins[FASTD], ds_group[FASTD];
+    int sp_kind[MAXS];          // complete (the species count is at most MAXS)
+};
+
 struct KArgs {
     // problem
     int T, D, S, K, P, NSLOT, G, total_bins, nsplit, n_pulls;
@@ -46,14 +70,12 @@ struct KArgs {
     int precision;    // 0 fp64, 1 mixed
     double cut;       // band cut on the log-density
     double s0, s1;    // stopping power model
-    int ds_bins[MAXD], ds_off[MAXD], ds_group[MAXD], ds_in_group[MAXD];
-    double ds_eps[MAXD];
-    int g_nds[MAXG], g_ds[MAXG][MAXGDS], g_bins[MAXG], g_edge_off[MAXG], g_node_off[MAXG];
-    int g_resp[MAXG][NRESP];
-    int g_zero[MAXG];           // first edge of the group is 0 (gamma bin-at-zero)
-    int sp_kind[MAXS];
-    unsigned sp_mask[MAXS];     // bit d set when species contributes to dataset d
+    int max_nds;                // most datasets in one response group
+    int fast;                   // every group and dataset is in the kernel-parameter copy ft
+    FastTables ft;
     // device-resident problem arrays
+    const Tables* tb;
+    const double* rfac;         // [D][S] rate coefficient eps_d f_ds of species s in dataset d (0: absent)
     const double* edges;        // per group, J_g + 1 edges, concatenated
     const float* ntab_f;        // [bin][3][NGM_F]: offset from centre, ln(x/xc), weight
     const float* xc_f;          // [bin] bin centre
@@ -61,7 +83,6 @@ struct KArgs {
     const double* ntab_d;       // [bin][3][NGM_D]: x, ln x, weight
     const float* btab_f;        // [bin][8] linear bins, symmetric 3-node rule: xc, offset, ln(1+offset/xc),
                                 // ln(1-offset/xc), centre weight, side weight, -, -
-    int g_jlin[MAXG];           // first bin of the group from which every bin is linear
     const double* E;            // fine centres [K]
     const float* E_hi;          // double-float split of E
     const float* E_lo;
@@ -97,7 +118,7 @@ struct KArgs {
     int Jmax;
     int sp_first, sp_count;
     double* out_species;   // [J][S] for gsn_expected
-    int out_dataset;
+    int out_dataset, out_bins;
     // statistics: evaluated (bin, column) pairs per kernel class (NULL = off)
     unsigned long long* work;
     // tensor-core per-species contraction

@@ -24,7 +24,7 @@
 namespace gsn {
 
 // ------------------------------------------------------------- columns -----
-template <class R, int RES>
+template <class R, int RES, bool FAST>
 __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
     const int t = blockIdx.z, g = blockIdx.y;
     const int k = blockIdx.x * COLBLK + threadIdx.x;
@@ -35,15 +35,16 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
     __shared__ float sdf[8];      // per-toy double-float constants (mixed)
     __shared__ R sred[2][COLBLK / 32];
     const double* prm = a.params + (long long)t * a.params_stride;
-    if (threadIdx.x < NRESP) sres[threadIdx.x] = prm[a.g_resp[g][threadIdx.x]];
+    if (threadIdx.x < NRESP) sres[threadIdx.x] = prm[tb_g_resp<FAST>(a, g, threadIdx.x)] * tb_g_rscale<FAST>(a, g, threadIdx.x);
     for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
         const int dd = i / a.S, s = i % a.S;
         double v = 0.0;
-        if (dd < a.g_nds[g]) {
-            const int d = a.g_ds[g][dd];
-            if (a.sp_kind[s] != 2 && ((a.sp_mask[s] >> d) & 1u)) {
+        if (dd < tb_g_nds<FAST>(a, g)) {
+            const int d = tb_g_ds<FAST>(a, g, dd);
+            const double f = a.rfac[d * a.S + s];
+            if (a.ft.sp_kind[s] != 2 && f != 0.0) {
                 const int p = a.slot_map[d * a.NSLOT + s];
-                if (p >= 0) v = a.ds_eps[d] * prm[p];
+                if (p >= 0) v = f * prm[p];
             }
         }
         srate[dd][s] = (R)v;
@@ -174,8 +175,8 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
                     xmin = mu * (R(1) + tlo);
                 }
             }
-            if (a.g_zero[g]) {
-                const R x1 = (R)a.edges[a.g_edge_off[g] + 1];
+            if (tb_g_zero<FAST>(a, g)) {
+                const R x1 = (R)a.edges[tb_g_edge_off<FAST>(a, g) + 1];
                 if (xmin <= x1) {
                     R P, Pd, Ps2;
                     gamma_bin_zero<R>(d, s, x1, P, Pd, Ps2);
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
         f[F_N] = Nk;
         f[F_XMIN] = xmin;
         f[F_XMAX] = xmax;
-        for (int dd = 0; dd < a.g_nds[g]; ++dd) {
+        for (int dd = 0; dd < tb_g_nds<FAST>(a, g); ++dd) {
             R T = 0;
             if constexpr (sizeof(R) == 4) {
                 // the lo parts first: the hi products then enter exactly into the running sum, so
@@ -234,7 +235,7 @@ template <class R, int RES, int NG>
 DEV int forward_loop(const KArgs& a, int t, int g, int split, float xlo_w, float xhi_w, bool valid,
                      bool is_zero, const R* nodes, R xc, double* accd) {
     int ncol = 0;
-    const int nds = a.g_nds[g];
+    const int nds = tb_g_nds(a, g);
     const int kchunk = (a.K + a.nsplit - 1) / a.nsplit;
     const int k_beg = split * kchunk, k_end = min(a.K, k_beg + kchunk);
     const R* blk = reinterpret_cast<const R*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
@@ -297,10 +298,10 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(KArgs a) {
     const int j = j0 + lane;
     const bool valid = j >= wlo && j < whi;
     const int jr = min(max(j, wlo), whi - 1);
-    const int nb = a.g_node_off[g] + jr;
+    const int nb = tb_g_node_off(a, g) + jr;
     const int jf = max(j0, wlo), jl = min(j0 + 31, whi - 1);
-    const float xlo_w = (float)a.edges[a.g_edge_off[g] + jf];
-    const float xhi_w = (float)a.edges[a.g_edge_off[g] + jl + 1];
+    const float xlo_w = (float)a.edges[tb_g_edge_off(a, g) + jf];
+    const float xhi_w = (float)a.edges[tb_g_edge_off(a, g) + jl + 1];
     const unsigned char cls = a.bclass[nb];
     const bool low = __any_sync(0xffffffffu, cls != BIN_LIN);
     double accd[MAXGDS] = {0.0, 0.0, 0.0};
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(KArgs a) {
     count_work(a, K_FORWARD, valid, ncol);
     if (valid) {
         double* out = a.mubuf + ((long long)t * a.nsplit + split) * a.total_bins;
-        for (int dd = 0; dd < a.g_nds[g]; ++dd) out[a.ds_off[a.g_ds[g][dd]] + j] = accd[dd];
+        for (int dd = 0; dd < tb_g_nds(a, g); ++dd) out[tb_ds_off(a, tb_g_ds(a, g, dd)) + j] = accd[dd];
     }
 }
 
@@ -332,13 +333,13 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_gauss64(KArgs a) {
     toy_window_union(a, t, g, wlo, whi);
     const int j0 = (tile * FWD_WARPS + warp) * 31;
     if (j0 >= whi || j0 + 31 <= wlo) return;
-    const int J = a.g_bins[g];
+    const int J = tb_g_bins(a, g);
     const int j = j0 + lane;
     const bool valid = lane < 31 && j >= wlo && j < whi;
-    const double xe = a.edges[a.g_edge_off[g] + min(j, J)];
+    const double xe = a.edges[tb_g_edge_off(a, g) + min(j, J)];
     const int jf = max(j0, wlo), jl = min(j0 + 30, whi - 1);
-    const double xlo_w = a.edges[a.g_edge_off[g] + jf], xhi_w = a.edges[a.g_edge_off[g] + jl + 1];
-    const int nds = a.g_nds[g];
+    const double xlo_w = a.edges[tb_g_edge_off(a, g) + jf], xhi_w = a.edges[tb_g_edge_off(a, g) + jl + 1];
+    const int nds = tb_g_nds(a, g);
     const int kchunk = (a.K + a.nsplit - 1) / a.nsplit;
     const int k_beg = split * kchunk, k_end = min(a.K, k_beg + kchunk);
     const double* blk = reinterpret_cast<const double*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_gauss64(KArgs a) {
     count_work(a, K_FORWARD, valid, ncol);
     if (valid) {
         double* out = a.mubuf + ((long long)t * a.nsplit + split) * a.total_bins;
-        for (int dd = 0; dd < nds; ++dd) out[a.ds_off[a.g_ds[g][dd]] + j] = acc[dd];
+        for (int dd = 0; dd < nds; ++dd) out[tb_ds_off(a, tb_g_ds(a, g, dd)) + j] = acc[dd];
     }
 }
 
@@ -383,33 +384,39 @@ DEV void peak_bins(const double* ed, int J, double m, double w, double cut, int&
     hi = l;
 }
 
-// AnaPeak species of each dataset (at most MAXPK per dataset), with the bins their profile reaches
+// AnaPeak species of one dataset (at most MAXPK), with the bins their profile reaches;
+// r holds eps_d f_ds times the rate
 constexpr int MAXPK = 8;
 struct PeakInfo {
-    int s[MAXD][MAXPK], lo[MAXD][MAXPK], hi[MAXD][MAXPK], n[MAXD];
-    double r[MAXD][MAXPK], m[MAXD][MAXPK], w[MAXD][MAXPK];
+    int s[MAXPK], lo[MAXPK], hi[MAXPK], n;
+    double r[MAXPK], m[MAXPK], w[MAXPK];
 };
 
-DEV void load_peaks(const KArgs& a, const double* prm, PeakInfo& pk) {
-    if (threadIdx.x < a.D) {
-        const int d = threadIdx.x;
-        const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
+// Called by the whole block with the same d; returns the number of peaks (pk untouched when the
+// dataset has none, so no barrier is needed then).
+DEV int load_peaks(const KArgs& a, const double* prm, int d, PeakInfo& pk) {
+    if (a.tb->ds_npk[d] == 0) return 0;
+    __syncthreads();  // earlier readers of pk are done
+    if (threadIdx.x == 0) {
+        const double* ed = a.edges + tb_g_edge_off(a, tb_ds_group(a, d));
         int np = 0;
         for (int s = 0; s < a.S && np < MAXPK; ++s) {
-            if (a.sp_kind[s] != 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
+            const double f = a.rfac[d * a.S + s];
+            if (a.ft.sp_kind[s] != 2 || f == 0.0) continue;
             const int pr = a.slot_map[d * a.NSLOT + s];
-            pk.s[d][np] = s;
-            pk.r[d][np] = pr >= 0 ? prm[pr] : 0.0;
-            pk.m[d][np] = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
-            pk.w[d][np] = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
+            pk.s[np] = s;
+            pk.r[np] = pr >= 0 ? f * prm[pr] : 0.0;
+            pk.m[np] = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
+            pk.w[np] = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
             int lo, hi;
-            peak_bins(ed, a.ds_bins[d], pk.m[d][np], pk.w[d][np], a.cut, lo, hi);
-            pk.lo[d][np] = lo; pk.hi[d][np] = hi;
+            peak_bins(ed, tb_ds_bins(a, d), pk.m[np], pk.w[np], a.cut, lo, hi);
+            pk.lo[np] = lo; pk.hi[np] = hi;
             ++np;
         }
-        pk.n[d] = np;
+        pk.n = np;
     }
     __syncthreads();
+    return pk.n;
 }
 
 // sum of the nsplit partial mu rows of one bin, in a fixed order (four interleaved accumulators)
@@ -435,7 +442,6 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
     const double* prm = a.params + (long long)t * a.params_stride;
     const double* cnt = a.counts + (long long)t * a.counts_stride;
     R* wout = reinterpret_cast<R*>(a.wbuf) + (long long)t * a.total_bins;
-    load_peaks(a, prm, pk);
     const int chunk = (a.total_bins + a.dev_chunks - 1) / a.dev_chunks;
     const int b0 = c * chunk, b1 = min(a.total_bins, b0 + chunk);
     const long long sstride = a.total_bins;
@@ -443,21 +449,21 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
     double part = 0.0;
     int bad_mu = 0, bad_fin = 0;
     for (int d = 0; d < a.D; ++d) {
-        const int J = a.ds_bins[d], off = a.ds_off[d];
+        const int J = tb_ds_bins(a, d), off = tb_ds_off(a, d);
         const int j0 = max(0, b0 - off), j1 = min(J, b1 - off);
         if (j0 >= j1) continue;
         int lo = a.win[t * a.win_stride + 2 * d], hi = a.win[t * a.win_stride + 2 * d + 1];
         lo = max(lo, 0); hi = min(hi, J);
-        const double eps = a.ds_eps[d];
-        const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
+        const int npk = load_peaks(a, prm, d, pk);
+        const double* ed = a.edges + tb_g_edge_off(a, tb_ds_group(a, d));
         for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             double w = 0.0;
             if (j >= lo && j < hi) {
                 double mu = sum_splits(mrow + off + j, sstride, a.nsplit);
-                for (int q = 0; q < pk.n[d]; ++q) {
-                    if (j < pk.lo[d][q] || j >= pk.hi[d][q]) continue;
-                    const double m = pk.m[d][q], wd = pk.w[d][q];
-                    mu += eps * pk.r[d][q] * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
+                for (int q = 0; q < npk; ++q) {
+                    if (j < pk.lo[q] || j >= pk.hi[q]) continue;
+                    const double m = pk.m[q], wd = pk.w[q];
+                    mu += pk.r[q] * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
                 }
                 const double n = cnt[off + j];
                 double term;
@@ -493,22 +499,23 @@ __global__ void __launch_bounds__(256) k_devfinal(KArgs a) {
     double* gdir = a.gdirect + (long long)t * a.P;
     if (a.want_grad)
         for (int p = threadIdx.x; p < a.P; p += blockDim.x) gdir[p] = 0.0;
-    load_peaks(a, prm, pk);
+    __syncthreads();  // gdir zeroed before thread 0 accumulates into it
     if (a.want_grad) {
         const float* wf = reinterpret_cast<const float*>(a.wbuf) + (long long)t * a.total_bins;
         const double* wd64 = reinterpret_cast<const double*>(a.wbuf) + (long long)t * a.total_bins;
         for (int d = 0; d < a.D; ++d) {
-            const int off = a.ds_off[d];
-            const double eps = a.ds_eps[d];
-            const double* ed = a.edges + a.g_edge_off[a.ds_group[d]];
-            for (int q = 0; q < pk.n[d]; ++q) {
-                const int s = pk.s[d][q];
+            const int npk = load_peaks(a, prm, d, pk);
+            const int off = tb_ds_off(a, d);
+            const double* ed = a.edges + tb_g_edge_off(a, tb_ds_group(a, d));
+            for (int q = 0; q < npk; ++q) {
+                const int s = pk.s[q];
+                const double f = a.rfac[d * a.S + s];
                 const int pr = a.slot_map[d * a.NSLOT + s];
                 const int pm = a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s];
                 const int pw = a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s];
-                const double r = pk.r[d][q], m = pk.m[d][q], wd = pk.w[d][q];
+                const double r = pk.r[q], m = pk.m[q], wd = pk.w[q];  // r = eps_d f_ds rate
                 double gr = 0.0, gm = 0.0, gw = 0.0;
-                for (int j = pk.lo[d][q] + threadIdx.x; j < pk.hi[d][q]; j += blockDim.x) {
+                for (int j = pk.lo[q] + threadIdx.x; j < pk.hi[q]; j += blockDim.x) {
                     const double wj = a.precision == 1 ? (double)wf[off + j] : wd64[off + j];
                     if (wj == 0.0) continue;
                     const double z0 = (ed[j] - m) / wd, z1 = (ed[j + 1] - m) / wd;
@@ -521,9 +528,9 @@ __global__ void __launch_bounds__(256) k_devfinal(KArgs a) {
                 gm = block_sum_d(gm, sh);
                 gw = block_sum_d(gw, sh);
                 if (threadIdx.x == 0) {
-                    if (pr >= 0) gdir[pr] += eps * gr;
-                    gdir[pm] += eps * r * gm;
-                    gdir[pw] += eps * r * gw;
+                    if (pr >= 0) gdir[pr] += f * gr;
+                    gdir[pm] += r * gm;
+                    gdir[pw] += r * gw;
                 }
             }
         }
@@ -561,11 +568,12 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* su = reinterpret_cast<R*>(smem_raw);                        // [MAXGDS][W*32]
     double* sresp = reinterpret_cast<double*>(smem_raw + sizeof(R) * MAXGDS * W * 32 + 16);  // [W][NRESP]
-    const int nds = a.g_nds[g];
-    const int J = a.g_bins[g];
-    const double* ed = a.edges + a.g_edge_off[g];
+    const int nds = tb_g_nds(a, g);
+    const int J = tb_g_bins(a, g);
+    const double* ed = a.edges + tb_g_edge_off(a, g);
     const double* prm = a.params + (long long)t * a.params_stride;
-    const double LY = prm[a.g_resp[g][0]], rb = prm[a.g_resp[g][3]], rc = prm[a.g_resp[g][4]];
+    const double LY = prm[tb_g_resp(a, g, 0)] * tb_g_rscale(a, g, 0);
+    const double rb = prm[tb_g_resp(a, g, 3)] * tb_g_rscale(a, g, 3), rc = prm[tb_g_resp(a, g, 4)] * tb_g_rscale(a, g, 4);
     int wlo, whi;
     toy_window_union(a, t, g, wlo, whi);
 
@@ -597,10 +605,10 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     }
     const R* wv[MAXGDS];
     for (int dd = 0; dd < MAXGDS; ++dd)
-        wv[dd] = reinterpret_cast<const R*>(a.wbuf) + (long long)t * a.total_bins + a.ds_off[a.g_ds[g][dd < nds ? dd : 0]];
+        wv[dd] = reinterpret_cast<const R*>(a.wbuf) + (long long)t * a.total_bins + tb_ds_off(a, tb_g_ds(a, g, dd < nds ? dd : 0));
     R U0[MAXGDS] = {0, 0, 0};
     R U1 = 0, U2 = 0;
-    const int nbase = a.g_node_off[g];
+    const int nbase = tb_g_node_off(a, g);
     if constexpr (sizeof(R) == 8 && RES == 0) {
         // exact Gaussian bin integrals from the edges, derivatives from the edge densities
         const double mu = c[F_MUH], isg = c[F_A];
@@ -726,7 +734,7 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
         const int dd = i / a.S, s = i % a.S;
         double v = 0.0;
-        if (dd < nds && a.sp_kind[s] != 2 && ((a.sp_mask[s] >> a.g_ds[g][dd]) & 1u)) {
+        if (dd < nds && a.ft.sp_kind[s] != 2 && a.rfac[tb_g_ds(a, g, dd) * a.S + s] != 0.0) {
             R acc = 0;
             if constexpr (sizeof(R) == 4) {
                 const float* Srow = a.Sf + (long long)s * a.K + kbase;
@@ -759,13 +767,15 @@ __global__ void __launch_bounds__(128) k_gradfinal(KArgs a) {
         for (int p = 0; p < a.P; ++p) gr[p] = gd[p];
         for (int g = 0; g < a.G; ++g) {
             const double* v = vals + g * a.NPART;
-            for (int i = 0; i < NRESP; ++i) gr[a.g_resp[g][i]] += v[i];
-            for (int dd = 0; dd < a.g_nds[g]; ++dd) {
-                const int d = a.g_ds[g][dd];
+            // the slots hold unscaled parameters: d(scale p)/dp = scale
+            for (int i = 0; i < NRESP; ++i) gr[tb_g_resp(a, g, i)] += v[i] * tb_g_rscale(a, g, i);
+            for (int dd = 0; dd < tb_g_nds(a, g); ++dd) {
+                const int d = tb_g_ds(a, g, dd);
                 for (int s = 0; s < a.S; ++s) {
-                    if (a.sp_kind[s] == 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
+                    const double f = a.rfac[d * a.S + s];
+                    if (a.ft.sp_kind[s] == 2 || f == 0.0) continue;
                     const int p = a.slot_map[d * a.NSLOT + s];
-                    if (p >= 0) gr[p] += a.ds_eps[d] * v[NRESP + dd * a.S + s];
+                    if (p >= 0) gr[p] += f * v[NRESP + dd * a.S + s];
                 }
             }
         }
@@ -821,16 +831,16 @@ template <class R, int RES>
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_species(KArgs a) {
     const int tile = blockIdx.x, g = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int J = a.g_bins[g];
+    const int J = tb_g_bins(a, g);
     const int j0 = (tile * FWD_WARPS + warp) * 32;
     if (j0 >= J) return;
     const int j = j0 + lane;
     const bool valid = j < J;
     const int jr = min(j, J - 1);
-    const int nb = a.g_node_off[g] + jr;
+    const int nb = tb_g_node_off(a, g) + jr;
     const int jl = min(j0 + 31, J - 1);
-    const float xlo_w = (float)a.edges[a.g_edge_off[g] + j0];
-    const float xhi_w = (float)a.edges[a.g_edge_off[g] + jl + 1];
+    const float xlo_w = (float)a.edges[tb_g_edge_off(a, g) + j0];
+    const float xhi_w = (float)a.edges[tb_g_edge_off(a, g) + jl + 1];
     const unsigned char cls = a.bclass[nb];
     const bool low = __any_sync(0xffffffffu, cls != BIN_LIN);
     const int nsp = min(16, a.sp_count - blockIdx.z * 16);
@@ -857,14 +867,14 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_species(KArgs a) {
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_species_gauss64(KArgs a) {
     const int tile = blockIdx.x, g = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int J = a.g_bins[g];
+    const int J = tb_g_bins(a, g);
     const int j0 = (tile * FWD_WARPS + warp) * 31;
     if (j0 >= J) return;
     const int j = j0 + lane;
     const bool valid = lane < 31 && j < J;
-    const double xe = a.edges[a.g_edge_off[g] + min(j, J)];
+    const double xe = a.edges[tb_g_edge_off(a, g) + min(j, J)];
     const int jl = min(j0 + 30, J - 1);
-    const double xlo_w = a.edges[a.g_edge_off[g] + j0], xhi_w = a.edges[a.g_edge_off[g] + jl + 1];
+    const double xlo_w = a.edges[tb_g_edge_off(a, g) + j0], xhi_w = a.edges[tb_g_edge_off(a, g) + jl + 1];
     const int sp0 = a.sp_first + blockIdx.z * 16;
     const int nsp = min(16, a.sp_count - blockIdx.z * 16);
     const double* blk = reinterpret_cast<const double*>(a.blkbuf) + (long long)g * a.nblk * 2;
@@ -893,45 +903,48 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_species_gauss64(KArgs a) {
         for (int i = 0; i < nsp; ++i) a.Mbuf[((long long)g * a.S + sp0 + i) * a.Jmax + j] = acc[i];
 }
 
-// mu_dj = eps_d sum_s mask r_s M[g][s][j] (smeared species; peaks are added by k_deviance)
+// mu_dj = sum_s eps_d f_ds r_s M[g][s][j] (smeared species; peaks are added by k_deviance)
 __global__ void k_mu_from_species(KArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.total_bins) return;
-    int d = 0;
-    while (d + 1 < a.D && i >= a.ds_off[d + 1]) ++d;
-    const int j = i - a.ds_off[d];
-    const int g = a.ds_group[d];
+    int lo = 0, hi = a.D - 1;  // last dataset whose first bin is <= i
+    while (lo < hi) { const int m = (lo + hi + 1) >> 1; if (tb_ds_off(a, m) <= i) lo = m; else hi = m - 1; }
+    const int d = lo;
+    const int j = i - tb_ds_off(a, d);
+    const int g = tb_ds_group(a, d);
     const double* prm = a.params;
     double mu = 0.0;
     for (int s = 0; s < a.S; ++s) {
-        if (a.sp_kind[s] == 2 || !((a.sp_mask[s] >> d) & 1u)) continue;
+        const double f = a.rfac[d * a.S + s];
+        if (a.ft.sp_kind[s] == 2 || f == 0.0) continue;
         const int p = a.slot_map[d * a.NSLOT + s];
         if (p < 0) continue;
-        mu = fma(prm[p], a.Mbuf[((long long)g * a.S + s) * a.Jmax + j], mu);
+        mu = fma(f * prm[p], a.Mbuf[((long long)g * a.S + s) * a.Jmax + j], mu);
     }
-    a.mubuf[i] = a.ds_eps[d] * mu;
+    a.mubuf[i] = mu;
 }
 
 // expected counts per bin and species of one dataset
 __global__ void k_expected_out(KArgs a) {
     const int d = a.out_dataset;
-    const int J = a.ds_bins[d];
+    const int J = tb_ds_bins(a, d);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= J * a.S) return;
     const int j = i / a.S, s = i % a.S;
-    const int g = a.ds_group[d];
+    const int g = tb_ds_group(a, d);
     const double* prm = a.params;
     double v = 0.0;
-    if ((a.sp_mask[s] >> d) & 1u) {
+    const double f = a.rfac[d * a.S + s];
+    if (f != 0.0) {
         const int pr = a.slot_map[d * a.NSLOT + s];
         const double r = pr >= 0 ? prm[pr] : 0.0;
-        if (a.sp_kind[s] == 2) {
-            const double* ed = a.edges + a.g_edge_off[g];
+        if (a.ft.sp_kind[s] == 2) {
+            const double* ed = a.edges + tb_g_edge_off(a, g);
             const double m = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
             const double wd = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
-            v = a.ds_eps[d] * r * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
+            v = f * r * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
         } else {
-            v = a.ds_eps[d] * r * a.Mbuf[((long long)g * a.S + s) * a.Jmax + j];
+            v = f * r * a.Mbuf[((long long)g * a.S + s) * a.Jmax + j];
         }
     }
     a.out_species[i] = v;
@@ -1037,11 +1050,16 @@ cudaError_t run_probe(int which, int nsm, double* ops) {
 cudaError_t launch_columns(const KArgs& a, cudaStream_t st) {
     dim3 grid(a.nblk, a.G, a.T);
     if (a.precision == 1) {
-        if (a.res == 0) k_columns<float, 0><<<grid, COLBLK, 0, st>>>(a);
-        else            k_columns<float, 1><<<grid, COLBLK, 0, st>>>(a);
+        if (a.fast) {
+            if (a.res == 0) k_columns<float, 0, true><<<grid, COLBLK, 0, st>>>(a);
+            else            k_columns<float, 1, true><<<grid, COLBLK, 0, st>>>(a);
+        } else {
+            if (a.res == 0) k_columns<float, 0, false><<<grid, COLBLK, 0, st>>>(a);
+            else            k_columns<float, 1, false><<<grid, COLBLK, 0, st>>>(a);
+        }
     } else {
-        if (a.res == 0) k_columns<double, 0><<<grid, COLBLK, 0, st>>>(a);
-        else            k_columns<double, 1><<<grid, COLBLK, 0, st>>>(a);
+        if (a.res == 0) k_columns<double, 0, false><<<grid, COLBLK, 0, st>>>(a);
+        else            k_columns<double, 1, false><<<grid, COLBLK, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -1107,7 +1125,7 @@ cudaError_t launch_mu_from_species(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_expected_out(const KArgs& a, cudaStream_t st) {
-    const int n = a.ds_bins[a.out_dataset] * a.S;
+    const int n = a.out_bins * a.S;
     k_expected_out<<<(n + 255) / 256, 256, 0, st>>>(a);
     return cudaGetLastError();
 }

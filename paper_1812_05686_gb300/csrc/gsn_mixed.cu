@@ -112,25 +112,25 @@ DEV float pair_value(const RecF& c, float xc, float dl, float lp, float lm, floa
 }
 
 // ------------------------------------------------------------- forward -----
-template <int RES, int NDS>
+template <int RES, int NDS, bool FAST>
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
     const int tile = blockIdx.x, split = blockIdx.y;
     const int t = blockIdx.z / a.G, g = blockIdx.z % a.G;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ RecF srec[FWD_WARPS][32];
     int wlo, whi;
-    toy_window_union(a, t, g, wlo, whi);
+    toy_window_union<FAST>(a, t, g, wlo, whi);
     // warps tile the toy's window from its first bin, so no warp starts outside it
     const int j0 = wlo + (tile * FWD_WARPS + warp) * 32;
     if (j0 >= whi) return;
     const int j = j0 + lane;
     const bool valid = j < whi;
     const int jr = min(j, whi - 1);
-    const int nb = a.g_node_off[g] + jr;
+    const int nb = tb_g_node_off<FAST>(a, g) + jr;
     const int jf = j0, jl = min(j0 + 31, whi - 1);
-    const float xlo_w = (float)a.edges[a.g_edge_off[g] + jf];
-    const float xhi_w = (float)a.edges[a.g_edge_off[g] + jl + 1];
-    const int nds = a.g_nds[g];
+    const float xlo_w = (float)a.edges[tb_g_edge_off<FAST>(a, g) + jf];
+    const float xhi_w = (float)a.edges[tb_g_edge_off<FAST>(a, g) + jl + 1];
+    const int nds = tb_g_nds<FAST>(a, g);
     const int kchunk = (a.K + a.nsplit - 1) / a.nsplit;
     const int k_beg = split * kchunk, k_end = min(a.K, k_beg + kchunk);
     const float* blk = reinterpret_cast<const float*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
 
     double accd[MAXGDS] = {0.0, 0.0, 0.0};
     int ncol = 0;
-    if (j0 < a.g_jlin[g]) {  // the warp holds bins below the first linear bin
+    if (j0 < tb_g_jlin<FAST>(a, g)) {  // the warp holds bins below the first linear bin
         // warp holds bins of the general node table (log-spaced or the bin at zero)
         const unsigned char cls = a.bclass[nb];
         const float* nodes = a.ntab_f + (long long)nb * 3 * NGM_F;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
         double* out = a.mubuf + ((long long)t * a.nsplit + split) * a.total_bins;
 #pragma unroll
         for (int dd = 0; dd < MAXGDS; ++dd)
-            if (dd < nds) out[a.ds_off[a.g_ds[g][dd]] + j] = accd[dd];
+            if (dd < nds) out[tb_ds_off<FAST>(a, tb_g_ds<FAST>(a, g, dd)) + j] = accd[dd];
     }
 }
 
@@ -259,7 +259,7 @@ DEV float warp_sum_comp(float s, float c) {
 #define GSN_BW_MINBLOCKS 4
 #endif
 
-template <int RES, int NDS>
+template <int RES, int NDS, bool FAST>
 __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
     const int task = blockIdx.x, g = blockIdx.y, t = blockIdx.z;
     const int W = a.bw_warps;
@@ -272,13 +272,14 @@ __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
     float4* sbin = reinterpret_cast<float4*>(smem_raw);                      // per warp 384 floats of bin data
     float* su = reinterpret_cast<float*>(smem_raw + sizeof(float4) * 3 * 32 * W);   // [MAXGDS][W*32]
     double* sresp = reinterpret_cast<double*>(smem_raw + sizeof(float4) * 3 * 32 * W + sizeof(float) * MAXGDS * W * 32);
-    const int nds = a.g_nds[g];
-    const int J = a.g_bins[g];
-    const double* ed = a.edges + a.g_edge_off[g];
+    const int nds = tb_g_nds<FAST>(a, g);
+    const int J = tb_g_bins<FAST>(a, g);
+    const double* ed = a.edges + tb_g_edge_off<FAST>(a, g);
     const double* prm = a.params + (long long)t * a.params_stride;
-    const double LY = prm[a.g_resp[g][0]], rb = prm[a.g_resp[g][3]], rc = prm[a.g_resp[g][4]];
+    const double LY = prm[tb_g_resp<FAST>(a, g, 0)] * tb_g_rscale<FAST>(a, g, 0);
+    const double rb = prm[tb_g_resp<FAST>(a, g, 3)] * tb_g_rscale<FAST>(a, g, 3), rc = prm[tb_g_resp<FAST>(a, g, 4)] * tb_g_rscale<FAST>(a, g, 4);
     int wlo, whi;
-    toy_window_union(a, t, g, wlo, whi);
+    toy_window_union<FAST>(a, t, g, wlo, whi);
 
     float c[NFP];
     {
@@ -309,9 +310,9 @@ __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
         }
     }
     const float* wrow = reinterpret_cast<const float*>(a.wbuf) + (long long)t * a.total_bins;
-    const float* wv0 = wrow + a.ds_off[a.g_ds[g][0]];
-    const float* wv1 = wrow + a.ds_off[a.g_ds[g][nds > 1 ? 1 : 0]];
-    const float* wv2 = wrow + a.ds_off[a.g_ds[g][nds > 2 ? 2 : 0]];
+    const float* wv0 = wrow + tb_ds_off<FAST>(a, tb_g_ds<FAST>(a, g, 0));
+    const float* wv1 = wrow + tb_ds_off<FAST>(a, tb_g_ds<FAST>(a, g, nds > 1 ? 1 : 0));
+    const float* wv2 = wrow + tb_ds_off<FAST>(a, tb_g_ds<FAST>(a, g, nds > 2 ? 2 : 0));
     const float TN0 = c[F_TN0], TN1 = NDS > 1 ? c[F_TN0 + 1] : 0.f, TN2 = NDS > 2 ? c[F_TN0 + 2] : 0.f;
     // accumulators: U0 per dataset (rates), U1/U2 (gamma: d/dmu at fixed variance, d/dvar at fixed mean,
     // scaled by mu/d and s^2; gauss: z- and (z^2-1)-weighted sums)
@@ -323,8 +324,8 @@ __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
     const float Ag = fmaf(SQ_HALF_L2E, A, A * SQ_HALF_L2E_LO);
     const float mL2EA = -mul_l2e(A);
     const bool wpoly = RES == 1 && __all_sync(0xffffffffu, !kval || c[F_B] >= D_POLY);
-    const int jlin = a.g_jlin[g];
-    const int nbase = a.g_node_off[g];
+    const int jlin = tb_g_jlin<FAST>(a, g);
+    const int nbase = tb_g_node_off<FAST>(a, g);
 
     // bins of the general node table, one at a time
     for (int j = ja; j <= min(jb, jlin - 1); ++j) {
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
     for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
         const int dd = i / a.S, s = i % a.S;
         double v = 0.0;
-        if (dd < nds && a.sp_kind[s] != 2 && ((a.sp_mask[s] >> a.g_ds[g][dd]) & 1u)) {
+        if (dd < nds && a.ft.sp_kind[s] != 2 && a.rfac[tb_g_ds<FAST>(a, g, dd) * a.S + s] != 0.0) {
             const float* Srow = a.Sf + (long long)s * a.K + kbase;
             float acc = 0.f, cmp = 0.f, part32 = 0.f;
             for (int cc = 0; cc < ncol; ++cc) {
@@ -563,40 +564,38 @@ __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
     }
 }
 
-template <int RES>
+template <int RES, bool FAST>
 static cudaError_t launch_fwd(const KArgs& a, cudaStream_t st, int nds) {
     dim3 grid(a.ntile, a.nsplit, a.T * a.G);
-    if (nds == 1) k_forward_m<RES, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
-    else if (nds == 2) k_forward_m<RES, 2><<<grid, FWD_WARPS * 32, 0, st>>>(a);
-    else k_forward_m<RES, 3><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    if (nds == 1) k_forward_m<RES, 1, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    else if (nds == 2) k_forward_m<RES, 2, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+    else k_forward_m<RES, 3, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int RES>
+template <int RES, bool FAST>
 static cudaError_t launch_bwd(const KArgs& a, cudaStream_t st, int nds) {
     dim3 grid(a.nbtask, a.G, a.T);
     const int threads = a.bw_warps * 32;
     const size_t sm = sizeof(float4) * 3 * threads + sizeof(float) * MAXGDS * threads + sizeof(double) * a.bw_warps * NRESP;
-    if (nds == 1) k_backward_m<RES, 1><<<grid, threads, sm, st>>>(a);
-    else if (nds == 2) k_backward_m<RES, 2><<<grid, threads, sm, st>>>(a);
-    else k_backward_m<RES, 3><<<grid, threads, sm, st>>>(a);
+    if (nds == 1) k_backward_m<RES, 1, FAST><<<grid, threads, sm, st>>>(a);
+    else if (nds == 2) k_backward_m<RES, 2, FAST><<<grid, threads, sm, st>>>(a);
+    else k_backward_m<RES, 3, FAST><<<grid, threads, sm, st>>>(a);
     return cudaGetLastError();
 }
 
-static int max_group_datasets(const KArgs& a) {
-    int m = 1;
-    for (int g = 0; g < a.G; ++g) m = a.g_nds[g] > m ? a.g_nds[g] : m;
-    return m;
-}
+static int max_group_datasets(const KArgs& a) { return a.max_nds > 1 ? a.max_nds : 1; }
 
 cudaError_t launch_forward_mixed(const KArgs& a, cudaStream_t st) {
     const int nds = max_group_datasets(a);
-    return a.res == 0 ? launch_fwd<0>(a, st, nds) : launch_fwd<1>(a, st, nds);
+    if (a.fast) return a.res == 0 ? launch_fwd<0, true>(a, st, nds) : launch_fwd<1, true>(a, st, nds);
+    return a.res == 0 ? launch_fwd<0, false>(a, st, nds) : launch_fwd<1, false>(a, st, nds);
 }
 
 cudaError_t launch_backward_mixed(const KArgs& a, cudaStream_t st) {
     const int nds = max_group_datasets(a);
-    return a.res == 0 ? launch_bwd<0>(a, st, nds) : launch_bwd<1>(a, st, nds);
+    if (a.fast) return a.res == 0 ? launch_bwd<0, true>(a, st, nds) : launch_bwd<1, true>(a, st, nds);
+    return a.res == 0 ? launch_bwd<0, false>(a, st, nds) : launch_bwd<1, false>(a, st, nds);
 }
 
 }  // namespace gsn

@@ -139,16 +139,16 @@ __global__ void __launch_bounds__(TC_ROWS) k_species_tc(const __grid_constant__ 
     const int tile = blockIdx.x, g = blockIdx.y;
     const int split = blockIdx.z % a.tc_nsplit, sp0 = (blockIdx.z / a.tc_nsplit) * TC_N;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int J = a.g_bins[g];
+    const int J = tb_g_bins(a, g);
     const int j0 = tile * TC_ROWS;
     if (j0 >= J) return;  // whole CTA exits before any allocation
     const int j = j0 + tid;
     const bool valid = j < J;
     const int jr = min(j, J - 1);
-    const int nb = a.g_node_off[g] + jr;
+    const int nb = tb_g_node_off(a, g) + jr;
     const int jl = min(j0 + TC_ROWS - 1, J - 1);
-    const float xlo_w = (float)a.edges[a.g_edge_off[g] + j0];
-    const float xhi_w = (float)a.edges[a.g_edge_off[g] + jl + 1];
+    const float xlo_w = (float)a.edges[tb_g_edge_off(a, g) + j0];
+    const float xhi_w = (float)a.edges[tb_g_edge_off(a, g) + jl + 1];
 
     // column range: this split's share of the band of the 128 bins, in whole chunks
     const float* blk = reinterpret_cast<const float*>(a.blkbuf) + (long long)g * a.nblk * 2;

@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH):
         "gsn_peak_probe": (C.c_int, [C.c_int, C.c_int, _DP]),
         "gsn_eval_grad_noalloc": (C.c_int, [vp, vp, vp, vp, vp]),
         "gsn_plan_info": (C.c_int, [vp, C.c_int, C.c_int, _IP]),
+        "gsn_set_dataset_factors": (C.c_int, [vp, C.c_int, C.c_int, _DP, _DP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -87,7 +88,7 @@ def exported_symbols():
             "gsn_set_data", "gsn_set_species", "gsn_set_params", "gsn_eval", "gsn_eval_grad",
             "gsn_eval_grad_batch", "gsn_eval_grad_batch_dev", "gsn_expected", "gsn_stream",
             "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe", "gsn_eval_grad_noalloc",
-            "gsn_plan_info"]
+            "gsn_plan_info", "gsn_set_dataset_factors"]
 
 
 GSN_K_COUNT = 8
@@ -232,6 +233,16 @@ class Context:
     def stream(self):
         return self.lib.gsn_stream(self.h)
 
+    def set_dataset_factors(self, resp_scale=None, rate_factor=None):
+        """Per-dataset response multipliers (D, 5) and rate fractions (D, S) of a multivariate fit."""
+        rs = pr = None
+        rf = pf = None
+        if resp_scale is not None:
+            rs, pr = _d(resp_scale)
+        if rate_factor is not None:
+            rf, pf = _d(rate_factor)
+        self._check(self.lib.gsn_set_dataset_factors(self.h, self.n_datasets, self.n_species, pr, pf))
+
     def plan_info(self, n_toys=1, grad=True):
         """Work decomposition of a launch of n_toys toys (gsn_plan_info)."""
         out = (C.c_int * 5)()
@@ -267,6 +278,8 @@ def context_from_workload(work: dict, precision=GSN_FP64, counts=None, **kw) -> 
     ctx.set_data(edges, counts, work["exposure"], work["win_lo"], work["win_hi"])
     ctx.set_species(work["fine_centres"], work["spectra"], work["kind"], work["shift"], work["mask"])
     ctx.set_params(int(work["n_params"]), work["slot_map"], work["pull_param"], work["pull_centre"], work["pull_width"])
+    if work.get("resp_scale") is not None or work.get("rate_factor") is not None:
+        ctx.set_dataset_factors(work.get("resp_scale"), work.get("rate_factor"))
     return ctx
 
 
