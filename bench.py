@@ -56,9 +56,11 @@ def parse():
     ap.add_argument("--fp64-toys", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="toys", choices=["toys", "single", "species"],
+    ap.add_argument("--mv-toys", type=int, default=1024, help="toys of the multivariate workload")
+    ap.add_argument("--workload", default="toys", choices=["toys", "single", "species", "multivariate"],
                     help="toys: the batched pseudo-experiments (default); single: sequential single-point "
-                         "NLL + gradient calls; species: gsn_eval with a response-cache miss (tensor cores)")
+                         "NLL + gradient calls; species: gsn_eval with a response-cache miss (tensor cores); "
+                         "multivariate: batched toys of the 2-D workload (4 x 64 slices)")
     return ap.parse_args()
 
 
@@ -462,12 +464,106 @@ def run_species(args):
           flush=True)
 
 
+MV_WORKLOAD = ("multivariate_like: 4 datasets x 64 slices (energy x second observable) x 1000 bins, 32 species x "
+               "50000 fine points, gamma response, per-slice LY and a multipliers and rate fractions, 37 params")
+
+
+def run_multivariate(args):
+    """Batched toys of the 2-D multivariate workload, mixed path timed, FP64 path on the first toys."""
+    import numpy as np
+    import torch
+
+    from paper_1812_05686_gb300 import gsn, inputs as I
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    w = I.multivariate_like()
+    D, P, T = len(w["edges"]), w["n_params"], args.mv_toys
+    nb = len(w["edges"][0]) - 1
+    ctx = gsn.context_from_workload(w, gsn.GSN_MIXED, stream=stream.cuda_stream)
+    # benchmark input only: the Asimov mean at theta0 from the mixed path (one response evaluation)
+    mu0 = np.concatenate([ctx.expected(w["theta0"], d).sum(axis=1) for d in range(D)])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000)
+    counts = torch.poisson(torch.from_numpy(mu0).to(dev).expand(T, -1).contiguous(), generator=gen)
+    params = torch.from_numpy(I.perturbed_points(w["theta0"], T, 1000 + T)).to(dev)
+    wins = torch.zeros(T, D, 2, dtype=torch.int32, device=dev)
+    wins[:, :, 1] = nb
+    nll = torch.empty(T, dtype=torch.float64, device=dev)
+    grad = torch.empty(T, P, dtype=torch.float64, device=dev)
+    status = torch.empty(T, dtype=torch.int32, device=dev)
+
+    def step():
+        rc = ctx.eval_grad_batch_dev(params, counts, wins, nll, grad, status)
+        if rc != 0:
+            raise RuntimeError(ctx.last_error())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ctx.profile(True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    value = T / (ms * 1e-3)
+    fp64 = None
+    nf = min(args.fp64_toys, T, 4)
+    if nf > 0:
+        ctx64 = gsn.context_from_workload(w, gsn.GSN_FP64, stream=stream.cuda_stream)
+        n64 = torch.empty(nf, dtype=torch.float64, device=dev)
+        g64 = torch.empty(nf, P, dtype=torch.float64, device=dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        rc = ctx64.eval_grad_batch_dev(params[:nf], counts[:nf], wins[:nf], n64, g64, None)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        if rc != 0:
+            raise RuntimeError(ctx64.last_error())
+        gm, gd = grad[:nf].cpu().numpy(), g64.cpu().numpy()
+        norm = np.max(np.abs(gm - gd), axis=1) / np.maximum(np.max(np.abs(gd), axis=1), 1.0)
+        fp64 = {"value": nf / (f0.elapsed_time(f1) * 1e-3), "unit": UNIT, "toys": nf,
+                "max_abs_dnll_mixed_vs_fp64": float(np.max(np.abs(n64.cpu().numpy() - nll[:nf].cpu().numpy()))),
+                "grad_normwise_err_mixed_vs_fp64": float(norm.max())}
+    dom = max(("forward", "backward"), key=lambda k: prof[k][0])
+    kms, kn, kunits = prof[dom]
+    per_launch_s = kms * 1e-3 / max(kn, 1)
+    sm_mhz = clk.get("sm_mhz") or 1455.0
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = nsm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
+    achieved = kunits / max(kn, 1) * FLOP_PER_PAIR[dom] / per_launch_s
+    line = {"metric": "NLL+grad evals/sec (batched toys, 2-D multivariate workload) on 1 GB300", "value": value,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32 (f64 deviance and reductions)", "data": "synthetic",
+            "config": {"workload": MV_WORKLOAD, "toys": T, "datasets": D, "precision": "mixed",
+                       "plan": ctx.plan_info(min(T, 83), True)},
+            "fp64_path": fp64, "status_nonzero_toys": int(torch.count_nonzero(status).item()),
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "kernel": dom, "pairs_per_launch": kunits / max(kn, 1),
+                         "ms_per_launch": per_launch_s * 1e3},
+            "clocks": clk, "gpu_launches": sum(v[1] for v in prof.values()),
+            "kernels": {k: {"ms_total": v[0], "launches": v[1], "pairs": v[2]} for k, v in prof.items() if v[1]}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "single":
         return run_single(args)
     if args.workload == "species":
         return run_species(args)
+    if args.workload == "multivariate":
+        return run_multivariate(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

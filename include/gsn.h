@@ -187,6 +187,9 @@ int gsn_set_dataset_factors(gsn_ctx* ctx, int n_datasets, int n_species, const d
                             const double* rate_factor);
 
 /* NLL at params[n_params] with the counts and windows of gsn_set_data.
+ * Keeps the per-species shapes of every response group (section 2.5 value
+ * cache, shared with gsn_expected) and recomputes them only when a response
+ * parameter (LY, kB, a, b, c) changes; rate-only steps skip the response.
  * Errors: GSN_ERR_NONPOSITIVE_MU (nll = +inf), GSN_ERR_NONFINITE. */
 int gsn_eval(gsn_ctx* ctx, const double* params, double* nll);
 
@@ -215,7 +218,8 @@ int gsn_eval_grad_batch_dev(gsn_ctx* ctx, int n_toys, const double* params_dev,
 
 /* Expected counts per bin and species of one dataset (the validation quantity
  * of section 3.1): mu_per_species[n_bins[d]][n_species]; columns of species
- * absent from the dataset are zero. */
+ * absent from the dataset are zero.  Uses the value cache of gsn_eval, so the
+ * datasets of one parameter point cost one response evaluation. */
 int gsn_expected(gsn_ctx* ctx, const double* params, int dataset, double* mu_per_species);
 
 /* Stream of the context (cudaStream_t), e.g. to order caller work after it. */

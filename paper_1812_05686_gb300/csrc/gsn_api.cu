@@ -1058,6 +1058,23 @@ static int species_status(gsn_ctx* c) {
     return GSN_OK;
 }
 
+// Per-species shapes M[g][s][j] at the response parameters of params (already on the device in
+// c->params): recomputed only when a response parameter differs bit for bit from the cached
+// point -- the value cache of section 2.5, shared by gsn_eval and gsn_expected.
+static int species_cached(gsn_ctx* c, const double* params, bool& hit) {
+    std::vector<double> key;
+    for (int g = 0; g < c->G; ++g)
+        for (int i = 0; i < NRESP; ++i) key.push_back(params[c->tab.g_resp[g][i]]);
+    hit = c->cache_valid && key.size() == c->cache_key.size() &&
+          std::memcmp(key.data(), c->cache_key.data(), key.size() * sizeof(double)) == 0;
+    if (hit) return GSN_OK;
+    int rc;
+    if ((rc = compute_species(c, (const double*)c->params.p))) return rc;
+    c->cache_key = key;
+    c->cache_valid = true;
+    return GSN_OK;
+}
+
 int gsn_eval(gsn_ctx* c, const double* params, double* nll) {
     if (!c) return GSN_ERR_ARG;
     int rc;
@@ -1068,16 +1085,8 @@ int gsn_eval(gsn_ctx* c, const double* params, double* nll) {
     if ((rc = ensure(c, c->nll_b, sizeof(double)))) return rc;
     if ((rc = ensure(c, c->status_b, sizeof(int)))) return rc;
     CUDA_TRY(c, cudaMemcpyAsync(c->params.p, params, c->P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    std::vector<double> key;
-    for (int g = 0; g < c->G; ++g)
-        for (int i = 0; i < NRESP; ++i) key.push_back(params[c->tab.g_resp[g][i]]);
-    const bool hit = c->cache_valid && key.size() == c->cache_key.size() &&
-                     std::memcmp(key.data(), c->cache_key.data(), key.size() * sizeof(double)) == 0;
-    if (!hit) {
-        if ((rc = compute_species(c, (const double*)c->params.p))) return rc;
-        c->cache_key = key;
-        c->cache_valid = true;
-    }
+    bool hit = false;
+    if ((rc = species_cached(c, params, hit))) return rc;
     KArgs a = c->base;
     Plan p = make_plan(c, 1);
     p.nsplit = 1;
@@ -1106,8 +1115,8 @@ int gsn_expected(gsn_ctx* c, const double* params, int dataset, double* mu_per_s
     if ((rc = check_params_host(c, params))) return rc;
     if ((rc = ensure(c, c->params, c->P * sizeof(double)))) return rc;
     CUDA_TRY(c, cudaMemcpyAsync(c->params.p, params, c->P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if ((rc = compute_species(c, (const double*)c->params.p))) return rc;
-    c->cache_valid = false;
+    bool hit = false;
+    if ((rc = species_cached(c, params, hit))) return rc;
     const size_t n = (size_t)c->nb[dataset] * c->S;
     if ((rc = ensure(c, c->outbuf, n * sizeof(double)))) return rc;
     KArgs a = c->base;
@@ -1120,7 +1129,7 @@ int gsn_expected(gsn_ctx* c, const double* params, int dataset, double* mu_per_s
     if ((rc = launch(c, K_SPECIES, a, launch_expected_out))) return rc;
     CUDA_TRY(c, cudaMemcpyAsync(mu_per_species, c->outbuf.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    return species_status(c);
+    return hit ? GSN_OK : species_status(c);
 }
 
 int gsn_eval_grad_batch_dev(gsn_ctx* c, int n_toys, const double* params_dev, const double* toy_counts_dev,

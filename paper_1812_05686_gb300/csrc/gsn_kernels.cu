@@ -752,33 +752,37 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
 // ------------------------------------------------------------ gradfinal ----
 __global__ void __launch_bounds__(128) k_gradfinal(KArgs a) {
     const int t = blockIdx.x;
-    extern __shared__ double vals[];  // [G][NPART]
-    for (int i = threadIdx.x; i < a.G * a.NPART; i += blockDim.x) {
-        const int g = i / a.NPART, v = i % a.NPART;
-        const double* p = a.partbuf + ((long long)t * a.G + g) * a.nbtask * a.NPART + v;
-        double s = 0.0;
-        for (int task = 0; task < a.nbtask; ++task) s += p[(long long)task * a.NPART];
-        vals[i] = s;
-    }
-    __syncthreads();
+    __shared__ double vals[NRESP + MAXGDS * MAXS];  // one group's reduced partials
+    double* gr = a.grad + (long long)t * a.P;
     if (threadIdx.x == 0) {
-        double* gr = a.grad + (long long)t * a.P;
         const double* gd = a.gdirect + (long long)t * a.P;
         for (int p = 0; p < a.P; ++p) gr[p] = gd[p];
-        for (int g = 0; g < a.G; ++g) {
-            const double* v = vals + g * a.NPART;
+    }
+    // group by group (fixed order): sum of the per-task partials, then the slot-map scatter
+    for (int g = 0; g < a.G; ++g) {
+        for (int v = threadIdx.x; v < a.NPART; v += blockDim.x) {
+            const double* p = a.partbuf + ((long long)t * a.G + g) * a.nbtask * a.NPART + v;
+            double s = 0.0;
+            for (int task = 0; task < a.nbtask; ++task) s += p[(long long)task * a.NPART];
+            vals[v] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
             // the slots hold unscaled parameters: d(scale p)/dp = scale
-            for (int i = 0; i < NRESP; ++i) gr[tb_g_resp(a, g, i)] += v[i] * tb_g_rscale(a, g, i);
+            for (int i = 0; i < NRESP; ++i) gr[tb_g_resp(a, g, i)] += vals[i] * tb_g_rscale(a, g, i);
             for (int dd = 0; dd < tb_g_nds(a, g); ++dd) {
                 const int d = tb_g_ds(a, g, dd);
                 for (int s = 0; s < a.S; ++s) {
                     const double f = a.rfac[d * a.S + s];
                     if (a.ft.sp_kind[s] == 2 || f == 0.0) continue;
                     const int p = a.slot_map[d * a.NSLOT + s];
-                    if (p >= 0) gr[p] += f * v[NRESP + dd * a.S + s];
+                    if (p >= 0) gr[p] += f * vals[NRESP + dd * a.S + s];
                 }
             }
         }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
         bool fin = true;
         for (int p = 0; p < a.P; ++p) fin = fin && isfinite(gr[p]);
         if (!fin && a.status && a.status[t] == 0) a.status[t] = -4;
@@ -1098,7 +1102,7 @@ cudaError_t launch_backward(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_gradfinal(const KArgs& a, cudaStream_t st) {
-    k_gradfinal<<<a.T, 128, sizeof(double) * a.G * a.NPART, st>>>(a);
+    k_gradfinal<<<a.T, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
