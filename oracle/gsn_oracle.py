@@ -35,6 +35,10 @@ Readings (the paper gives no formula for them):
 * spectra are point-sampled at the fine centres and normalised to unit sum;
   AnaShift moves the normalised spectrum up by round(shift / dE) fine bins;
 * AnaPeak: a Gaussian of position m and width w directly in p.e.;
+* Monte Carlo template species (the template fit of section 3.2): a histogram
+  in the dataset's own visible bins ("templates" key: [species][dataset] array
+  or None), normalised to unit sum; it enters as eps_d f_ds r_s T_dsj with no
+  response;
 * NLL = sum_d sum_{j in window} [mu - n + n ln(n/mu)] + 1/2 sum_pulls ((p-c)/sigma)^2,
   i.e. -ln L of Eq. (LL) up to a data-only constant, with the pull term read
   as the usual Gaussian constraint (Eq. (LL) prints its sign/factor garbled).
@@ -53,7 +57,7 @@ import math
 import numpy as np
 from scipy import special
 
-KIND_ANA, KIND_ANA_SHIFT, KIND_ANA_PEAK = 0, 1, 2
+KIND_ANA, KIND_ANA_SHIFT, KIND_ANA_PEAK, KIND_MC_TEMPLATE = 0, 1, 2, 3
 RES_GAUSS, RES_GAMMA = 0, 1
 _RESP = ("LY", "kB", "a", "b", "c")
 
@@ -88,7 +92,7 @@ def quenched_energy_dkB(E, kB, s0, s1):
 def species_spectra(work):
     """Normalised (and, for AnaShift, shifted) fine spectra S'[s, k] (section 4.3, reading).
 
-    Rows of AnaPeak species are zero (they do not pass through the response).
+    Rows of AnaPeak and template species are zero (they do not pass through the response).
     """
     E = np.asarray(work["fine_centres"], np.float64)
     f = np.asarray(work["spectra"], np.float64)
@@ -96,7 +100,7 @@ def species_spectra(work):
     dE = (E[-1] - E[0]) / (E.size - 1) if E.size > 1 else 1.0
     for s in range(f.shape[0]):
         kind = int(work["kind"][s])
-        if kind == KIND_ANA_PEAK:
+        if kind in (KIND_ANA_PEAK, KIND_MC_TEMPLATE):
             continue
         tot = f[s].sum()
         row = f[s] / tot if tot > 0 else np.zeros_like(f[s])
@@ -168,6 +172,18 @@ def peak_profile(edges, m, w):
     return _norm_cdf_diff(z[:-1], z[1:])
 
 
+def template(work, s, d):
+    """Normalised visible-bin template of species s in dataset d (zeros if it has none there)."""
+    J = len(work["edges"][d]) - 1
+    tpl = work.get("templates")
+    h = None if tpl is None else tpl[s][d]
+    if h is None:
+        return np.zeros(J)
+    h = np.asarray(h, np.float64)
+    tot = h.sum()
+    return h / tot if tot > 0 else np.zeros(J)
+
+
 # ------------------------------------------------------- parameter map ------
 def dataset_values(work, params, d):
     """Per-dataset slot values from the global parameters (section 2.2 synchronisation)."""
@@ -219,8 +235,9 @@ def response_matrix(work, edges, resp):
 def expected_per_species(work, params, d):
     """Expected counts per bin and species of dataset d, shape (J, S) (section 3.1 validation quantity).
 
-    Column s holds eps_d f_ds r_s sum_k R[j,k] S'[s,k] for Ana/AnaShift species and
-    eps_d f_ds r_s * peak_j(m_s, w_s) for AnaPeak species; zero where mask[s, d] = 0.
+    Column s holds eps_d f_ds r_s sum_k R[j,k] S'[s,k] for Ana/AnaShift species,
+    eps_d f_ds r_s * peak_j(m_s, w_s) for AnaPeak species and eps_d f_ds r_s T_dsj for
+    template species; zero where mask[s, d] = 0.
     R is built from the response slots times the dataset's response multipliers.
     """
     vals = dataset_values(work, params, d)
@@ -230,7 +247,9 @@ def expected_per_species(work, params, d):
     edges = np.asarray(work["edges"][d], np.float64)
     eps = float(work["exposure"][d])
     Sp = species_spectra(work)
-    R = response_matrix(work, edges, resp)
+    kinds = np.asarray(work["kind"])
+    mask = np.asarray(work["mask"])[:, d].astype(bool)
+    R = response_matrix(work, edges, resp) if np.any(mask & (kinds < KIND_ANA_PEAK)) else None
     J, S = edges.size - 1, Sp.shape[0]
     out = np.zeros((J, S))
     for s in range(S):
@@ -238,6 +257,8 @@ def expected_per_species(work, params, d):
             continue
         if int(work["kind"][s]) == KIND_ANA_PEAK:
             out[:, s] = eps * frac[s] * rates[s] * peak_profile(edges, peaks[s, 0], peaks[s, 1])
+        elif int(work["kind"][s]) == KIND_MC_TEMPLATE:
+            out[:, s] = eps * frac[s] * rates[s] * template(work, s, d)
         else:
             out[:, s] = eps * frac[s] * rates[s] * (R @ Sp[s])
     return out
@@ -327,46 +348,50 @@ def nll_grad(work, params, counts, windows=None):
         w = np.zeros(edges.size - 1)
         w[lo:hi] = 1.0 - n[lo:hi] / mu[lo:hi]
         gs = np.zeros(vals.size)  # gradient wrt the dataset's slots
-        # smeared species
-        Eq, mu_k, var_k = column_mean_var(work, resp)
-        smeared = mask & (np.asarray(work["kind"]) != KIND_ANA_PEAK)
-        T = eps * ((frac * rates)[smeared][:, None] * Sp[smeared]).sum(axis=0) if smeared.any() else np.zeros(E.size)
-        R = response_matrix(work, edges, resp)
-        u = w @ R  # u_k = sum_j w_j R_jk
-        for s in np.nonzero(smeared)[0]:
-            gs[s] += eps * frac[s] * float(Sp[s] @ u)
-        # response parameters through (mu_k, var_k)
-        x = edges[:, None]
-        if int(work["resolution"]) == RES_GAUSS:
-            sig = np.sqrt(var_k)
-            z = (x - mu_k[None, :]) / sig[None, :]
-            phi = np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
-            dR_dmu = -(phi[1:] - phi[:-1]) / sig[None, :]
-            dR_dsig = -(z[1:] * phi[1:] - z[:-1] * phi[:-1]) / sig[None, :]
-            g_mu = (w @ dR_dmu) * T
-            g_sig = (w @ dR_dsig) * T
-            g_var = g_sig / (2.0 * sig)
-        else:
-            dsh, sc = gamma_shape_scale(mu_k, var_k)
-            y = np.clip(edges, 0.0, None)[:, None] / sc[None, :]
-            dd = np.broadcast_to(dsh[None, :], y.shape)
-            Pd = _gamma_P_dshape(dd, y)
-            py = _gamma_pdf_times_y(dd, y)
-            dR_dd = Pd[1:] - Pd[:-1]
-            dR_ds = -(py[1:] - py[:-1]) / sc[None, :]
-            g_d = (w @ dR_dd) * T
-            g_s = (w @ dR_ds) * T
-            g_mu = g_d * (2.0 * mu_k / var_k) + g_s * (-var_k / mu_k**2)
-            g_var = g_d * (-(mu_k**2) / var_k**2) + g_s / mu_k
-        g_mu_tot = g_mu + g_var * (resp["b"] + 2.0 * resp["c"] * mu_k)
+        # smeared species and the response parameters (datasets of template / peak species only skip this)
+        smeared = mask & (np.asarray(work["kind"]) < KIND_ANA_PEAK)
         base = S
-        gs[base + 0] += float(g_mu_tot @ Eq)
-        gs[base + 1] += float(g_mu_tot @ (resp["LY"] * quenched_energy_dkB(E, resp["kB"], work["birks_s0"], work["birks_s1"])))
-        gs[base + 2] += float(g_var.sum())
-        gs[base + 3] += float(g_var @ mu_k)
-        gs[base + 4] += float(g_var @ (mu_k * mu_k))
-        # the slots hold the unscaled parameters: d(scale_i p_i)/dp_i = scale_i
-        gs[base:base + 5] *= scale
+        if smeared.any():
+            Eq, mu_k, var_k = column_mean_var(work, resp)
+            T = eps * ((frac * rates)[smeared][:, None] * Sp[smeared]).sum(axis=0)
+            R = response_matrix(work, edges, resp)
+            u = w @ R  # u_k = sum_j w_j R_jk
+            for s in np.nonzero(smeared)[0]:
+                gs[s] += eps * frac[s] * float(Sp[s] @ u)
+            # response parameters through (mu_k, var_k)
+            x = edges[:, None]
+            if int(work["resolution"]) == RES_GAUSS:
+                sig = np.sqrt(var_k)
+                z = (x - mu_k[None, :]) / sig[None, :]
+                phi = np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+                dR_dmu = -(phi[1:] - phi[:-1]) / sig[None, :]
+                dR_dsig = -(z[1:] * phi[1:] - z[:-1] * phi[:-1]) / sig[None, :]
+                g_mu = (w @ dR_dmu) * T
+                g_sig = (w @ dR_dsig) * T
+                g_var = g_sig / (2.0 * sig)
+            else:
+                dsh, sc = gamma_shape_scale(mu_k, var_k)
+                y = np.clip(edges, 0.0, None)[:, None] / sc[None, :]
+                dd = np.broadcast_to(dsh[None, :], y.shape)
+                Pd = _gamma_P_dshape(dd, y)
+                py = _gamma_pdf_times_y(dd, y)
+                dR_dd = Pd[1:] - Pd[:-1]
+                dR_ds = -(py[1:] - py[:-1]) / sc[None, :]
+                g_d = (w @ dR_dd) * T
+                g_s = (w @ dR_ds) * T
+                g_mu = g_d * (2.0 * mu_k / var_k) + g_s * (-var_k / mu_k**2)
+                g_var = g_d * (-(mu_k**2) / var_k**2) + g_s / mu_k
+            g_mu_tot = g_mu + g_var * (resp["b"] + 2.0 * resp["c"] * mu_k)
+            gs[base + 0] += float(g_mu_tot @ Eq)
+            gs[base + 1] += float(g_mu_tot @ (resp["LY"] * quenched_energy_dkB(E, resp["kB"], work["birks_s0"], work["birks_s1"])))
+            gs[base + 2] += float(g_var.sum())
+            gs[base + 3] += float(g_var @ mu_k)
+            gs[base + 4] += float(g_var @ (mu_k * mu_k))
+            # the slots hold the unscaled parameters: d(scale_i p_i)/dp_i = scale_i
+            gs[base:base + 5] *= scale
+        # template species: mu is linear in the rate
+        for s in np.nonzero(mask & (np.asarray(work["kind"]) == KIND_MC_TEMPLATE))[0]:
+            gs[s] += eps * frac[s] * float(w @ template(work, s, d))
         # peak species
         for s in np.nonzero(mask & (np.asarray(work["kind"]) == KIND_ANA_PEAK))[0]:
             m, wd = peaks[s]

@@ -16,7 +16,8 @@ Workload dictionary keys
 ------------------------
 fine_centres (K,)        ascending fine true-energy centres [MeV]
 spectra      (S, K)      unnormalised species shapes at the centres
-kind         (S,)        0 = Ana, 1 = AnaShift, 2 = AnaPeak (section 4.3)
+kind         (S,)        0 = Ana, 1 = AnaShift, 2 = AnaPeak (section 4.3), 3 = Monte Carlo
+                         template (section 3.2: a visible-bin histogram per dataset)
 shift        (S,)        true-energy shift of AnaShift species [MeV]
 mask         (S, D)      1 where species s contributes to dataset d
 edges        [D] arrays  visible-energy bin edges [p.e.], ascending
@@ -36,12 +37,13 @@ resp_scale   (D, 5)      optional fixed multipliers of the response slots (LY, k
                          of each dataset (section 2.4 slices; default 1)
 rate_factor  (D, S)      optional fixed fraction of each species' rate in each dataset
                          (section 2.4 slices; default 1)
+templates    [S][D]      optional visible-bin histograms of template species (None elsewhere)
 """
 from __future__ import annotations
 
 import numpy as np
 
-KIND_ANA, KIND_ANA_SHIFT, KIND_ANA_PEAK = 0, 1, 2
+KIND_ANA, KIND_ANA_SHIFT, KIND_ANA_PEAK, KIND_MC_TEMPLATE = 0, 1, 2, 3
 RES_GAUSS, RES_GAMMA = 0, 1
 
 # Stopping-power model constants used by every workload (MeV/cm and MeV^2/cm):
@@ -266,6 +268,97 @@ def multivariate_like(seed: int = 5, n_datasets: int = 4, n_slices: int = 64, n_
         theta0=theta0, param_names=[f"r_{n}" for n in names] + ["LY", "kB", "a", "b", "c"],
         resp_scale=resp_scale, rate_factor=rate_factor, n_slices=n_slices,
     )
+
+
+def _visible_shapes(rng, x, n):
+    """n smooth positive shapes over visible-bin centres x [p.e.]: exponentials, bumps, betas, flat."""
+    out = []
+    for i in range(n):
+        kind = i % 4
+        if kind == 0:
+            h = np.exp(-x / rng.uniform(50.0, 300.0))
+        elif kind == 1:
+            h = np.exp(-0.5 * ((x - rng.uniform(100.0, 0.9 * x[-1])) / rng.uniform(20.0, 60.0)) ** 2)
+        elif kind == 2:
+            q = rng.uniform(0.3, 1.0) * x[-1]
+            h = np.where(x < q, x * x * (q - x) ** 2, 0.0)
+        else:
+            h = np.ones_like(x)
+        out.append(h / h.max())
+    return out
+
+
+def _template_set(rng, edges_per_dataset, base_shapes):
+    """Per-dataset Monte Carlo-like templates of each base shape: a 2% tilt between datasets and 1%
+    seeded multiplicative noise (finite simulation statistics)."""
+    tpl = []
+    for h0 in base_shapes:
+        row = []
+        for d, e in enumerate(edges_per_dataset):
+            x = 0.5 * (np.asarray(e[:-1]) + np.asarray(e[1:]))
+            h = h0 * (1.0 + 0.02 * d * (x / x[-1] - 0.5)) * (1.0 + 0.01 * rng.standard_normal(x.size))
+            row.append(np.clip(h, 0.0, None))
+        tpl.append(row)
+    return tpl
+
+
+def template_like(seed: int = 8, n_bins: int = 1000, n_species: int = 16) -> dict:
+    """Monte Carlo template fit (section 3.2): every species is a visible-energy histogram.
+
+    Two datasets (exposures 1.0 and 0.6) of n_bins bins of 1 p.e.; n_species seeded template
+    shapes (exponentials, bumps, betas, flat) with per-dataset variations; rates log-uniform in
+    [1e3, 1e5].  No response parameters: the slot map leaves LY, kB, a, b, c unused.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    D, S = 2, n_species
+    edges = [unit_edges(n_bins) for _ in range(D)]
+    x = unit_edges(n_bins)
+    shapes = _visible_shapes(rng, 0.5 * (x[:-1] + x[1:]), S)
+    sm = -np.ones((D, n_slots(S)), dtype=np.int32)
+    for d in range(D):
+        sm[d, :S] = np.arange(S)
+    rates = 10.0 ** rng.uniform(3.0, 5.0, size=S)
+    return dict(
+        name=f"template_like_2x{n_bins}x{S}", fine_centres=np.array([0.5e-3]), spectra=np.zeros((S, 1)),
+        kind=np.full(S, KIND_MC_TEMPLATE, np.int32), shift=np.zeros(S), mask=np.ones((S, D), np.uint8),
+        edges=edges, exposure=np.array([1.0, 0.6]), win_lo=np.zeros(D, np.int32),
+        win_hi=np.full(D, n_bins, np.int32), resolution=RES_GAMMA, birks_s0=BIRKS_S0, birks_s1=BIRKS_S1,
+        n_params=S, slot_map=sm, pull_param=np.zeros(0, np.int32), pull_centre=np.zeros(0),
+        pull_width=np.zeros(0), theta0=rates, param_names=[f"r_tpl{i}" for i in range(S)],
+        templates=_template_set(rng, edges, shapes),
+    )
+
+
+def with_templates(work: dict, n_templates: int, seed: int = 9) -> dict:
+    """A workload plus n_templates Monte Carlo template species (new rate parameters appended)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    S0, D, P0 = work["spectra"].shape[0], len(work["edges"]), int(work["n_params"])
+    S = S0 + n_templates
+    x = np.asarray(work["edges"][0])
+    shapes = _visible_shapes(rng, 0.5 * (x[:-1] + x[1:]), n_templates)
+    sm = -np.ones((D, n_slots(S)), dtype=np.int32)
+    old = np.asarray(work["slot_map"])
+    for d in range(D):
+        sm[d, :S0] = old[d, :S0]
+        sm[d, S:S + 5] = old[d, S0:S0 + 5]
+        sm[d, S + 5:S + 5 + 2 * S0] = old[d, S0 + 5:]
+        sm[d, S0:S] = P0 + np.arange(n_templates)
+    tpl = [None] * S0 + _template_set(rng, work["edges"], shapes)
+    tpl = [t if t is not None else [None] * D for t in tpl]
+    out = dict(work)
+    out.update(
+        name=work["name"] + f"+{n_templates}tpl",
+        spectra=np.vstack([work["spectra"], np.zeros((n_templates, work["spectra"].shape[1]))]),
+        kind=np.concatenate([work["kind"], np.full(n_templates, KIND_MC_TEMPLATE, np.int32)]),
+        shift=np.concatenate([work["shift"], np.zeros(n_templates)]),
+        mask=np.vstack([work["mask"], np.ones((n_templates, D), np.uint8)]),
+        n_params=P0 + n_templates, slot_map=sm, templates=tpl,
+        theta0=np.concatenate([work["theta0"], 10.0 ** rng.uniform(2.0, 4.0, size=n_templates)]),
+        param_names=list(work["param_names"]) + [f"r_tpl{i}" for i in range(n_templates)],
+    )
+    if work.get("rate_factor") is not None:
+        out["rate_factor"] = np.hstack([work["rate_factor"], np.ones((D, n_templates))])
+    return out
 
 
 def perturbed_points(theta0: np.ndarray, n: int, seed0: int, rel: float = 0.01) -> np.ndarray:
