@@ -57,10 +57,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mv-toys", type=int, default=1024, help="toys of the multivariate workload")
-    ap.add_argument("--workload", default="toys", choices=["toys", "single", "species", "multivariate"],
+    ap.add_argument("--workload", default="toys", choices=["toys", "single", "species", "multivariate", "templates"],
                     help="toys: the batched pseudo-experiments (default); single: sequential single-point "
                          "NLL + gradient calls; species: gsn_eval with a response-cache miss (tensor cores); "
-                         "multivariate: batched toys of the 2-D workload (4 x 64 slices)")
+                         "multivariate: batched toys of the 2-D workload (4 x 64 slices); templates: batched "
+                         "toys of a Monte Carlo template fit (no response)")
     return ap.parse_args()
 
 
@@ -556,6 +557,80 @@ def run_multivariate(args):
     print(json.dumps(line), flush=True)
 
 
+TPL_WORKLOAD = ("template_like: Monte Carlo template fit, 2 datasets x 1000 bins, 16 template species "
+                "(visible-bin histograms), 16 rate params, ragged windows 600-1000 bins")
+
+
+def run_templates(args):
+    """Batched toys of a pure template fit: only the FP64 deviance stage runs (no response)."""
+    import numpy as np
+    import torch
+
+    from paper_1812_05686_gb300 import gsn, inputs as I
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    w = I.template_like()
+    D, P, T = len(w["edges"]), w["n_params"], args.toys
+    nb = len(w["edges"][0]) - 1
+    ctx = gsn.context_from_workload(w, gsn.GSN_MIXED, stream=stream.cuda_stream)
+    # benchmark input: the expected counts at theta0 from the library (templates times rates)
+    mu0 = np.concatenate([ctx.expected(w["theta0"], d).sum(axis=1) for d in range(D)])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2000)
+    counts = torch.poisson(torch.from_numpy(mu0).to(dev).expand(T, -1).contiguous(), generator=gen)
+    params = torch.from_numpy(I.perturbed_points(w["theta0"], T, 2000 + T)).to(dev)
+    win = I.toy_windows(T, nb, 600, 1000, 2000 + 2 * T)
+    wins = torch.from_numpy(np.repeat(win[:, None, :], D, axis=1).astype(np.int32)).to(dev)
+    nll = torch.empty(T, dtype=torch.float64, device=dev)
+    grad = torch.empty(T, P, dtype=torch.float64, device=dev)
+    status = torch.empty(T, dtype=torch.int32, device=dev)
+
+    def step():
+        rc = ctx.eval_grad_batch_dev(params, counts, wins, nll, grad, status)
+        if rc != 0:
+            raise RuntimeError(ctx.last_error())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ctx.profile(True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    # roofline of the deviance stage: FP64, 2 FMA per template and bin (mu and the rate gradient)
+    S = w["spectra"].shape[0]
+    kms, kn, _ = prof["deviance"]
+    per_launch_s = kms * 1e-3 / max(kn, 1)
+    bins_per_launch = min(T, 4096) * D * nb
+    flops = bins_per_launch * 4.0 * S
+    dfma = gsn.peak_probe(gsn.GSN_PROBE_DFMA)
+    hbm = bins_per_launch * (8 + 4)  # counts read, w written (FP32)
+    line = {"metric": "NLL+grad evals/sec (batched toys, Monte Carlo template fit) on 1 GB300", "value": T / (ms * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f64 (template contraction and deviance)", "data": "synthetic",
+            "config": {"workload": TPL_WORKLOAD, "toys": T},
+            "status_nonzero_toys": int(torch.count_nonzero(status).item()),
+            "roofline": {"bound": "alu (fp64)", "achieved": flops / per_launch_s / 1e12, "peak": 2 * dfma / 1e12,
+                         "unit": "TFLOP/s", "frac": flops / per_launch_s / (2 * dfma), "kernel": "deviance",
+                         "peak_basis": "measured DFMA rate (gsn_peak_probe) x 2",
+                         "hbm_gbs": hbm / per_launch_s / 1e9, "ms_per_launch": per_launch_s * 1e3},
+            "clocks": clk, "gpu_launches": sum(v[1] for v in prof.values()),
+            "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "single":
@@ -564,6 +639,8 @@ def main():
         return run_species(args)
     if args.workload == "multivariate":
         return run_multivariate(args)
+    if args.workload == "templates":
+        return run_templates(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

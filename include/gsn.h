@@ -9,7 +9,8 @@
  *                + 1/2 sum_p ((theta_p - c_p) / sigma_p)^2
  *
  *   mu_dj = eps_d [ sum_{s smeared} f_ds r_s sum_k R_jk(theta) S'_sk
- *                   + sum_{s peak} f_ds r_s int_{bin j} N(x; m_s, w_s) dx ]
+ *                   + sum_{s peak} f_ds r_s int_{bin j} N(x; m_s, w_s) dx
+ *                   + sum_{s template} f_ds r_s T_dsj ]
  *
  * with R_jk the bin integral of the analytic detector response of fine
  * true-energy column k (section 2.3): visible mean mu_k = LY * E_q(E_k; kB)
@@ -65,6 +66,8 @@ extern "C" {
 #define GSN_ANA                   0  /* fine spectrum smeared by the response */
 #define GSN_ANA_SHIFT             1  /* fine spectrum shifted up in true energy, then smeared */
 #define GSN_ANA_PEAK              2  /* Gaussian peak in p.e. with free position m and width w */
+#define GSN_MC_TEMPLATE           3  /* Monte Carlo template: a histogram in each dataset's visible
+                                        bins (section 3.2 template fit, gsn_set_template) */
 
 /* per-dataset parameter slots: gsn_n_slots(S) = 3 S + 5
  *   [0, S)              rate r_s of species s (counts per unit exposure)
@@ -185,6 +188,18 @@ int gsn_set_params(gsn_ctx* ctx, int n_params, const int* slot_map, int n_pulls,
  * Errors: GSN_ERR_ARG (sizes, values), GSN_ERR_STATE (data or species missing). */
 int gsn_set_dataset_factors(gsn_ctx* ctx, int n_datasets, int n_species, const double* resp_scale,
                             const double* rate_factor);
+
+/* Monte Carlo template of species s in dataset d (section 3.2: the template
+ * fit, where a species' expected visible spectrum comes from simulation rather
+ * than from the analytic response).  hist holds n_bins[d] values >= 0 with a
+ * positive sum; the library normalises it to unit sum, so r_s counts per unit
+ * exposure as for the other kinds.  Species s must be of kind GSN_MC_TEMPLATE;
+ * a template species without a histogram in a dataset contributes nothing
+ * there; hist = NULL removes it.  Datasets whose species are all templates or
+ * peaks need no response slots (slot_map -1), and a fit of templates only runs
+ * no response kernel.  Call after gsn_set_species (which clears the templates).
+ * Errors: GSN_ERR_ARG, GSN_ERR_STATE. */
+int gsn_set_template(gsn_ctx* ctx, int species, int dataset, const double* hist);
 
 /* NLL at params[n_params] with the counts and windows of gsn_set_data.
  * Keeps the per-species shapes of every response group (section 2.5 value

@@ -43,6 +43,7 @@ struct gsn_ctx {
     std::vector<int> slot_map;
     std::vector<double> rscale;       // [D][5] response multipliers of each dataset (section 2.4 slices)
     std::vector<double> rfrac;        // [D][S] rate fraction of each species in each dataset
+    std::map<std::pair<int, int>, std::vector<double>> tpl;  // (dataset, species) -> normalised template
     std::vector<int> pull_p;
     std::vector<double> pull_c, pull_w;
     bool have_data = false, have_species = false, have_params = false, ready = false;
@@ -217,7 +218,24 @@ int finalize(gsn_ctx* c) {
             if (!c->mask[s * c->D + d]) continue;
             rfac[(size_t)d * c->S + s] = c->eps[d] * c->rfrac[(size_t)d * c->S + s];
             if (c->kind[s] == GSN_ANA_PEAK && rfac[(size_t)d * c->S + s] != 0.0) ++tb.ds_npk[d];
+            if (c->kind[s] < GSN_ANA_PEAK && rfac[(size_t)d * c->S + s] != 0.0) tb.ds_resp[d] = 1;
         }
+    // Monte Carlo templates, datasets in order: species, offset, normalised histogram
+    std::vector<int> tpl_s;
+    std::vector<long long> tpl_off;
+    std::vector<double> tpl_h;
+    for (int d = 0; d < c->D; ++d) {
+        tb.ds_tpl0[d] = (int)tpl_s.size();
+        for (int s = 0; s < c->S; ++s) {
+            const auto it = c->tpl.find(std::make_pair(d, s));
+            if (it == c->tpl.end() || rfac[(size_t)d * c->S + s] == 0.0) continue;
+            tpl_s.push_back(s);
+            tpl_off.push_back((long long)tpl_h.size());
+            tpl_h.insert(tpl_h.end(), it->second.begin(), it->second.end());
+        }
+        tb.ds_ntpl[d] = (int)tpl_s.size() - tb.ds_tpl0[d];
+    }
+    a.ntpl = (int)tpl_s.size();
     // response groups: identical edges, response slots and response multipliers (at most MAXGDS each)
     c->G = 0;
     int off = 0;
@@ -253,6 +271,11 @@ int finalize(gsn_ctx* c) {
     c->total_bins = off;
     a.total_bins = off;
     a.G = c->G;
+    a.response = 0;
+    for (int g = 0; g < c->G; ++g) {
+        for (int i = 0; i < tb.g_nds[g]; ++i) tb.g_active[g] |= tb.ds_resp[tb.g_ds[g][i]];
+        a.response |= tb.g_active[g];
+    }
     // edges and node tables per group
     std::vector<double> edges_all, ntab_d;
     std::vector<float> ntab_f, xc_f, btab_f;
@@ -352,12 +375,13 @@ int finalize(gsn_ctx* c) {
         a.ft.g_nds[g] = tb.g_nds[g];
         for (int i = 0; i < MAXGDS; ++i) a.ft.g_ds[g][i] = tb.g_ds[g][i];
         a.ft.g_bins[g] = tb.g_bins[g]; a.ft.g_edge_off[g] = tb.g_edge_off[g]; a.ft.g_node_off[g] = tb.g_node_off[g];
-        a.ft.g_jlin[g] = tb.g_jlin[g]; a.ft.g_zero[g] = tb.g_zero[g];
+        a.ft.g_jlin[g] = tb.g_jlin[g]; a.ft.g_zero[g] = tb.g_zero[g]; a.ft.g_active[g] = tb.g_active[g];
         for (int i = 0; i < NRESP; ++i) { a.ft.g_resp[g][i] = tb.g_resp[g][i]; a.ft.g_rscale[g][i] = tb.g_rscale[g][i]; }
     }
     for (int s = 0; s < c->S; ++s) a.ft.sp_kind[s] = tb.sp_kind[s];
     for (int d = 0; d < std::min(c->D, FASTD); ++d) {
         a.ft.ds_off[d] = tb.ds_off[d]; a.ft.ds_bins[d] = tb.ds_bins[d]; a.ft.ds_group[d] = tb.ds_group[d];
+        a.ft.ds_resp[d] = tb.ds_resp[d];
     }
     int rc;
     {
@@ -365,6 +389,9 @@ int finalize(gsn_ctx* c) {
         if ((rc = upload(c, tv, &a.tb))) return rc;
     }
     if ((rc = upload(c, rfac, &a.rfac))) return rc;
+    if ((rc = upload(c, tpl_s, &a.tpl_s))) return rc;
+    if ((rc = upload(c, tpl_off, &a.tpl_off))) return rc;
+    if ((rc = upload(c, tpl_h, &a.tpl))) return rc;
     if ((rc = upload(c, edges_all, &a.edges))) return rc;
     if ((rc = upload(c, bcls, &a.bclass))) return rc;
     if (mixed) {
@@ -416,7 +443,7 @@ int reserve(gsn_ctx* c, int T, const Plan& p) {
     if ((rc = ensure(c, c->wbuf, (size_t)T * c->total_bins * rs))) return rc;
     if ((rc = ensure(c, c->partbuf, (size_t)T * c->G * p.nbtask * npart * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->gdirect, (size_t)T * c->P * sizeof(double)))) return rc;
-    if ((rc = ensure(c, c->devbuf, (size_t)T * p.dev_chunks * 2 * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->devbuf, (size_t)T * p.dev_chunks * (2 + c->base.ntpl) * sizeof(double)))) return rc;
     return GSN_OK;
 }
 
@@ -485,12 +512,14 @@ int launch(gsn_ctx* c, int kernel, KArgs& a, F fn) {
 
 int run_step(gsn_ctx* c, KArgs& a, bool grad) {
     int rc;
-    if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
-    if ((rc = launch(c, K_FORWARD, a, launch_forward))) return rc;
+    if (a.response) {  // a fit of templates and peaks only has no response to build
+        if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
+        if ((rc = launch(c, K_FORWARD, a, launch_forward))) return rc;
+    }
     if ((rc = launch(c, K_DEVIANCE, a, launch_deviance))) return rc;
     if ((rc = launch(c, K_DEVFINAL, a, launch_devfinal))) return rc;
     if (grad) {
-        if ((rc = launch(c, K_BACKWARD, a, launch_backward))) return rc;
+        if (a.response && (rc = launch(c, K_BACKWARD, a, launch_backward))) return rc;
         if ((rc = launch(c, K_GRADFINAL, a, launch_gradfinal))) return rc;
     }
     return GSN_OK;
@@ -537,7 +566,7 @@ int choose_plan(gsn_ctx* c, int T, KArgs a, bool grad, Plan& out) {
     const Plan h = heuristic_plan(c, T);
     out = h;
     if (stream_capturing(c)) return GSN_OK;  // no timing inside a caller's capture
-    if (!c->opt.autotune || (h.nsplit == 1 && h.bw_bsplit == 1)) { c->tuned[key] = h; return GSN_OK; }
+    if (!c->opt.autotune || !c->base.response || (h.nsplit == 1 && h.bw_bsplit == 1)) { c->tuned[key] = h; return GSN_OK; }
     const cudaStream_t st = c->stream;
     int rc;
     if ((rc = prepare(c, T, h, a))) return rc;
@@ -844,6 +873,7 @@ int gsn_set_data(gsn_ctx* c, int n_datasets, const int* n_bins, const double* co
     }
     if (c->have_species && n_datasets != c->D) c->have_species = c->have_params = false;
     if (n_datasets != c->D) { c->rscale.clear(); c->rfrac.clear(); }
+    if (n_datasets != c->D || nb != c->nb) c->tpl.clear();
     c->D = n_datasets; c->nb = nb; c->edges = ed; c->counts = cn; c->eps = ex; c->wlo = lo; c->whi = hi;
     c->have_data = true;
     c->ready = false;
@@ -866,8 +896,8 @@ int gsn_set_species(gsn_ctx* c, int n_species, int n_fine, const double* fine_ce
     std::vector<double> Sn((size_t)n_species * n_fine, 0.0);
     std::vector<int> kd(kind, kind + n_species);
     for (int s = 0; s < n_species; ++s) {
-        if (kd[s] < GSN_ANA || kd[s] > GSN_ANA_PEAK) return fail(c, GSN_ERR_ARG, "unknown species kind");
-        if (kd[s] == GSN_ANA_PEAK) continue;
+        if (kd[s] < GSN_ANA || kd[s] > GSN_MC_TEMPLATE) return fail(c, GSN_ERR_ARG, "unknown species kind");
+        if (kd[s] == GSN_ANA_PEAK || kd[s] == GSN_MC_TEMPLATE) continue;  // rows not used
         double tot = 0.0;
         for (int k = 0; k < n_fine; ++k) {
             const double v = spectra[(size_t)s * n_fine + k];
@@ -893,6 +923,7 @@ int gsn_set_species(gsn_ctx* c, int n_species, int n_fine, const double* fine_ce
         if (np > 8) return fail(c, GSN_ERR_ARG, "at most 8 AnaPeak species per dataset");
     }
     if (n_species != c->S) c->rfrac.clear();
+    c->tpl.clear();
     c->S = n_species; c->K = n_fine; c->E = E; c->Sn = Sn; c->kind = kd;
     c->mask.assign(dataset_mask, dataset_mask + (size_t)n_species * c->D);
     c->have_species = true;
@@ -911,8 +942,11 @@ int gsn_set_params(gsn_ctx* c, int n_params, const int* slot_map, int n_pulls, c
     for (int d = 0; d < c->D; ++d) {
         for (int i = 0; i < NS; ++i)
             if (sm[d * NS + i] < -1 || sm[d * NS + i] >= n_params) return fail(c, GSN_ERR_ARG, "slot_map entry out of range");
-        for (int i = 0; i < 5; ++i)
-            if (sm[d * NS + c->S + i] < 0) return fail(c, GSN_ERR_ARG, "response slots (LY, kB, a, b, c) must be mapped");
+        bool smeared = false;
+        for (int s = 0; s < c->S; ++s) smeared = smeared || (c->kind[s] < GSN_ANA_PEAK && c->mask[s * c->D + d]);
+        for (int i = 0; i < 5 && smeared; ++i)
+            if (sm[d * NS + c->S + i] < 0)
+                return fail(c, GSN_ERR_ARG, "response slots (LY, kB, a, b, c) of datasets with smeared species must be mapped");
         for (int s = 0; s < c->S; ++s)
             if (c->kind[s] == GSN_ANA_PEAK && c->mask[s * c->D + d] &&
                 (sm[d * NS + GSN_SLOT_M(c->S, s)] < 0 || sm[d * NS + GSN_SLOT_W(c->S, s)] < 0))
@@ -927,6 +961,29 @@ int gsn_set_params(gsn_ctx* c, int n_params, const int* slot_map, int n_pulls, c
     c->P = n_params; c->slot_map = sm; c->pull_p = pp; c->pull_c = pc; c->pull_w = pw;
     c->have_params = true;
     c->ready = false;
+    return GSN_OK;
+}
+
+int gsn_set_template(gsn_ctx* c, int species, int dataset, const double* hist) {
+    if (!c) return GSN_ERR_ARG;
+    if (!c->have_data || !c->have_species)
+        return fail(c, GSN_ERR_STATE, "gsn_set_data and gsn_set_species must come before the templates");
+    if (species < 0 || species >= c->S || dataset < 0 || dataset >= c->D)
+        return fail(c, GSN_ERR_ARG, "species or dataset out of range");
+    if (c->kind[species] != GSN_MC_TEMPLATE) return fail(c, GSN_ERR_ARG, "the species is not of kind GSN_MC_TEMPLATE");
+    const auto key = std::make_pair(dataset, species);
+    c->ready = false;
+    if (!hist) { c->tpl.erase(key); return GSN_OK; }
+    const int J = c->nb[dataset];
+    std::vector<double> h(hist, hist + J);
+    double tot = 0.0;
+    for (double v : h) {
+        if (!(v >= 0.0) || !std::isfinite(v)) return fail(c, GSN_ERR_ARG, "template values must be finite and >= 0");
+        tot += v;
+    }
+    if (!(tot > 0.0)) return fail(c, GSN_ERR_ARG, "a template must have a positive sum");
+    for (double& v : h) v /= tot;
+    c->tpl[key] = h;
     return GSN_OK;
 }
 
@@ -1029,6 +1086,7 @@ static int compute_species(gsn_ctx* c, const double* params_dev) {
     a.counts_stride = 0; a.win_stride = 0;
     a.Mbuf = (double*)c->Mbuf.p;
     a.sp_first = 0; a.sp_count = c->S;
+    if (!a.response) return GSN_OK;  // templates and peaks only: no per-species response shapes
     if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
     if (c->opt.precision == GSN_MIXED) {
         if ((rc = prepare_tensor_core(c))) return rc;
@@ -1231,7 +1289,7 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
         (size_t)c->total_bins * rs,                             // w
         (size_t)c->G * p.nbtask * a.NPART * sizeof(double),     // partial gradients
         (size_t)c->P * sizeof(double),                          // direct gradient terms
-        (size_t)p.dev_chunks * 2 * sizeof(double)};             // deviance partials
+        (size_t)p.dev_chunks * (2 + c->base.ntpl) * sizeof(double)};  // deviance and template partials
     size_t off[7], total = 0;
     for (int i = 0; i < 7; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
     if (total > GSN_NOALLOC_SCRATCH_BYTES)
@@ -1248,11 +1306,13 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     a.nll = nll_dev; a.grad = grad_dev; a.status = status_dev;
     a.want_grad = 1;
     a.work = nullptr;
-    CUDA_TRY(c, launch_columns(a, c->stream));
-    CUDA_TRY(c, launch_forward(a, c->stream));
+    if (a.response) {
+        CUDA_TRY(c, launch_columns(a, c->stream));
+        CUDA_TRY(c, launch_forward(a, c->stream));
+    }
     CUDA_TRY(c, launch_deviance(a, c->stream));
     CUDA_TRY(c, launch_devfinal(a, c->stream));
-    CUDA_TRY(c, launch_backward(a, c->stream));
+    if (a.response) CUDA_TRY(c, launch_backward(a, c->stream));
     CUDA_TRY(c, launch_gradfinal(a, c->stream));
     return GSN_OK;
 }

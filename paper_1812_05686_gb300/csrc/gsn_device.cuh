@@ -40,6 +40,8 @@ template <bool FAST = false> DEV double tb_g_rscale(const KArgs& a, int g, int i
 template <bool FAST = false> DEV int tb_ds_off(const KArgs& a, int d) { return (FAST || d < FASTD) ? a.ft.ds_off[d] : a.tb->ds_off[d]; }
 template <bool FAST = false> DEV int tb_ds_bins(const KArgs& a, int d) { return (FAST || d < FASTD) ? a.ft.ds_bins[d] : a.tb->ds_bins[d]; }
 template <bool FAST = false> DEV int tb_ds_group(const KArgs& a, int d) { return (FAST || d < FASTD) ? a.ft.ds_group[d] : a.tb->ds_group[d]; }
+template <bool FAST = false> DEV int tb_ds_resp(const KArgs& a, int d) { return (FAST || d < FASTD) ? a.ft.ds_resp[d] : a.tb->ds_resp[d]; }
+template <bool FAST = false> DEV int tb_g_active(const KArgs& a, int g) { return (FAST || g < FASTG) ? a.ft.g_active[g] : a.tb->g_active[g]; }
 
 // ------------------------------------------------------------------ math --
 DEV float ex2f(float x) {  // 2^x on the SFU

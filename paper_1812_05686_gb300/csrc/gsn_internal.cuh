@@ -43,10 +43,13 @@ constexpr int NRESP = 5;  // LY, kB, a, b, c
 struct Tables {
     int ds_bins[MAXD], ds_off[MAXD], ds_group[MAXD], ds_in_group[MAXD];
     int ds_npk[MAXD];           // AnaPeak species present in the dataset
+    int ds_ntpl[MAXD], ds_tpl0[MAXD];  // Monte Carlo templates of the dataset: count, first global index
+    int ds_resp[MAXD];          // the dataset has smeared species (its mu includes the response)
     int g_nds[MAXG], g_ds[MAXG][MAXGDS], g_bins[MAXG], g_edge_off[MAXG], g_node_off[MAXG];
     int g_resp[MAXG][NRESP];    // global parameter of each response slot
     int g_zero[MAXG];           // first edge of the group is 0 (gamma bin-at-zero)
     int g_jlin[MAXG];           // first bin of the group from which every bin is linear
+    int g_active[MAXG];         // some dataset of the group has smeared species
     double g_rscale[MAXG][NRESP];  // fixed multipliers of the response parameters (section 2.4 slices)
     int sp_kind[MAXS];
 };
@@ -57,9 +60,9 @@ struct Tables {
 constexpr int FASTG = 8, FASTD = 8;
 struct FastTables {
     int g_nds[FASTG], g_ds[FASTG][MAXGDS], g_bins[FASTG], g_edge_off[FASTG], g_node_off[FASTG];
-    int g_jlin[FASTG], g_zero[FASTG], g_resp[FASTG][NRESP];
+    int g_jlin[FASTG], g_zero[FASTG], g_active[FASTG], g_resp[FASTG][NRESP];
     double g_rscale[FASTG][NRESP];
-    int ds_off[FASTD], ds_bins[FASTD], ds_group[FASTD];
+    int ds_off[FASTD], ds_bins[FASTD], ds_group[FASTD], ds_resp[FASTD];
     int sp_kind[MAXS];          // complete (the species count is at most MAXS)
 };
 
@@ -72,6 +75,12 @@ struct KArgs {
     double s0, s1;    // stopping power model
     int max_nds;                // most datasets in one response group
     int fast;                   // every group and dataset is in the kernel-parameter copy ft
+    int response;               // some species passes through the response (else columns, forward
+                                // and adjoint are skipped: a pure template fit)
+    int ntpl;                   // Monte Carlo templates over all datasets
+    const int* tpl_s;           // [ntpl] species of each template (datasets in order)
+    const long long* tpl_off;   // [ntpl] offset of its normalised histogram in tpl
+    const double* tpl;          // concatenated histograms, n_bins of the template's dataset each
     FastTables ft;
     // device-resident problem arrays
     const Tables* tb;
@@ -107,7 +116,8 @@ struct KArgs {
     int nbtask, bw_warps, bw_bsplit, NPART;
     int ntile;             // forward tiles per group (max over groups)
     int dev_chunks;        // deviance blocks per toy
-    double* devpart;       // [T][dev_chunks][2]: partial deviance sum, status flags
+    double* devpart;       // [T][dev_chunks][2 + ntpl]: partial deviance sum, status flags,
+                           // partial sum_j w_j T_j of every template
     // outputs
     double* nll;
     double* grad;

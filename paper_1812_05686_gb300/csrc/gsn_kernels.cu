@@ -27,6 +27,7 @@ namespace gsn {
 template <class R, int RES, bool FAST>
 __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
     const int t = blockIdx.z, g = blockIdx.y;
+    if (!tb_g_active<FAST>(a, g)) return;  // no smeared species in the group
     const int k = blockIdx.x * COLBLK + threadIdx.x;
     __shared__ double sres[NRESP];
     // eps_d r_s as an unevaluated pair (hi + lo): one rounding of eps_d r_s to FP32 would be
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
         if (dd < tb_g_nds<FAST>(a, g)) {
             const int d = tb_g_ds<FAST>(a, g, dd);
             const double f = a.rfac[d * a.S + s];
-            if (a.ft.sp_kind[s] != 2 && f != 0.0) {
+            if (a.ft.sp_kind[s] < 2 && f != 0.0) {  // smeared species (Ana, AnaShift)
                 const int p = a.slot_map[d * a.NSLOT + s];
                 if (p >= 0) v = f * prm[p];
             }
@@ -290,6 +291,7 @@ template <class R, int RES>
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(KArgs a) {
     const int tile = blockIdx.x, split = blockIdx.y;
     const int t = blockIdx.z / a.G, g = blockIdx.z % a.G;
+    if (!tb_g_active(a, g)) return;  // no smeared species in the group
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int wlo, whi;
     toy_window_union(a, t, g, wlo, whi);
@@ -328,6 +330,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(KArgs a) {
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_gauss64(KArgs a) {
     const int tile = blockIdx.x, split = blockIdx.y;
     const int t = blockIdx.z / a.G, g = blockIdx.z % a.G;
+    if (!tb_g_active(a, g)) return;  // no smeared species in the group
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int wlo, whi;
     toy_window_union(a, t, g, wlo, whi);
@@ -439,9 +442,14 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
     const int t = blockIdx.x, c = blockIdx.y;
     __shared__ double sh[32];
     __shared__ PeakInfo pk;
+    __shared__ double tcoef[MAXS];    // eps_d f_ds r_s of the dataset's Monte Carlo templates
+    __shared__ long long toff[MAXS];  // and the offsets of their histograms
     const double* prm = a.params + (long long)t * a.params_stride;
     const double* cnt = a.counts + (long long)t * a.counts_stride;
     R* wout = reinterpret_cast<R*>(a.wbuf) + (long long)t * a.total_bins;
+    const int pstride = 2 + a.ntpl;
+    double* dp = a.devpart + ((long long)t * a.dev_chunks + c) * pstride;
+    for (int q = threadIdx.x; q < a.ntpl; q += blockDim.x) dp[2 + q] = 0.0;  // datasets outside the block
     const int chunk = (a.total_bins + a.dev_chunks - 1) / a.dev_chunks;
     const int b0 = c * chunk, b1 = min(a.total_bins, b0 + chunk);
     const long long sstride = a.total_bins;
@@ -455,16 +463,28 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
         int lo = a.win[t * a.win_stride + 2 * d], hi = a.win[t * a.win_stride + 2 * d + 1];
         lo = max(lo, 0); hi = min(hi, J);
         const int npk = load_peaks(a, prm, d, pk);
+        const int ntp = a.tb->ds_ntpl[d];
+        if (ntp > 0) {
+            __syncthreads();  // earlier readers of tcoef / toff are done
+            for (int q = threadIdx.x; q < ntp; q += blockDim.x) {
+                const int gq = a.tb->ds_tpl0[d] + q, s = a.tpl_s[gq];
+                const int p = a.slot_map[d * a.NSLOT + s];
+                tcoef[q] = p >= 0 ? a.rfac[d * a.S + s] * prm[p] : 0.0;
+                toff[q] = a.tpl_off[gq];
+            }
+            __syncthreads();
+        }
         const double* ed = a.edges + tb_g_edge_off(a, tb_ds_group(a, d));
         for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             double w = 0.0;
             if (j >= lo && j < hi) {
-                double mu = sum_splits(mrow + off + j, sstride, a.nsplit);
+                double mu = tb_ds_resp(a, d) ? sum_splits(mrow + off + j, sstride, a.nsplit) : 0.0;
                 for (int q = 0; q < npk; ++q) {
                     if (j < pk.lo[q] || j >= pk.hi[q]) continue;
                     const double m = pk.m[q], wd = pk.w[q];
                     mu += pk.r[q] * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
                 }
+                for (int q = 0; q < ntp; ++q) mu = fma(tcoef[q], a.tpl[toff[q] + j], mu);
                 const double n = cnt[off + j];
                 double term;
                 if (n > 0.0) {
@@ -479,13 +499,22 @@ __global__ void __launch_bounds__(256) k_deviance(KArgs a) {
             }
             wout[off + j] = (R)w;
         }
+        // template rate gradients: this block's share of sum_j w_j T_j (w as the adjoint reads it)
+        for (int q = 0; q < ntp; ++q) {
+            double gpart = 0.0;
+            for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+                const double wj = (double)wout[off + j];  // written above by this thread
+                if (wj != 0.0) gpart = fma(wj, a.tpl[toff[q] + j], gpart);
+            }
+            gpart = block_sum_d(gpart, sh);
+            if (threadIdx.x == 0) dp[2 + a.tb->ds_tpl0[d] + q] = gpart;
+        }
     }
     const double sum = block_sum_d(part, sh);
     const int any_bad_mu = __syncthreads_or(bad_mu), any_bad_fin = __syncthreads_or(bad_fin);
     if (threadIdx.x == 0) {
-        double* o = a.devpart + ((long long)t * a.dev_chunks + c) * 2;
-        o[0] = sum;
-        o[1] = (double)(any_bad_mu | (any_bad_fin << 1));
+        dp[0] = sum;
+        dp[1] = (double)(any_bad_mu | (any_bad_fin << 1));
     }
 }
 
@@ -536,10 +565,23 @@ __global__ void __launch_bounds__(256) k_devfinal(KArgs a) {
         }
     }
     if (threadIdx.x == 0) {
-        const double* dp = a.devpart + (long long)t * a.dev_chunks * 2;
+        const int pstride = 2 + a.ntpl;
+        const double* dp = a.devpart + (long long)t * a.dev_chunks * pstride;
         double nll = 0.0;
         int flags = 0;
-        for (int c = 0; c < a.dev_chunks; ++c) { nll += dp[2 * c]; flags |= (int)dp[2 * c + 1]; }
+        for (int c = 0; c < a.dev_chunks; ++c) { nll += dp[pstride * c]; flags |= (int)dp[pstride * c + 1]; }
+        if (a.want_grad && a.ntpl > 0) {
+            // Monte Carlo template rates: d mu_dj / d r_s = eps_d f_ds T_dsj
+            for (int d = 0; d < a.D; ++d)
+                for (int q = 0; q < a.tb->ds_ntpl[d]; ++q) {
+                    const int gq = a.tb->ds_tpl0[d] + q, s = a.tpl_s[gq];
+                    const int p = a.slot_map[d * a.NSLOT + s];
+                    if (p < 0) continue;
+                    double g = 0.0;
+                    for (int c = 0; c < a.dev_chunks; ++c) g += dp[pstride * c + 2 + gq];
+                    gdir[p] += a.rfac[d * a.S + s] * g;
+                }
+        }
         for (int i = 0; i < a.n_pulls; ++i) {
             const int p = a.pull_param[i];
             const double z = (prm[p] - a.pull_c[i]) / a.pull_w[i];
@@ -559,6 +601,7 @@ __global__ void __launch_bounds__(256) k_devfinal(KArgs a) {
 template <class R, int RES>
 __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     const int task = blockIdx.x, g = blockIdx.y, t = blockIdx.z;
+    if (!tb_g_active(a, g)) return;  // no smeared species in the group
     const int W = a.bw_warps;
     const int cbw = task / a.bw_bsplit, bsp = task % a.bw_bsplit;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -734,7 +777,7 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
         const int dd = i / a.S, s = i % a.S;
         double v = 0.0;
-        if (dd < nds && a.ft.sp_kind[s] != 2 && a.rfac[tb_g_ds(a, g, dd) * a.S + s] != 0.0) {
+        if (dd < nds && a.ft.sp_kind[s] < 2 && a.rfac[tb_g_ds(a, g, dd) * a.S + s] != 0.0) {
             R acc = 0;
             if constexpr (sizeof(R) == 4) {
                 const float* Srow = a.Sf + (long long)s * a.K + kbase;
@@ -760,6 +803,7 @@ __global__ void __launch_bounds__(128) k_gradfinal(KArgs a) {
     }
     // group by group (fixed order): sum of the per-task partials, then the slot-map scatter
     for (int g = 0; g < a.G; ++g) {
+        if (!tb_g_active(a, g)) continue;  // no adjoint partials for groups without smeared species
         for (int v = threadIdx.x; v < a.NPART; v += blockDim.x) {
             const double* p = a.partbuf + ((long long)t * a.G + g) * a.nbtask * a.NPART + v;
             double s = 0.0;
@@ -774,7 +818,7 @@ __global__ void __launch_bounds__(128) k_gradfinal(KArgs a) {
                 const int d = tb_g_ds(a, g, dd);
                 for (int s = 0; s < a.S; ++s) {
                     const double f = a.rfac[d * a.S + s];
-                    if (a.ft.sp_kind[s] == 2 || f == 0.0) continue;
+                    if (a.ft.sp_kind[s] >= 2 || f == 0.0) continue;
                     const int p = a.slot_map[d * a.NSLOT + s];
                     if (p >= 0) gr[p] += f * vals[NRESP + dd * a.S + s];
                 }
@@ -834,6 +878,7 @@ DEV void species_loop(const KArgs& a, int g, float xlo_w, float xhi_w, bool vali
 template <class R, int RES>
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_species(KArgs a) {
     const int tile = blockIdx.x, g = blockIdx.y;
+    if (!tb_g_active(a, g)) return;  // no smeared species in the group
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int J = tb_g_bins(a, g);
     const int j0 = (tile * FWD_WARPS + warp) * 32;
@@ -870,6 +915,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_species(KArgs a) {
 // FP64 Gaussian per-species path: exact erfc bin integrals (lanes <-> edges, 31 bins per warp)
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_species_gauss64(KArgs a) {
     const int tile = blockIdx.x, g = blockIdx.y;
+    if (!tb_g_active(a, g)) return;  // no smeared species in the group
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int J = tb_g_bins(a, g);
     const int j0 = (tile * FWD_WARPS + warp) * 31;
@@ -920,7 +966,7 @@ __global__ void k_mu_from_species(KArgs a) {
     double mu = 0.0;
     for (int s = 0; s < a.S; ++s) {
         const double f = a.rfac[d * a.S + s];
-        if (a.ft.sp_kind[s] == 2 || f == 0.0) continue;
+        if (a.ft.sp_kind[s] >= 2 || f == 0.0) continue;
         const int p = a.slot_map[d * a.NSLOT + s];
         if (p < 0) continue;
         mu = fma(f * prm[p], a.Mbuf[((long long)g * a.S + s) * a.Jmax + j], mu);
@@ -947,6 +993,11 @@ __global__ void k_expected_out(KArgs a) {
             const double m = prm[a.slot_map[d * a.NSLOT + a.S + 5 + 2 * s]];
             const double wd = prm[a.slot_map[d * a.NSLOT + a.S + 6 + 2 * s]];
             v = f * r * ncdf_diff((ed[j] - m) / wd, (ed[j + 1] - m) / wd);
+        } else if (a.ft.sp_kind[s] == 3) {
+            for (int q = 0; q < a.tb->ds_ntpl[d]; ++q) {
+                const int gq = a.tb->ds_tpl0[d] + q;
+                if (a.tpl_s[gq] == s) v = f * r * a.tpl[a.tpl_off[gq] + j];
+            }
         } else {
             v = f * r * a.Mbuf[((long long)g * a.S + s) * a.Jmax + j];
         }

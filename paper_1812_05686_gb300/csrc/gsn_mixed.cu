@@ -116,6 +116,7 @@ template <int RES, int NDS, bool FAST>
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
     const int tile = blockIdx.x, split = blockIdx.y;
     const int t = blockIdx.z / a.G, g = blockIdx.z % a.G;
+    if (!tb_g_active<FAST>(a, g)) return;  // no smeared species in the group
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ RecF srec[FWD_WARPS][32];
     int wlo, whi;
@@ -262,6 +263,7 @@ DEV float warp_sum_comp(float s, float c) {
 template <int RES, int NDS, bool FAST>
 __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
     const int task = blockIdx.x, g = blockIdx.y, t = blockIdx.z;
+    if (!tb_g_active<FAST>(a, g)) return;  // no smeared species in the group
     const int W = a.bw_warps;
     const int cbw = task / a.bw_bsplit, bsp = task % a.bw_bsplit;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -550,7 +552,7 @@ __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
     for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
         const int dd = i / a.S, s = i % a.S;
         double v = 0.0;
-        if (dd < nds && a.ft.sp_kind[s] != 2 && a.rfac[tb_g_ds<FAST>(a, g, dd) * a.S + s] != 0.0) {
+        if (dd < nds && a.ft.sp_kind[s] < 2 && a.rfac[tb_g_ds<FAST>(a, g, dd) * a.S + s] != 0.0) {
             const float* Srow = a.Sf + (long long)s * a.K + kbase;
             float acc = 0.f, cmp = 0.f, part32 = 0.f;
             for (int cc = 0; cc < ncol; ++cc) {

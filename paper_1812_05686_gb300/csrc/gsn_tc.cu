@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_species_tc(const __grid_constant__ 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int J = tb_g_bins(a, g);
     const int j0 = tile * TC_ROWS;
-    if (j0 >= J) return;  // whole CTA exits before any allocation
+    if (j0 >= J || !tb_g_active(a, g)) return;  // whole CTA exits before any allocation
     const int j = j0 + tid;
     const bool valid = j < J;
     const int jr = min(j, J - 1);

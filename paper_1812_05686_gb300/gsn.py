@@ -20,7 +20,7 @@ GSN_ERR_ARG, GSN_ERR_CUDA, GSN_ERR_NONPOSITIVE_MU, GSN_ERR_NONFINITE, GSN_ERR_ST
 GSN_ERR_TIMEOUT = -7
 GSN_FP64, GSN_MIXED = 0, 1
 GSN_RES_GAUSS, GSN_RES_GAMMA = 0, 1
-GSN_ANA, GSN_ANA_SHIFT, GSN_ANA_PEAK = 0, 1, 2
+GSN_ANA, GSN_ANA_SHIFT, GSN_ANA_PEAK, GSN_MC_TEMPLATE = 0, 1, 2, 3
 
 
 class gsn_options(C.Structure):
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH):
         "gsn_eval_grad_noalloc": (C.c_int, [vp, vp, vp, vp, vp]),
         "gsn_plan_info": (C.c_int, [vp, C.c_int, C.c_int, _IP]),
         "gsn_set_dataset_factors": (C.c_int, [vp, C.c_int, C.c_int, _DP, _DP]),
+        "gsn_set_template": (C.c_int, [vp, C.c_int, C.c_int, _DP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -88,7 +89,7 @@ def exported_symbols():
             "gsn_set_data", "gsn_set_species", "gsn_set_params", "gsn_eval", "gsn_eval_grad",
             "gsn_eval_grad_batch", "gsn_eval_grad_batch_dev", "gsn_expected", "gsn_stream",
             "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe", "gsn_eval_grad_noalloc",
-            "gsn_plan_info", "gsn_set_dataset_factors"]
+            "gsn_plan_info", "gsn_set_dataset_factors", "gsn_set_template"]
 
 
 GSN_K_COUNT = 8
@@ -243,6 +244,14 @@ class Context:
             rf, pf = _d(rate_factor)
         self._check(self.lib.gsn_set_dataset_factors(self.h, self.n_datasets, self.n_species, pr, pf))
 
+    def set_template(self, species, dataset, hist):
+        """Monte Carlo template (visible-bin histogram) of a GSN_MC_TEMPLATE species in one dataset."""
+        if hist is None:
+            self._check(self.lib.gsn_set_template(self.h, int(species), int(dataset), None))
+            return
+        h, ph = _d(hist)
+        self._check(self.lib.gsn_set_template(self.h, int(species), int(dataset), ph))
+
     def plan_info(self, n_toys=1, grad=True):
         """Work decomposition of a launch of n_toys toys (gsn_plan_info)."""
         out = (C.c_int * 5)()
@@ -280,6 +289,10 @@ def context_from_workload(work: dict, precision=GSN_FP64, counts=None, **kw) -> 
     ctx.set_params(int(work["n_params"]), work["slot_map"], work["pull_param"], work["pull_centre"], work["pull_width"])
     if work.get("resp_scale") is not None or work.get("rate_factor") is not None:
         ctx.set_dataset_factors(work.get("resp_scale"), work.get("rate_factor"))
+    for s, row in enumerate(work.get("templates") or []):
+        for d, hist in enumerate(row or []):
+            if hist is not None:
+                ctx.set_template(s, d, hist)
     return ctx
 
 

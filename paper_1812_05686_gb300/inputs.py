@@ -319,7 +319,7 @@ def template_like(seed: int = 8, n_bins: int = 1000, n_species: int = 16) -> dic
         sm[d, :S] = np.arange(S)
     rates = 10.0 ** rng.uniform(3.0, 5.0, size=S)
     return dict(
-        name=f"template_like_2x{n_bins}x{S}", fine_centres=np.array([0.5e-3]), spectra=np.zeros((S, 1)),
+        name=f"template_like_2x{n_bins}x{S}", fine_centres=np.array([0.5e-3, 1.5e-3]), spectra=np.zeros((S, 2)),
         kind=np.full(S, KIND_MC_TEMPLATE, np.int32), shift=np.zeros(S), mask=np.ones((S, D), np.uint8),
         edges=edges, exposure=np.array([1.0, 0.6]), win_lo=np.zeros(D, np.int32),
         win_hi=np.full(D, n_bins, np.int32), resolution=RES_GAMMA, birks_s0=BIRKS_S0, birks_s1=BIRKS_S1,
