@@ -436,3 +436,53 @@ def nll_batch(work, params, counts, windows):
 
 def nll_grad_batch(work, params, counts, windows):
     return np.array([nll_grad(work, params[t], counts[t], windows[t]) for t in range(len(params))])
+
+
+# ------------------------------------------------------- profile likelihood ----
+def fit(work, counts, start, free, lo=None, hi=None, windows=None, scale=None):
+    """Minimise the NLL over the parameters flagged in `free` (section 4.2 profile likelihood).
+
+    The library minimiser scipy L-BFGS-B is the step; the objective and its gradient are this
+    module's nll / nll_grad.  Bounds lo / hi (None = unbounded; rates are usually bounded at 0);
+    the search runs in scaled variables u = x / scale (default |start|, 1 where start is 0).
+    Returns (x_min, nll_min).
+    """
+    from scipy import optimize
+    x0 = np.asarray(start, np.float64)
+    free = np.asarray(free, bool)
+    sc = np.where(x0 != 0.0, np.abs(x0), 1.0) if scale is None else np.asarray(scale, np.float64)
+    idx = np.nonzero(free)[0]
+    if idx.size == 0:
+        return x0.copy(), nll(work, x0, counts, windows)
+
+    def full(u):
+        x = x0.copy()
+        x[idx] = u * sc[idx]
+        return x
+
+    def f(u):
+        x = full(u)
+        return nll(work, x, counts, windows), nll_grad(work, x, counts, windows)[idx] * sc[idx]
+
+    bounds = None
+    if lo is not None or hi is not None:
+        l = np.full(x0.size, -np.inf) if lo is None else np.asarray(lo, np.float64)
+        h = np.full(x0.size, np.inf) if hi is None else np.asarray(hi, np.float64)
+        bounds = [(l[i] / sc[i] if np.isfinite(l[i]) else None, h[i] / sc[i] if np.isfinite(h[i]) else None)
+                  for i in idx]
+    res = optimize.minimize(f, x0[idx] / sc[idx], jac=True, method="L-BFGS-B", bounds=bounds,
+                            options=dict(maxiter=5000, ftol=1e-15, gtol=1e-10, maxcor=20))
+    x = full(res.x)
+    return x, nll(work, x, counts, windows)
+
+
+def discovery_q0(work, counts, start, free, null_param, lo=None, hi=None, windows=None, scale=None):
+    """Discovery test statistic q0 = 2 (min NLL with parameter null_param fixed at 0 - min NLL),
+    0 when the free fit prefers a negative-going signal (one-sided, section 4.2)."""
+    x1, f1 = fit(work, counts, start, free, lo, hi, windows, scale)
+    s0 = np.asarray(start, np.float64).copy()
+    s0[null_param] = 0.0
+    free0 = np.asarray(free, bool).copy()
+    free0[null_param] = False
+    x0, f0 = fit(work, counts, s0, free0, lo, hi, windows, scale)
+    return max(0.0, 2.0 * (f0 - f1)), x1, f1, x0, f0

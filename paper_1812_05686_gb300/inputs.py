@@ -271,16 +271,18 @@ def multivariate_like(seed: int = 5, n_datasets: int = 4, n_slices: int = 64, n_
 
 
 def _visible_shapes(rng, x, n):
-    """n smooth positive shapes over visible-bin centres x [p.e.]: exponentials, bumps, betas, flat."""
+    """n smooth positive shapes over visible-bin centres x [p.e.]: exponentials, bumps, betas, flat
+    (scales relative to the range: decay lengths 5-30%, bump centres 10-90%, widths 2-6%)."""
     out = []
+    xm = max(float(x[-1]), 1.0)
     for i in range(n):
         kind = i % 4
         if kind == 0:
-            h = np.exp(-x / rng.uniform(50.0, 300.0))
+            h = np.exp(-x / (rng.uniform(0.05, 0.3) * xm))
         elif kind == 1:
-            h = np.exp(-0.5 * ((x - rng.uniform(100.0, 0.9 * x[-1])) / rng.uniform(20.0, 60.0)) ** 2)
+            h = np.exp(-0.5 * ((x - rng.uniform(0.1, 0.9) * xm) / (rng.uniform(0.02, 0.06) * xm)) ** 2)
         elif kind == 2:
-            q = rng.uniform(0.3, 1.0) * x[-1]
+            q = rng.uniform(0.3, 1.0) * xm
             h = np.where(x < q, x * x * (q - x) ** 2, 0.0)
         else:
             h = np.ones_like(x)

@@ -470,3 +470,46 @@ TEMPLATE_MUTANTS = {
 def test_planted_template_mistake_is_caught(monkeypatch, name):
     monkeypatch.setattr(O, "template", TEMPLATE_MUTANTS[name])
     assert pin_template_reproduces_smeared_species() > 1e-6
+
+
+# ------------------------------------------ profile likelihood (section 4.2) --------
+def _counting_experiment(n_obs, b):
+    """One bin, a signal and a background template; the background rate is known."""
+    w = I.template_like(n_bins=1, n_species=2)
+    w["templates"] = [[np.ones(1)], [np.ones(1)]]
+    w["exposure"] = np.array([1.0])
+    w["edges"] = w["edges"][:1]
+    w["mask"] = np.ones((2, 1), np.uint8)
+    w["win_lo"], w["win_hi"] = np.zeros(1, np.int32), np.ones(1, np.int32)
+    w["slot_map"] = w["slot_map"][:1]
+    w["theta0"] = np.array([5.0, b])
+    return w, np.array([float(n_obs)])
+
+
+@pytest.mark.parametrize("n_obs,b", [(30, 12.0), (7, 2.5), (4, 6.0)])
+def test_discovery_q0_matches_counting_closed_form(n_obs, b):
+    """q0 of a counting experiment with known background b: 2 (n ln(n/b) - (n - b)) for n > b, else 0
+    (the asymptotic discovery statistic)."""
+    w, n = _counting_experiment(n_obs, b)
+    q0, x1, f1, x0, f0 = O.discovery_q0(w, n, w["theta0"], free=[True, False], null_param=0,
+                                        lo=[0.0, 0.0], hi=[np.inf, np.inf])
+    ref = 2.0 * (n_obs * np.log(n_obs / b) - (n_obs - b)) if n_obs > b else 0.0
+    assert abs(q0 - ref) < 1e-8 * max(1.0, ref)
+    assert abs(x1[0] - max(n_obs - b, 0.0)) < 1e-6 * max(1.0, n_obs)
+
+
+def test_oracle_fit_recovers_asimov_minimum():
+    """The bounded L-BFGS fit of Asimov data returns the generating rates (templates + smeared species)."""
+    w = I.with_templates(I.borexino_like(n_bins=150, n_fine=1000), 2)
+    mu = np.concatenate([O.expected_counts(w, w["theta0"], d) for d in range(2)])
+    S = w["spectra"].shape[0]
+    # rates of species with counts in the histograms (the others leave the NLL unchanged)
+    tot = sum(O.expected_per_species(w, w["theta0"], d).sum(axis=0) for d in range(2))
+    seen = [s for s in range(S) if tot[s] > 1e-3 * tot.max()]
+    rates = np.unique(w["slot_map"][:, seen][w["slot_map"][:, seen] >= 0])
+    free = np.zeros(w["n_params"], bool)
+    free[rates] = True
+    start = w["theta0"] * np.where(free, 1.05, 1.0)
+    x, f = O.fit(w, mu, start, free, lo=np.zeros(w["n_params"]))
+    assert f < 1e-8
+    assert np.max(np.abs(x[rates] / w["theta0"][rates] - 1.0)) < 1e-4
