@@ -231,6 +231,34 @@ int gsn_eval_grad_batch_dev(gsn_ctx* ctx, int n_toys, const double* params_dev,
                             const double* toy_counts_dev, const int* toy_win_dev,
                             double* nll_dev, double* grad_dev, int* status_dev);
 
+/* Batched minimisation of the NLL of every toy (the profile likelihood of
+ * section 4.2; the toy Monte Carlo discovery test takes two calls, with the
+ * signal rate free and fixed at 0, and q0 = 2 (NLL_fixed - NLL_free)).  Each
+ * toy runs its own projected L-BFGS (FP64 state, history of 8 pairs,
+ * backtracking Armijo line search) in scaled variables u = x / scale; every
+ * iteration is one batched NLL + gradient evaluation (as in
+ * gsn_eval_grad_batch_dev, with the context's precision) and one update.
+ *   params_dev   [n_toys][n_params] device: start points in, minima out
+ *   toy_counts_dev, toy_win_dev   as in gsn_eval_grad_batch_dev
+ *   free_mask    [n_params] host: 1 = minimised over, 0 = held at its start value
+ *   lo, hi       [n_params] host bounds (NULL: unbounded); rates usually lo = 0
+ *   scale        [n_params] host, > 0 (NULL: 1); near 1/sqrt(Fisher) conditions best
+ *   max_evals    evaluations per toy (<= 0: 200); gtol: largest projected
+ *                scaled gradient component at convergence (< 0: 1e-6 for FP64,
+ *                1e-4 for the mixed path, whose NLL carries FP32 rounding); ftol:
+ *                relative NLL decrease of an accepted step at convergence (< 0: 1e-10)
+ *   nll_dev      [n_toys] device: NLL at the minimum
+ *   evals_dev    [n_toys] device or NULL: evaluations used
+ *   status_dev   [n_toys] device or NULL: 0 converged, 1 evaluation limit,
+ *                2 line search failed (the point returned is the best found),
+ *                -4 non-finite NLL at the start point
+ * Synchronous.  At most 64 parameters.  The paper has no batched minimiser: it
+ * fits toys one after another with MINUIT. */
+int gsn_minimize_batch_dev(gsn_ctx* ctx, int n_toys, double* params_dev, const double* toy_counts_dev,
+                           const int* toy_win_dev, const unsigned char* free_mask, const double* lo,
+                           const double* hi, const double* scale, int max_evals, double gtol, double ftol,
+                           double* nll_dev, int* evals_dev, int* status_dev);
+
 /* Expected counts per bin and species of one dataset (the validation quantity
  * of section 3.1): mu_per_species[n_bins[d]][n_species]; columns of species
  * absent from the dataset are zero.  Uses the value cache of gsn_eval, so the

@@ -76,6 +76,8 @@ struct gsn_ctx {
     Buf work;  // unsigned long long[K_COUNT] on the device
     // tensor-core per-species contraction (mixed): TF32 hi / lo split of S' and their TMA maps
     Buf s_hi, s_lo, tc_part, tc_err;
+    // batched minimiser: workspace, configuration, evaluation outputs
+    Buf fit_ws, fit_cfg, fit_eval, fit_ist;
     alignas(64) unsigned char tm_hi[128], tm_lo[128];
     bool tc_ready = false;
 };
@@ -770,6 +772,8 @@ void gsn_destroy(gsn_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     free_owned(c);
+    for (Buf* b : {&c->fit_ws, &c->fit_cfg, &c->fit_eval, &c->fit_ist})
+        if (b->p) cudaFree(b->p);
     for (Buf* b : {&c->colbuf, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
                    &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf, &c->s_hi, &c->s_lo,
                    &c->tc_part, &c->tc_err})
@@ -1197,6 +1201,82 @@ int gsn_eval_grad_batch_dev(gsn_ctx* c, int n_toys, const double* params_dev, co
     if (n_toys == 0) return GSN_OK;
     if (!params_dev || !toy_counts_dev || !toy_win_dev || !nll_dev) return fail(c, GSN_ERR_ARG, "NULL argument");
     return batch_device(c, n_toys, params_dev, toy_counts_dev, toy_win_dev, nll_dev, grad_dev, status_dev);
+}
+
+int gsn_minimize_batch_dev(gsn_ctx* c, int n_toys, double* params_dev, const double* toy_counts_dev,
+                           const int* toy_win_dev, const unsigned char* free_mask, const double* lo, const double* hi,
+                           const double* scale, int max_evals, double gtol, double ftol, double* nll_dev,
+                           int* evals_dev, int* status_dev) {
+    if (!c) return GSN_ERR_ARG;
+    int rc;
+    if ((rc = finalize(c))) return rc;
+    if (n_toys < 0) return fail(c, GSN_ERR_ARG, "n_toys must be >= 0");
+    if (n_toys == 0) return GSN_OK;
+    if (!params_dev || !toy_counts_dev || !toy_win_dev || !nll_dev || !free_mask)
+        return fail(c, GSN_ERR_ARG, "NULL argument");
+    if (c->P > 64) return fail(c, GSN_ERR_ARG, "the minimiser handles at most 64 parameters");
+    if (max_evals < 1) max_evals = 200;
+    // the mixed NLL carries FP32 rounding (~1e-7 relative): its gradient cannot resolve 1e-6 sigma
+    if (!(gtol >= 0.0)) gtol = c->opt.precision == GSN_MIXED ? 1e-4 : 1e-6;
+    if (!(ftol >= 0.0)) ftol = 1e-10;
+    const int T = n_toys, P = c->P, M = FIT_HISTORY;
+    // configuration: free mask, bounds, scales
+    std::vector<double> cfg((size_t)3 * P);
+    std::vector<unsigned char> fr(free_mask, free_mask + P);
+    for (int i = 0; i < P; ++i) {
+        cfg[i] = lo ? lo[i] : -INFINITY;
+        cfg[P + i] = hi ? hi[i] : INFINITY;
+        cfg[2 * P + i] = scale ? scale[i] : 1.0;
+        if (!(cfg[2 * P + i] > 0.0) || !std::isfinite(cfg[2 * P + i]) || cfg[i] > cfg[P + i] || std::isnan(cfg[i]) ||
+            std::isnan(cfg[P + i]))
+            return fail(c, GSN_ERR_ARG, "bad bound or scale of parameter " + std::to_string(i));
+    }
+    const size_t ws_doubles = (size_t)T * P * 4 + (size_t)T * M * P * 2 + (size_t)T * M + (size_t)T * 4;
+    if ((rc = ensure(c, c->fit_ws, ws_doubles * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->fit_cfg, cfg.size() * sizeof(double) + 64 + P))) return rc;
+    if ((rc = ensure(c, c->fit_eval, ((size_t)T * (P + 1)) * sizeof(double) + (size_t)T * sizeof(int)))) return rc;
+    if ((rc = ensure(c, c->fit_ist, ((size_t)T * 8 + 1) * sizeof(int)))) return rc;
+    double* ws = (double*)c->fit_ws.p;
+    FitArgs f{};
+    f.T = T; f.P = P; f.max_evals = max_evals; f.gtol = gtol; f.ftol = ftol;
+    f.fnoise = c->opt.precision == GSN_MIXED ? 1e-7 : 1e-13;
+    f.X = ws; f.G = ws + (size_t)T * P; f.D = ws + (size_t)2 * T * P; f.XT = ws + (size_t)3 * T * P;
+    f.S = ws + (size_t)4 * T * P; f.Y = f.S + (size_t)T * M * P; f.RHO = f.Y + (size_t)T * M * P;
+    f.dstate = f.RHO + (size_t)T * M;
+    double* cf = (double*)c->fit_cfg.p;
+    f.lo = cf; f.hi = cf + P; f.scale = cf + 2 * P;
+    f.free = (const unsigned char*)(cf + 3 * P);
+    double* ev = (double*)c->fit_eval.p;
+    f.nll = ev; f.grad = ev + T;
+    f.estatus = (const int*)(ev + (size_t)T * (P + 1));
+    f.istate = (int*)c->fit_ist.p;
+    f.active = f.istate + (size_t)T * 8;
+    CUDA_TRY(c, cudaMemcpyAsync(cf, cfg.data(), cfg.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync((void*)f.free, fr.data(), P, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(f.XT, params_dev, (size_t)T * P * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(f.istate, 0, (size_t)T * 8 * sizeof(int), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(f.dstate, 0, (size_t)T * 4 * sizeof(double), c->stream));
+    for (int it = 0; it < max_evals; ++it) {
+        if ((rc = batch_device(c, T, f.XT, toy_counts_dev, toy_win_dev, ev, ev + T, (int*)f.estatus))) return rc;
+        CUDA_TRY(c, cudaMemsetAsync(f.active, 0, sizeof(int), c->stream));
+        CUDA_TRY(c, launch_lbfgs(f, c->stream));
+        if ((it & 3) == 3 || it + 1 == max_evals) {
+            int active = 0;
+            CUDA_TRY(c, cudaMemcpyAsync(&active, f.active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            if (active == 0) break;
+        }
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(params_dev, f.X, (size_t)T * P * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpy2DAsync(nll_dev, sizeof(double), f.dstate, 4 * sizeof(double), sizeof(double), T,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+    if (evals_dev)
+        CUDA_TRY(c, cudaMemcpy2DAsync(evals_dev, sizeof(int), f.istate + 3, 8 * sizeof(int), sizeof(int), T,
+                                      cudaMemcpyDeviceToDevice, c->stream));
+    if (status_dev)
+        CUDA_TRY(c, cudaMemcpy2DAsync(status_dev, sizeof(int), f.istate + 4, 8 * sizeof(int), sizeof(int), T,
+                                      cudaMemcpyDeviceToDevice, c->stream));
+    return GSN_OK;
 }
 
 int gsn_eval_grad_batch(gsn_ctx* c, int n_toys, const double* params, const double* toy_counts, const int* toy_win,

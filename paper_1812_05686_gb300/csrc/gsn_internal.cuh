@@ -137,6 +137,33 @@ struct KArgs {
     int* tc_error;         // set to 1 by a CTA whose bounded wait timed out
 };
 
+// batched projected L-BFGS (gsn_fit.cu): per toy t, parameters [t][P]
+struct FitArgs {
+    int T, P, max_evals;
+    double gtol, ftol;          // projected gradient (scaled units), relative NLL decrease
+    double fnoise;              // relative rounding of the NLL tolerated by the line search
+    const unsigned char* free;  // [P] 1 = minimised over
+    const double* lo;           // [P] bounds
+    const double* hi;
+    const double* scale;        // [P] u = x / scale
+    const double* nll;          // evaluation of the trial points XT
+    const double* grad;
+    const int* estatus;
+    double* X;                  // accepted point, its gradient, search direction (scaled), trial point
+    double* G;
+    double* D;
+    double* XT;
+    double* S;                  // [T][M][P] curvature pairs (scaled), [T][M] 1 / (s . y)
+    double* Y;
+    double* RHO;
+    double* dstate;             // [T][4]: NLL at X, step, directional derivative
+    int* istate;                // [T][8]: state, pairs, newest slot, evaluations, status, restarts,
+                                // consecutive small decreases
+    int* active;                // toys still running after the update
+};
+cudaError_t launch_lbfgs(const FitArgs& f, cudaStream_t st);
+constexpr int FIT_HISTORY = 8;
+
 // launchers (gsn_kernels.cu); return cudaError_t of the launches
 cudaError_t launch_columns(const KArgs& a, cudaStream_t st);
 cudaError_t launch_forward(const KArgs& a, cudaStream_t st);

@@ -74,6 +74,8 @@ def load_library(path: str = LIB_PATH):
         "gsn_plan_info": (C.c_int, [vp, C.c_int, C.c_int, _IP]),
         "gsn_set_dataset_factors": (C.c_int, [vp, C.c_int, C.c_int, _DP, _DP]),
         "gsn_set_template": (C.c_int, [vp, C.c_int, C.c_int, _DP]),
+        "gsn_minimize_batch_dev": (C.c_int, [vp, C.c_int, vp, vp, vp, C.POINTER(C.c_ubyte), _DP, _DP, _DP,
+                                             C.c_int, C.c_double, C.c_double, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -89,7 +91,7 @@ def exported_symbols():
             "gsn_set_data", "gsn_set_species", "gsn_set_params", "gsn_eval", "gsn_eval_grad",
             "gsn_eval_grad_batch", "gsn_eval_grad_batch_dev", "gsn_expected", "gsn_stream",
             "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe", "gsn_eval_grad_noalloc",
-            "gsn_plan_info", "gsn_set_dataset_factors", "gsn_set_template"]
+            "gsn_plan_info", "gsn_set_dataset_factors", "gsn_set_template", "gsn_minimize_batch_dev"]
 
 
 GSN_K_COUNT = 8
@@ -243,6 +245,31 @@ class Context:
         if rate_factor is not None:
             rf, pf = _d(rate_factor)
         self._check(self.lib.gsn_set_dataset_factors(self.h, self.n_datasets, self.n_species, pr, pf))
+
+    def minimize_batch_dev(self, params, counts, wins, free, lo=None, hi=None, scale=None, max_evals=200,
+                           gtol=-1.0, ftol=-1.0, nll=None, evals=None, status=None):
+        """Batched L-BFGS minimisation (gsn_minimize_batch_dev); params (torch, device) is overwritten
+        with the minima.  Returns (nll, evals, status) device tensors."""
+        import torch
+        T = params.shape[0]
+        dev = params.device
+        nll = nll if nll is not None else torch.empty(T, dtype=torch.float64, device=dev)
+        evals = evals if evals is not None else torch.empty(T, dtype=torch.int32, device=dev)
+        status = status if status is not None else torch.empty(T, dtype=torch.int32, device=dev)
+        fr = np.ascontiguousarray(np.asarray(free, dtype=np.uint8))
+        args = []
+        for v in (lo, hi, scale):
+            if v is None:
+                args.append(None)
+            else:
+                a, pa = _d(v)
+                args.append((a, pa))
+        self._check(self.lib.gsn_minimize_batch_dev(
+            self.h, T, C.c_void_p(params.data_ptr()), C.c_void_p(counts.data_ptr()), C.c_void_p(wins.data_ptr()),
+            fr.ctypes.data_as(C.POINTER(C.c_ubyte)), *(a[1] if a else None for a in args), int(max_evals),
+            float(gtol), float(ftol), C.c_void_p(nll.data_ptr()), C.c_void_p(evals.data_ptr()),
+            C.c_void_p(status.data_ptr())))
+        return nll, evals, status
 
     def set_template(self, species, dataset, hist):
         """Monte Carlo template (visible-bin histogram) of a GSN_MC_TEMPLATE species in one dataset."""
