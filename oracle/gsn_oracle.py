@@ -32,6 +32,10 @@ Readings (the paper gives no formula for them):
 * "generalized gamma" response: the gamma density with shape d = mu^2/sigma^2
   and scale s = sigma^2/mu (mean mu, variance sigma^2), bin-integrated with the
   regularised incomplete gamma function;
+* generalized gamma with a free power p (resolution 2): Stacy's density
+  p x^(d-1) exp(-(x/s)^p) / (s^d Gamma(d/p)) with (d, s) moment-matched to the
+  column's mean and variance for the fit parameter p, bin-integrated as
+  P(d/p, (x/s)^p); the power sits in the last per-dataset slot;
 * spectra are point-sampled at the fine centres and normalised to unit sum;
   AnaShift moves the normalised spectrum up by round(shift / dE) fine bins;
 * AnaPeak: a Gaussian of position m and width w directly in p.e.;
@@ -43,11 +47,13 @@ Readings (the paper gives no formula for them):
   i.e. -ln L of Eq. (LL) up to a data-only constant, with the pull term read
   as the usual Gaussian constraint (Eq. (LL) prints its sign/factor garbled).
 
-Parity status of the gradient of the generalized-gamma response with respect to
-the shape d: the derivative of the regularised incomplete gamma function with
-respect to its shape has no library routine, so it is taken by fourth-order
-central differences in d (pinned against arbitrary-precision values in the
-tests).  Everything else is evaluated from closed forms or library special
+Parity status of the gradient of the gamma and generalized-gamma responses with
+respect to the shape: the derivative of the regularised incomplete gamma function
+with respect to its shape has no library routine, so it is taken by fourth-order
+central differences in the shape (pinned against arbitrary-precision values in
+the tests).  The generalized gamma's moment matching is solved by Newton's method
+on Stirling-series differences of log-gamma functions (pinned against 40-digit
+moments).  Everything else is evaluated from closed forms or library special
 functions.
 """
 from __future__ import annotations
@@ -58,7 +64,7 @@ import numpy as np
 from scipy import special
 
 KIND_ANA, KIND_ANA_SHIFT, KIND_ANA_PEAK, KIND_MC_TEMPLATE = 0, 1, 2, 3
-RES_GAUSS, RES_GAMMA = 0, 1
+RES_GAUSS, RES_GAMMA, RES_GGAMMA = 0, 1, 2
 _RESP = ("LY", "kB", "a", "b", "c")
 
 
@@ -166,6 +172,120 @@ def _gamma_pdf_times_y(d, y):
     return np.where(y > 0.0, v, 0.0)
 
 
+# ------------------------------------ generalized gamma with a free power p ----
+# Stacy's generalized gamma density, the line shape of the generalized-gamma response the paper cites
+# (section 2.3):  f(x; d, s, p) = p x^(d-1) exp(-(x/s)^p) / (s^d Gamma(d/p)),  x > 0,  whose CDF is
+# the regularised incomplete gamma P(d/p, (x/s)^p).  Reading: the power p is a fit parameter, and
+# every column's (d, s) follow from its mean and variance by moment matching,
+#     mu = s Gamma(x + a) / Gamma(x),   mu^2 + var = s^2 Gamma(x + 2a) / Gamma(x),   x = d/p, a = 1/p;
+# p = 1 is the gamma reading.  Eliminating s leaves one equation for x,
+#     H(x) = lnGamma(x + 2a) + lnGamma(x) - 2 lnGamma(x + a) = ln(1 + var/mu^2),
+# whose two sides are O(1/x): the log-gamma values themselves (O(x ln x)) cancel, so H and the other
+# log-gamma / digamma differences are evaluated from Stirling's series (Abramowitz & Stegun 6.1.40,
+# 6.3.18) with the leading terms combined analytically, after the recurrences lnGamma(z+1) =
+# lnGamma(z) + ln z and psi(z+1) = psi(z) + 1/z have moved the argument to >= 10.
+
+_BERNOULLI = (1.0 / 6, -1.0 / 30, 1.0 / 42, -1.0 / 30, 5.0 / 66, -691.0 / 2730, 7.0 / 6, -3617.0 / 510)  # B_2..B_16
+_X_STIRLING = 10.0
+
+
+def _lgamma_tail(z):
+    """lnGamma(z) - [(z - 1/2) ln z - z + ln(2 pi)/2] by the asymptotic series (z >= 10)."""
+    return sum(b / (2 * n * (2 * n - 1) * z ** (2 * n - 1)) for n, b in enumerate(_BERNOULLI, 1))
+
+
+def _digamma_tail(z):
+    """psi(z) - [ln z - 1/(2z)] by the asymptotic series (z >= 10)."""
+    return -sum(b / (2 * n * z ** (2 * n)) for n, b in enumerate(_BERNOULLI, 1))
+
+
+def _shift(x):
+    x = np.asarray(x, np.float64)
+    m = np.ceil(np.maximum(0.0, _X_STIRLING - x))
+    return x, m, x + m, int(m.max()) if m.size else 0
+
+
+def lgamma_diff(x, c):
+    """lnGamma(x + c) - lnGamma(x) for x > 0, c >= 0, without the cancellation of two log-gammas."""
+    x, m, xm, mmax = _shift(x)
+    out = (xm - 0.5) * np.log1p(c / xm) + c * np.log(xm + c) - c + _lgamma_tail(xm + c) - _lgamma_tail(xm)
+    for i in range(mmax):
+        out = out - np.where(i < m, np.log1p(c / (x + i)), 0.0)
+    return out
+
+
+def digamma_diff(x, c):
+    """psi(x + c) - psi(x) for x > 0, c >= 0."""
+    x, m, xm, mmax = _shift(x)
+    out = np.log1p(c / xm) + c / (2.0 * xm * (xm + c)) + _digamma_tail(xm + c) - _digamma_tail(xm)
+    for i in range(mmax):
+        out = out + np.where(i < m, c / ((x + i) * (x + c + i)), 0.0)
+    return out
+
+
+def ggamma_log_moment_ratio(x, a):
+    """H(x) = ln[Gamma(x + 2a) Gamma(x) / Gamma(x + a)^2] = ln(E[Y^2a] / E[Y^a]^2), Y ~ Gamma(x, 1)."""
+    x, m, xm, mmax = _shift(x)
+    e = a / xm
+    out = ((xm - 0.5) * np.log1p(-(e / (1.0 + e)) ** 2) + 2.0 * a * np.log1p(a / (xm + a))
+           + _lgamma_tail(xm + 2 * a) - 2.0 * _lgamma_tail(xm + a) + _lgamma_tail(xm))
+    for i in range(mmax):
+        xi = x + i
+        ei = a / xi
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.where(ei < 0.5, np.log1p(-(ei / (1.0 + ei)) ** 2),
+                         np.log(xi) + np.log(xi + 2 * a) - 2.0 * np.log(xi + a))
+        out = out - np.where(i < m, t, 0.0)
+    return out
+
+
+def ggamma_log_moment_ratio_dx(x, a):
+    """dH/dx = psi(x + 2a) - 2 psi(x + a) + psi(x)."""
+    x, m, xm, mmax = _shift(x)
+    out = (np.log1p(-(a / (xm + a)) ** 2) - a * a / (xm * (xm + a) * (xm + 2 * a))
+           + _digamma_tail(xm + 2 * a) - 2.0 * _digamma_tail(xm + a) + _digamma_tail(xm))
+    for i in range(mmax):
+        xi = x + i
+        out = out - np.where(i < m, 2.0 * a * a / (xi * (xi + a) * (xi + 2 * a)), 0.0)
+    return out
+
+
+def ggamma_shape_scale(mu, var, p):
+    """Moment matching for the generalized gamma of power p: shape d and scale s with mean mu and
+    variance var.  H(x) = ln(1 + var/mu^2) is solved for x = d/p by Newton's method on ln H against
+    ln x (H falls monotonically from +inf to 0); s = mu Gamma(x) / Gamma(x + 1/p)."""
+    mu = np.asarray(mu, np.float64)
+    var = np.asarray(var, np.float64)
+    a = 1.0 / p
+    r = np.log1p(var / (mu * mu))
+    u = np.log(a * a / r)  # large-x limit H ~ a^2 / x
+    for _ in range(80):
+        x = np.exp(u)
+        h = ggamma_log_moment_ratio(x, a)
+        g = np.log(h) - np.log(r)
+        step = np.clip(-g * h / (x * ggamma_log_moment_ratio_dx(x, a)), -5.0, 5.0)
+        u = u + step
+        if np.all(np.abs(g) < 1e-14):
+            break
+    else:
+        raise FloatingPointError("generalized-gamma moment matching did not converge")
+    x = np.exp(u)
+    return p * x, mu * np.exp(-lgamma_diff(x, a))
+
+
+def ggamma_bins(edges, d, s, p):
+    """R[j, k] = P(d_k/p, (x_{j+1}/s_k)^p) - P(d_k/p, (x_j/s_k)^p): bin integrals of the density."""
+    y = (np.clip(np.asarray(edges, np.float64), 0.0, None)[:, None] / s[None, :]) ** p
+    aa = np.broadcast_to((d / p)[None, :], y.shape)
+    return _gamma_cdf_diff(aa[:-1], y[:-1], y[1:])
+
+
+def response_ggamma(edges, mu, var, p):
+    """Generalized-gamma response of power p (moment-matched shape and scale per column)."""
+    d, s = ggamma_shape_scale(mu, var, p)
+    return ggamma_bins(edges, d, s, p)
+
+
 def peak_profile(edges, m, w):
     """AnaPeak: int over each bin of N(x; m, w) in p.e. (section 4.3, reading)."""
     z = (np.asarray(edges, np.float64) - m) / w
@@ -205,10 +325,13 @@ def dataset_factors(work, d):
 
 
 def _unpack(work, vals):
+    """Slots: S rates, (LY, kB, a, b, c), (m, w) per species, then the generalized-gamma power p."""
     S = np.asarray(work["spectra"]).shape[0]
     rates = vals[:S]
     resp = dict(zip(_RESP, vals[S:S + 5]))
-    peaks = vals[S + 5:].reshape(S, 2)
+    peaks = vals[S + 5:3 * S + 5].reshape(S, 2)
+    if int(work["resolution"]) == RES_GGAMMA:
+        resp["p"] = vals[3 * S + 5]
     return rates, resp, peaks
 
 
@@ -228,6 +351,8 @@ def response_matrix(work, edges, resp):
         raise FloatingPointError("non-positive mean or variance")
     if int(work["resolution"]) == RES_GAUSS:
         return response_gauss(edges, mu, np.sqrt(var))
+    if int(work["resolution"]) == RES_GGAMMA:
+        return response_ggamma(edges, mu, var, resp["p"])
     return response_gamma(edges, mu, var)
 
 
@@ -243,7 +368,7 @@ def expected_per_species(work, params, d):
     vals = dataset_values(work, params, d)
     rates, resp, peaks = _unpack(work, vals)
     scale, frac = dataset_factors(work, d)
-    resp = {k: resp[k] * scale[i] for i, k in enumerate(_RESP)}
+    resp = dict(resp, **{k: resp[k] * scale[i] for i, k in enumerate(_RESP)})
     edges = np.asarray(work["edges"][d], np.float64)
     eps = float(work["exposure"][d])
     Sp = species_spectra(work)
@@ -339,7 +464,7 @@ def nll_grad(work, params, counts, windows=None):
         vals = dataset_values(work, params, d)
         rates, resp, peaks = _unpack(work, vals)
         scale, frac = dataset_factors(work, d)
-        resp = {k: resp[k] * scale[i] for i, k in enumerate(_RESP)}
+        resp = dict(resp, **{k: resp[k] * scale[i] for i, k in enumerate(_RESP)})
         edges = np.asarray(work["edges"][d], np.float64)
         eps = float(work["exposure"][d])
         mask = np.asarray(work["mask"])[:, d].astype(bool)
@@ -369,6 +494,37 @@ def nll_grad(work, params, counts, windows=None):
                 g_mu = (w @ dR_dmu) * T
                 g_sig = (w @ dR_dsig) * T
                 g_var = g_sig / (2.0 * sig)
+            elif int(work["resolution"]) == RES_GGAMMA:
+                pw = resp["p"]
+                a = 1.0 / pw
+                dsh, sc = ggamma_shape_scale(mu_k, var_k, pw)
+                xs = dsh / pw
+                ee = np.clip(edges, 0.0, None)[:, None]
+                y = (ee / sc[None, :]) ** pw
+                aa = np.broadcast_to(xs[None, :], y.shape)
+                Pa = _gamma_P_dshape(aa, y)          # dP(a, y)/da at the edges
+                py = _gamma_pdf_times_y(aa, y)        # y dP/dy
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    pyl = np.where(ee > 0.0, py * np.log(ee / sc[None, :]), 0.0)
+                # bin-integral derivatives at fixed (d, s, p): a = d/p, y = (x/s)^p
+                dR_dd = (Pa[1:] - Pa[:-1]) / pw
+                dR_dlns = -pw * (py[1:] - py[:-1])
+                dR_dp = -(dsh / pw**2)[None, :] * (Pa[1:] - Pa[:-1]) + (pyl[1:] - pyl[:-1])
+                g_d = (w @ dR_dd) * T
+                g_u = (w @ dR_dlns) * T
+                g_pe = (w @ dR_dp) * T
+                # moment matching H(x, a) = ln rho, ln s = ln mu - G(x, a), G = lnGamma(x+a) - lnGamma(x):
+                # implicit derivatives of x = d/p and u = ln s with respect to (mu, var, p)
+                Hx = ggamma_log_moment_ratio_dx(xs, a)
+                Ha = 2.0 * (digamma_diff(xs, 2 * a) - digamma_diff(xs, a))
+                Gx = digamma_diff(xs, a)
+                Ga = special.digamma(xs + a)
+                r_mu = -2.0 * var_k / (mu_k * (mu_k**2 + var_k))
+                r_var = 1.0 / (mu_k**2 + var_k)
+                x_mu, x_var, x_p = r_mu / Hx, r_var / Hx, Ha / (pw**2 * Hx)
+                g_mu = g_d * pw * x_mu + g_u * (1.0 / mu_k - Gx * x_mu)
+                g_var = g_d * pw * x_var + g_u * (-Gx * x_var)
+                gs[3 * S + 5] += float(np.sum(g_pe + g_d * (xs + pw * x_p) + g_u * (-Gx * x_p + Ga / pw**2)))
             else:
                 dsh, sc = gamma_shape_scale(mu_k, var_k)
                 y = np.clip(edges, 0.0, None)[:, None] / sc[None, :]

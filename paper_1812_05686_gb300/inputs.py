@@ -23,11 +23,13 @@ mask         (S, D)      1 where species s contributes to dataset d
 edges        [D] arrays  visible-energy bin edges [p.e.], ascending
 exposure     (D,)        exposure of each dataset (section 4.1)
 win_lo/win_hi (D,)       default fit window [lo, hi) in bins
-resolution   int         0 = Gaussian, 1 = generalized gamma
+resolution   int         0 = Gaussian, 1 = gamma (generalized gamma of power 1),
+                         2 = generalized gamma with a free power p
 birks_s0/s1  float       stopping-power model S(E) = s0 + s1/E [MeV/cm, MeV^2/cm]
 n_params     int         number of global fit parameters
-slot_map     (D, 3S+5)   global parameter index of each per-dataset slot:
-                         [rate_0..rate_{S-1}, LY, kB, a, b, c, m_0, w_0, ..., m_{S-1}, w_{S-1}]
+slot_map     (D, 3S+6)   global parameter index of each per-dataset slot:
+                         [rate_0..rate_{S-1}, LY, kB, a, b, c, m_0, w_0, ..., m_{S-1}, w_{S-1}, p]
+                         (p: the power of the generalized-gamma response, resolution 2 only)
                          (-1 = unused: peak slots of non-peak species, rates of
                          species absent from the dataset)
 pull_param/pull_centre/pull_width   Gaussian pull terms (section 4.1, Eq. LL)
@@ -44,7 +46,7 @@ from __future__ import annotations
 import numpy as np
 
 KIND_ANA, KIND_ANA_SHIFT, KIND_ANA_PEAK, KIND_MC_TEMPLATE = 0, 1, 2, 3
-RES_GAUSS, RES_GAMMA = 0, 1
+RES_GAUSS, RES_GAMMA, RES_GGAMMA = 0, 1, 2
 
 # Stopping-power model constants used by every workload (MeV/cm and MeV^2/cm):
 # roughly electron dE/dx in a ~0.88 g/cm^3 organic scintillator.
@@ -53,7 +55,11 @@ BIRKS_S1 = 0.155
 
 
 def n_slots(n_species: int) -> int:
-    """Per-dataset slot count: S rates, 5 response parameters, 2 peak slots per species."""
+    """Per-dataset slot count: S rates, 5 response parameters, 2 peak slots per species, the power."""
+    return 3 * n_species + 6
+
+
+def slot_power(n_species: int) -> int:
     return 3 * n_species + 5
 
 
@@ -343,7 +349,8 @@ def with_templates(work: dict, n_templates: int, seed: int = 9) -> dict:
     for d in range(D):
         sm[d, :S0] = old[d, :S0]
         sm[d, S:S + 5] = old[d, S0:S0 + 5]
-        sm[d, S + 5:S + 5 + 2 * S0] = old[d, S0 + 5:]
+        sm[d, S + 5:S + 5 + 2 * S0] = old[d, S0 + 5:3 * S0 + 5]
+        sm[d, slot_power(S)] = old[d, slot_power(S0)]
         sm[d, S0:S] = P0 + np.arange(n_templates)
     tpl = [None] * S0 + _template_set(rng, work["edges"], shapes)
     tpl = [t if t is not None else [None] * D for t in tpl]
@@ -412,3 +419,20 @@ def toy_batch(work: dict, mu0: list, n_toys: int, seed0: int = 1000,
     win = toy_windows(n_toys, min(nb), min(w_min, min(nb)), min(w_max, min(nb)), seed0 + 2 * n_toys)
     windows = np.repeat(win[:, None, :], D, axis=1)  # (T, D, 2)
     return dict(counts=counts, params=params, windows=windows)
+
+
+def with_power(work: dict, p: float = 1.3, pull_width: float = 0.0) -> dict:
+    """The workload with the generalized-gamma response of power p (resolution 2): a new global
+    parameter "p" (appended) fills every dataset's power slot; pull_width > 0 adds a pull to p."""
+    S, D, P0 = work["spectra"].shape[0], len(work["edges"]), int(work["n_params"])
+    sm = np.array(work["slot_map"], dtype=np.int32, copy=True)
+    sm[:, slot_power(S)] = P0
+    out = dict(work)
+    out.update(name=work.get("name", "workload") + f"+ggamma{p:g}", resolution=RES_GGAMMA, slot_map=sm,
+               n_params=P0 + 1, theta0=np.concatenate([work["theta0"], [p]]),
+               param_names=list(work.get("param_names", [f"p{i}" for i in range(P0)])) + ["p"])
+    if pull_width > 0:
+        out.update(pull_param=np.concatenate([work["pull_param"], [P0]]).astype(np.int32),
+                   pull_centre=np.concatenate([work["pull_centre"], [p]]),
+                   pull_width=np.concatenate([work["pull_width"], [pull_width]]))
+    return out

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_host_only_calls(lib):
     from paper_1812_05686_gb300 import gsn
-    assert lib.gsn_n_slots(16) == 53
+    assert lib.gsn_n_slots(16) == 54
     o = gsn.gsn_options()
     assert lib.gsn_default_options(C.byref(o)) == 0
     assert o.precision == gsn.GSN_FP64 and o.max_toys_per_launch == 4096

@@ -38,7 +38,7 @@ def _workload_20_species(resolution):
         old = w["slot_map"][d]
         sm[d, :S] = old[:S]
         sm[d, 20:25] = old[S:S + 5]
-        sm[d, 25:25 + 2 * S] = old[S + 5:]
+        sm[d, 25:25 + 2 * S] = old[S + 5:3 * S + 5]
         sm[d, S:20] = P0 + np.arange(20 - S)
     theta = np.concatenate([w["theta0"], 10.0 ** rng.uniform(2, 4, 20 - S)])
     w2 = dict(w, spectra=spectra, kind=kind, shift=shift, mask=mask, slot_map=sm, n_params=P0 + 20 - S, theta0=theta)

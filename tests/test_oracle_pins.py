@@ -513,3 +513,149 @@ def test_oracle_fit_recovers_asimov_minimum():
     x, f = O.fit(w, mu, start, free, lo=np.zeros(w["n_params"]))
     assert f < 1e-8
     assert np.max(np.abs(x[rates] / w["theta0"][rates] - 1.0)) < 1e-4
+
+
+# --------------------- generalized gamma with a free power p (section 2.3) --------
+@pytest.mark.parametrize("x", [1e-5, 0.003, 0.5, 3.0, 9.9, 10.0, 57.0, 800.0, 2.0e4])
+def test_log_gamma_and_digamma_differences_against_mpmath(x):
+    X = mpmath.mpf(x)
+    for c in (0.25, 0.4, 1.0, 2.5):
+        lg = mpmath.loggamma(X + c) - mpmath.loggamma(X)
+        dg = mpmath.digamma(X + c) - mpmath.digamma(X)
+        H = mpmath.loggamma(X + 2 * c) + mpmath.loggamma(X) - 2 * mpmath.loggamma(X + c)
+        Hx = mpmath.digamma(X + 2 * c) + mpmath.digamma(X) - 2 * mpmath.digamma(X + c)
+        assert abs(float(O.lgamma_diff(np.array([x]), c)[0] / lg) - 1.0) < 1e-14
+        assert abs(float(O.digamma_diff(np.array([x]), c)[0] / dg) - 1.0) < 1e-14
+        assert abs(float(O.ggamma_log_moment_ratio(np.array([x]), c)[0] / H) - 1.0) < 1e-14
+        assert abs(float(O.ggamma_log_moment_ratio_dx(np.array([x]), c)[0] / Hx) - 1.0) < 1e-13
+
+
+def pin_ggamma_moments():
+    """Moment matching: the generalized gamma of the returned (d, s, p) has the requested mean and
+    variance, its moments E[X^r] = s^r Gamma((d + r)/p) / Gamma(d/p) taken in 40-digit arithmetic."""
+    mu = np.array([0.01, 0.3, 1.0, 5.0, 30.0, 200.0, 1000.0, 1.0e4])
+    var = 10.0 + 1.1 * mu + 2e-4 * mu * mu
+    worst = 0.0
+    for p in (0.4, 0.8, 1.0, 1.3, 2.0, 3.5):
+        d, s = O.ggamma_shape_scale(mu, var, p)
+        for i in range(mu.size):
+            D, Sc, Pw = mpmath.mpf(d[i]), mpmath.mpf(s[i]), mpmath.mpf(p)
+            m1 = Sc * mpmath.exp(mpmath.loggamma((D + 1) / Pw) - mpmath.loggamma(D / Pw))
+            m2 = Sc ** 2 * mpmath.exp(mpmath.loggamma((D + 2) / Pw) - mpmath.loggamma(D / Pw))
+            worst = max(worst, abs(float(m1 / mu[i]) - 1.0), abs(float((m2 - m1 ** 2) / var[i]) - 1.0))
+    return worst
+
+
+def test_ggamma_moment_matching_against_mpmath():
+    assert pin_ggamma_moments() < 1e-12
+
+
+def test_ggamma_power_one_is_the_gamma_response():
+    mu = np.array([0.02, 2.0, 50.0, 500.0, 1200.0]); var = 10.0 + 1.1 * mu + 2e-4 * mu * mu
+    d, s = O.ggamma_shape_scale(mu, var, 1.0)
+    assert np.max(np.abs(d / (mu * mu / var) - 1.0)) < 1e-13 and np.max(np.abs(s / (var / mu) - 1.0)) < 1e-13
+    edges = np.arange(0.0, 1500.0)
+    Rg, Rgg = O.response_gamma(edges, mu, var), O.response_ggamma(edges, mu, var, 1.0)
+    assert np.max(np.abs(Rgg - Rg)) < 1e-13
+
+
+def pin_ggamma_closed_forms():
+    """Power 2: shape 1 is the half-normal (CDF erf(x/s)), shape 2 the Rayleigh (CDF 1 - exp(-(x/s)^2))."""
+    edges = np.linspace(0.0, 12.0, 41)
+    s = np.array([2.7, 4.1])
+    half = O.ggamma_bins(edges, np.array([1.0, 1.0]), s, 2.0)
+    ray = O.ggamma_bins(edges, np.array([2.0, 2.0]), s, 2.0)
+    worst = 0.0
+    for k in range(2):
+        F1 = np.array([math.erf(e / s[k]) for e in edges])
+        F2 = np.array([-math.expm1(-(e / s[k]) ** 2) for e in edges])
+        worst = max(worst, float(np.max(np.abs(half[:, k] - np.diff(F1)))), float(np.max(np.abs(ray[:, k] - np.diff(F2)))))
+    return worst
+
+
+def test_ggamma_half_normal_and_rayleigh_closed_forms():
+    assert pin_ggamma_closed_forms() < 1e-14
+
+
+@pytest.mark.parametrize("m,var,p,lo,hi", [
+    (3.0, 13.3, 0.7, 0.0, 1.0), (3.0, 13.3, 1.6, 5.0, 6.0), (50.0, 65.5, 0.5, 49.0, 50.0),
+    (50.0, 65.5, 2.5, 80.0, 81.0), (480.0, 584.0, 1.3, 470.0, 471.0), (480.0, 584.0, 3.0, 560.0, 561.0)])
+def test_ggamma_bin_integral_against_mpmath_quadrature(m, var, p, lo, hi):
+    d, s = O.ggamma_shape_scale(np.array([m]), np.array([var]), p)
+    D, Sc, Pw = mpmath.mpf(d[0]), mpmath.mpf(s[0]), mpmath.mpf(p)
+    norm = Pw / (Sc ** D * mpmath.gamma(D / Pw))
+    if lo > 0:
+        ref = mpmath.quad(lambda x: norm * x ** (D - 1) * mpmath.exp(-(x / Sc) ** Pw), [lo, (lo + hi) / 2, hi])
+    else:
+        ref = mpmath.gammainc(D / Pw, 0, (mpmath.mpf(hi) / Sc) ** Pw, regularized=True)
+    got = O.ggamma_bins(np.array([lo, hi]), d, s, p)[0, 0]
+    assert abs(got / float(ref) - 1.0) < 1e-11
+
+
+def test_ggamma_rows_sum_to_one_from_zero():
+    mu = np.array([0.02, 2.0, 50.0, 500.0]); var = 10.0 + 1.1 * mu + 2e-4 * mu * mu
+    edges = np.concatenate([np.arange(0.0, 3000.0), np.arange(3000.0, 200001.0, 100.0)])
+    for p in (0.6, 1.5, 2.5):
+        R = O.response_ggamma(edges, mu, var, p)
+        assert np.max(np.abs(R.sum(axis=0) - 1.0)) < 1e-12
+
+
+def _gg_small(p=1.4):
+    w = I.with_power(I.borexino_like(n_bins=220, n_fine=1500), p)
+    mu = np.concatenate([O.expected_counts(w, w["theta0"], d) for d in range(2)])
+    return w, I.poisson_counts(mu, 61)
+
+
+def pin_ggamma_gradient():
+    w, n = _gg_small()
+    pt = I.perturbed_points(w["theta0"], 1, 62, rel=0.02)[0]
+    g = O.nll_grad(w, pt, n)
+    gf = O.nll_grad_fd(w, pt, n, rel=1e-4)
+    scale = np.abs(g) + 1e-3 * np.max(np.abs(g))
+    return float(np.max(np.abs(g - gf) / scale))
+
+
+def test_ggamma_gradient_matches_finite_differences():
+    assert pin_ggamma_gradient() < 2e-6
+
+
+def test_ggamma_asimov_and_rate_identity():
+    w, n = _gg_small(0.8)
+    mu = np.concatenate([O.expected_counts(w, w["theta0"], d) for d in range(2)])
+    assert O.nll(w, w["theta0"], mu) == pytest.approx(0.0, abs=1e-9)
+    assert np.max(np.abs(O.nll_grad(w, w["theta0"], mu))) < 1e-8
+    w["pull_param"] = np.zeros(0, np.int32); w["pull_centre"] = np.zeros(0); w["pull_width"] = np.zeros(0)
+    assert pin_rate_identity(w, I.perturbed_points(w["theta0"], 1, 63)[0], n) < 1e-11
+
+
+def test_ggamma_power_one_workload_matches_gamma_workload():
+    base = I.borexino_like(n_bins=200, n_fine=1500)
+    w = I.with_power(base, 1.0)
+    mu = np.concatenate([O.expected_counts(base, base["theta0"], d) for d in range(2)])
+    n = I.poisson_counts(mu, 64)
+    pt = I.perturbed_points(base["theta0"], 1, 65)[0]
+    assert abs(O.nll(w, np.concatenate([pt, [1.0]]), n) / O.nll(base, pt, n) - 1.0) < 1e-12
+    g, g0 = O.nll_grad(w, np.concatenate([pt, [1.0]]), n), O.nll_grad(base, pt, n)
+    assert np.max(np.abs(g[:-1] - g0)) <= 1e-9 * np.max(np.abs(g0))
+
+
+GG_MUTANTS = {
+    "power dropped from the CDF argument": ("ggamma_bins", lambda e, d, s, p: O._gamma_cdf_diff(
+        np.broadcast_to((d / p)[None, :], (len(e) - 1, d.size)),
+        np.clip(np.asarray(e)[:-1, None], 0, None) / s[None, :], np.asarray(e)[1:, None] / s[None, :])),
+    "moment ratio with a instead of 2a": ("ggamma_log_moment_ratio", lambda x, a: O.lgamma_diff(x, a) - 2.0 * O.lgamma_diff(x, 0.5 * a)),
+    "digamma difference sign": ("digamma_diff", lambda x, c: -(O.special.digamma(x + c) - O.special.digamma(x))),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GG_MUTANTS))
+def test_planted_ggamma_mistake_is_caught(monkeypatch, name):
+    attr, fn = GG_MUTANTS[name]
+    monkeypatch.setattr(O, attr, fn)
+    caught = []
+    for pin, tol in ((pin_ggamma_moments, 1e-12), (pin_ggamma_closed_forms, 1e-14), (pin_ggamma_gradient, 2e-6)):
+        try:
+            caught.append(pin() > tol)
+        except Exception:
+            caught.append(True)
+    assert any(caught), f"no pin caught the planted mistake '{name}'"
