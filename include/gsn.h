@@ -61,6 +61,11 @@ extern "C" {
 /* resolution shape (section 2.3) */
 #define GSN_RES_GAUSS             0
 #define GSN_RES_GAMMA             1  /* gamma density with mean mu_k, variance sigma_k^2 */
+#define GSN_RES_GGAMMA            2  /* generalized gamma of free power p (Stacy's density
+                                        p x^(d-1) exp(-(x/s)^p) / (s^d Gamma(d/p)), the
+                                        generalized-gamma line shape cited in section 2.3) with
+                                        (d, s) moment-matched to mu_k and sigma_k^2; p is the
+                                        fit parameter in the power slot; p = 1 is GSN_RES_GAMMA */
 
 /* species kinds (section 4.3) */
 #define GSN_ANA                   0  /* fine spectrum smeared by the response */
@@ -69,11 +74,12 @@ extern "C" {
 #define GSN_MC_TEMPLATE           3  /* Monte Carlo template: a histogram in each dataset's visible
                                         bins (section 3.2 template fit, gsn_set_template) */
 
-/* per-dataset parameter slots: gsn_n_slots(S) = 3 S + 5
+/* per-dataset parameter slots: gsn_n_slots(S) = 3 S + 6
  *   [0, S)              rate r_s of species s (counts per unit exposure)
  *   S + 0 .. S + 4      LY [p.e./MeV], kB [cm/MeV], a [p.e.^2], b [p.e.], c
  *   S + 5 + 2 s         peak position m_s [p.e.]   (AnaPeak species only)
- *   S + 5 + 2 s + 1     peak width w_s [p.e.]      (AnaPeak species only)   */
+ *   S + 5 + 2 s + 1     peak width w_s [p.e.]      (AnaPeak species only)
+ *   3 S + 5             power p > 0 of the generalized gamma (GSN_RES_GGAMMA only) */
 #define GSN_SLOT_LY(S)    ((S) + 0)
 #define GSN_SLOT_KB(S)    ((S) + 1)
 #define GSN_SLOT_A(S)     ((S) + 2)
@@ -81,6 +87,7 @@ extern "C" {
 #define GSN_SLOT_C(S)     ((S) + 4)
 #define GSN_SLOT_M(S, s)  ((S) + 5 + 2 * (s))
 #define GSN_SLOT_W(S, s)  ((S) + 6 + 2 * (s))
+#define GSN_SLOT_P(S)     (3 * (S) + 5)
 
 #define GSN_MAX_DATASETS  512  /* histograms, or slices of histograms (section 2.4) */
 #define GSN_MAX_SPECIES   64
@@ -91,7 +98,7 @@ typedef struct gsn_ctx gsn_ctx;
 
 typedef struct gsn_options {
     int    precision;      /* GSN_FP64 or GSN_MIXED */
-    int    resolution;     /* GSN_RES_GAUSS or GSN_RES_GAMMA */
+    int    resolution;     /* GSN_RES_GAUSS, GSN_RES_GAMMA or GSN_RES_GGAMMA */
     double band_cut;       /* response band: a column is evaluated only where its
                               density exceeds exp(-band_cut) times its value at
                               the mean (<= 0: 34.5 for FP64, 20.7 for mixed) */
@@ -128,7 +135,7 @@ void gsn_destroy(gsn_ctx* ctx);
 /* Message of the last failure on this context ("" if none; static string if ctx is NULL). */
 const char* gsn_last_error(const gsn_ctx* ctx);
 
-/* Number of per-dataset slots for n_species species (3 n_species + 5). */
+/* Number of per-dataset slots for n_species species (3 n_species + 6). */
 int gsn_n_slots(int n_species);
 
 /* Observed histograms (section 4.1 inputs: histogram, exposure).
@@ -204,7 +211,7 @@ int gsn_set_template(gsn_ctx* ctx, int species, int dataset, const double* hist)
 /* NLL at params[n_params] with the counts and windows of gsn_set_data.
  * Keeps the per-species shapes of every response group (section 2.5 value
  * cache, shared with gsn_expected) and recomputes them only when a response
- * parameter (LY, kB, a, b, c) changes; rate-only steps skip the response.
+ * parameter (LY, kB, a, b, c, p) changes; rate-only steps skip the response.
  * Errors: GSN_ERR_NONPOSITIVE_MU (nll = +inf), GSN_ERR_NONFINITE. */
 int gsn_eval(gsn_ctx* ctx, const double* params, double* nll);
 

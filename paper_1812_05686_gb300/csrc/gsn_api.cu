@@ -41,7 +41,8 @@ struct gsn_ctx {
     std::vector<unsigned char> mask;  // [S][D]
     int P = 0;
     std::vector<int> slot_map;
-    std::vector<double> rscale;       // [D][5] response multipliers of each dataset (section 2.4 slices)
+    std::vector<double> rscale;       // [D][NRESP] response multipliers of each dataset (section 2.4 slices;
+                                      // the power of the generalized gamma is not scaled)
     std::vector<double> rfrac;        // [D][S] rate fraction of each species in each dataset
     std::map<std::pair<int, int>, std::vector<double>> tpl;  // (dataset, species) -> normalised template
     std::vector<int> pull_p;
@@ -54,7 +55,7 @@ struct gsn_ctx {
     // persistent device buffers
     std::vector<Buf> owned;
     // scratch
-    Buf colbuf, blkbuf, mubuf, wbuf, partbuf, gdirect, devbuf, params, counts_b, win_b, nll_b, grad_b, status_b, Mbuf,
+    Buf colbuf, colbuf2, blkbuf, mubuf, wbuf, partbuf, gdirect, devbuf, params, counts_b, win_b, nll_b, grad_b, status_b, Mbuf,
         outbuf;
     unsigned long long scratch_gen = 0;  // bumped whenever a buffer is (re)allocated
     // launch plans chosen by the autotuner, per (toys in a launch, gradient wanted)
@@ -151,6 +152,9 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
 
 using Plan = gsn_ctx::PlanRec;
 
+// per-dataset slot of response parameter i (LY, kB, a, b, c, then the generalized-gamma power)
+int resp_slot(int S, int i) { return i < 5 ? S + i : GSN_SLOT_P(S); }
+
 // Work decomposition of one launch of T toys.  nsplit: fine-column ranges per forward tile
 // (partial mu rows, summed by the deviance); bw_warps x 32: columns per adjoint block;
 // bw_bsplit: bin ranges per adjoint column block; dev_chunks: deviance blocks per toy.
@@ -198,12 +202,14 @@ int finalize(gsn_ctx* c) {
     c->cache_valid = false;
     c->tc_ready = false;
     const bool mixed = c->opt.precision == GSN_MIXED;
-    const bool gamma = c->opt.resolution == GSN_RES_GAMMA;
+    // gamma-family responses (gamma, generalized gamma): support x > 0, the bin at zero and
+    // log-spaced nodes for the lowest bins
+    const bool gamma = c->opt.resolution != GSN_RES_GAUSS;
     const int NSLOT = gsn_n_slots(c->S);
     KArgs& a = c->base;
     a = KArgs{};
     a.D = c->D; a.S = c->S; a.K = c->K; a.P = c->P; a.NSLOT = NSLOT;
-    a.res = gamma ? 1 : 0;
+    a.res = c->opt.resolution;
     a.precision = mixed ? 1 : 0;
     a.cut = c->opt.band_cut;
     a.s0 = c->opt.birks_s0; a.s1 = c->opt.birks_s1;
@@ -251,7 +257,7 @@ int finalize(gsn_ctx* c) {
             if (tb.g_nds[g] >= MAXGDS || c->edges[d0] != c->edges[d]) continue;
             bool same = true;
             for (int i = 0; i < NRESP; ++i)
-                same = same && c->slot_map[d0 * NSLOT + c->S + i] == c->slot_map[d * NSLOT + c->S + i] &&
+                same = same && c->slot_map[d0 * NSLOT + resp_slot(c->S, i)] == c->slot_map[d * NSLOT + resp_slot(c->S, i)] &&
                        c->rscale[d0 * NRESP + i] == c->rscale[d * NRESP + i];
             if (same) gsel = g;
         }
@@ -261,7 +267,7 @@ int finalize(gsn_ctx* c) {
             gsel = c->G++;
             tb.g_nds[gsel] = 0;
             for (int i = 0; i < NRESP; ++i) {
-                tb.g_resp[gsel][i] = c->slot_map[d * NSLOT + c->S + i];
+                tb.g_resp[gsel][i] = c->slot_map[d * NSLOT + resp_slot(c->S, i)];
                 tb.g_rscale[gsel][i] = c->rscale[d * NRESP + i];
             }
         }
@@ -440,6 +446,8 @@ int reserve(gsn_ctx* c, int T, const Plan& p) {
     const int npart = NRESP + MAXGDS * c->S;
     int rc;
     if ((rc = ensure(c, c->colbuf, (size_t)T * c->G * c->K * NFP * rs))) return rc;
+    if (c->opt.resolution == GSN_RES_GGAMMA &&
+        (rc = ensure(c, c->colbuf2, (size_t)T * c->G * c->K * NFG * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->blkbuf, (size_t)T * c->G * nblk * 2 * rs))) return rc;
     if ((rc = ensure(c, c->mubuf, (size_t)T * p.nsplit * c->total_bins * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->wbuf, (size_t)T * c->total_bins * rs))) return rc;
@@ -456,7 +464,7 @@ void fill(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
     a.nsplit = p.nsplit; a.ntile = p.ntile;
     a.bw_warps = p.bw_warps; a.bw_bsplit = p.bw_bsplit; a.nbtask = p.nbtask;
     a.dev_chunks = p.dev_chunks;
-    a.colbuf = c->colbuf.p; a.blkbuf = c->blkbuf.p; a.mubuf = (double*)c->mubuf.p;
+    a.colbuf = c->colbuf.p; a.colbuf2 = (double*)c->colbuf2.p; a.blkbuf = c->blkbuf.p; a.mubuf = (double*)c->mubuf.p;
     a.wbuf = c->wbuf.p; a.partbuf = (double*)c->partbuf.p; a.gdirect = (double*)c->gdirect.p;
     a.devpart = (double*)c->devbuf.p;
 }
@@ -737,7 +745,7 @@ int gsn_default_options(gsn_options* o) {
     return GSN_OK;
 }
 
-int gsn_n_slots(int n_species) { return 3 * n_species + 5; }
+int gsn_n_slots(int n_species) { return 3 * n_species + 6; }
 
 int gsn_create(gsn_ctx** out, const gsn_options* opt) {
     if (!out) return GSN_ERR_ARG;
@@ -746,7 +754,10 @@ int gsn_create(gsn_ctx** out, const gsn_options* opt) {
     if (opt) c->opt = *opt; else gsn_default_options(&c->opt);
     gsn_options& o = c->opt;
     if (o.precision != GSN_FP64 && o.precision != GSN_MIXED) { delete c; return GSN_ERR_ARG; }
-    if (o.resolution != GSN_RES_GAUSS && o.resolution != GSN_RES_GAMMA) { delete c; return GSN_ERR_ARG; }
+    if (o.resolution != GSN_RES_GAUSS && o.resolution != GSN_RES_GAMMA && o.resolution != GSN_RES_GGAMMA) {
+        delete c;
+        return GSN_ERR_ARG;
+    }
     if (!(o.band_cut > 0)) o.band_cut = o.precision == GSN_FP64 ? 34.5 : 20.7;
     if (!(o.birks_s0 > 0)) o.birks_s0 = 1.55;
     if (o.birks_s1 < 0) o.birks_s1 = 0.155;
@@ -774,7 +785,7 @@ void gsn_destroy(gsn_ctx* c) {
     free_owned(c);
     for (Buf* b : {&c->fit_ws, &c->fit_cfg, &c->fit_eval, &c->fit_ist})
         if (b->p) cudaFree(b->p);
-    for (Buf* b : {&c->colbuf, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
+    for (Buf* b : {&c->colbuf, &c->colbuf2, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
                    &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf, &c->s_hi, &c->s_lo,
                    &c->tc_part, &c->tc_err})
         if (b->p) cudaFree(b->p);
@@ -951,6 +962,8 @@ int gsn_set_params(gsn_ctx* c, int n_params, const int* slot_map, int n_pulls, c
         for (int i = 0; i < 5 && smeared; ++i)
             if (sm[d * NS + c->S + i] < 0)
                 return fail(c, GSN_ERR_ARG, "response slots (LY, kB, a, b, c) of datasets with smeared species must be mapped");
+        if (smeared && c->opt.resolution == GSN_RES_GGAMMA && sm[d * NS + GSN_SLOT_P(c->S)] < 0)
+            return fail(c, GSN_ERR_ARG, "the power slot of datasets with smeared species must be mapped (generalized gamma)");
         for (int s = 0; s < c->S; ++s)
             if (c->kind[s] == GSN_ANA_PEAK && c->mask[s * c->D + d] &&
                 (sm[d * NS + GSN_SLOT_M(c->S, s)] < 0 || sm[d * NS + GSN_SLOT_W(c->S, s)] < 0))
@@ -998,11 +1011,15 @@ int gsn_set_dataset_factors(gsn_ctx* c, int n_datasets, int n_species, const dou
         return fail(c, GSN_ERR_STATE, "gsn_set_data and gsn_set_species must come before the dataset factors");
     if (n_datasets != c->D || n_species != c->S)
         return fail(c, GSN_ERR_ARG, "n_datasets / n_species differ from gsn_set_data / gsn_set_species");
+    // the caller's [D][5] multipliers of (LY, kB, a, b, c); the power slot keeps 1
     std::vector<double> rs((size_t)c->D * NRESP, 1.0), rf((size_t)c->D * c->S, 1.0);
     if (resp_scale) {
-        rs.assign(resp_scale, resp_scale + rs.size());
-        for (double v : rs)
-            if (!(v > 0.0) || !std::isfinite(v)) return fail(c, GSN_ERR_ARG, "resp_scale must be finite and > 0");
+        for (int d = 0; d < c->D; ++d)
+            for (int i = 0; i < 5; ++i) {
+                const double v = resp_scale[(size_t)d * 5 + i];
+                if (!(v > 0.0) || !std::isfinite(v)) return fail(c, GSN_ERR_ARG, "resp_scale must be finite and > 0");
+                rs[(size_t)d * NRESP + i] = v;
+            }
     }
     if (rate_factor) {
         rf.assign(rate_factor, rate_factor + rf.size());
@@ -1092,7 +1109,7 @@ static int compute_species(gsn_ctx* c, const double* params_dev) {
     a.sp_first = 0; a.sp_count = c->S;
     if (!a.response) return GSN_OK;  // templates and peaks only: no per-species response shapes
     if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
-    if (c->opt.precision == GSN_MIXED) {
+    if (c->opt.precision == GSN_MIXED && c->opt.resolution != GSN_RES_GGAMMA) {
         if ((rc = prepare_tensor_core(c))) return rc;
         const int tiles = (c->Jmax + 127) / 128 * c->G * ((c->S + 15) / 16);
         a.tc_nsplit = std::max(1, std::min(64, (3 * c->nsm + tiles - 1) / tiles));
@@ -1126,7 +1143,7 @@ static int species_status(gsn_ctx* c) {
 static int species_cached(gsn_ctx* c, const double* params, bool& hit) {
     std::vector<double> key;
     for (int g = 0; g < c->G; ++g)
-        for (int i = 0; i < NRESP; ++i) key.push_back(params[c->tab.g_resp[g][i]]);
+        for (int i = 0; i < NRESP; ++i) key.push_back(c->tab.g_resp[g][i] >= 0 ? params[c->tab.g_resp[g][i]] : 0.0);
     hit = c->cache_valid && key.size() == c->cache_key.size() &&
           std::memcmp(key.data(), c->cache_key.data(), key.size() * sizeof(double)) == 0;
     if (hit) return GSN_OK;
@@ -1362,16 +1379,17 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     KArgs a = c->base;
     const Plan p = make_plan(c, 1);
     const size_t rs = c->opt.precision == GSN_MIXED ? sizeof(float) : sizeof(double);
-    const size_t sizes[7] = {
+    const size_t sizes[8] = {
         (size_t)c->G * c->K * NFP * rs,                         // column records
         (size_t)c->G * a.nblk * 2 * rs,                         // band summaries
         (size_t)p.nsplit * c->total_bins * sizeof(double),      // partial mu
         (size_t)c->total_bins * rs,                             // w
         (size_t)c->G * p.nbtask * a.NPART * sizeof(double),     // partial gradients
         (size_t)c->P * sizeof(double),                          // direct gradient terms
-        (size_t)p.dev_chunks * (2 + c->base.ntpl) * sizeof(double)};  // deviance and template partials
-    size_t off[7], total = 0;
-    for (int i = 0; i < 7; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
+        (size_t)p.dev_chunks * (2 + c->base.ntpl) * sizeof(double),   // deviance and template partials
+        c->opt.resolution == GSN_RES_GGAMMA ? (size_t)c->G * c->K * NFG * sizeof(double) : 0};  // adjoint coefficients
+    size_t off[8], total = 0;
+    for (int i = 0; i < 8; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
     if (total > GSN_NOALLOC_SCRATCH_BYTES)
         return fail(c, GSN_ERR_ARG, "this problem needs " + std::to_string(total) + " bytes of scratch; the "
                     "no-allocation entry point holds " + std::to_string((size_t)GSN_NOALLOC_SCRATCH_BYTES));
@@ -1381,6 +1399,7 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     a.colbuf = base + off[0]; a.blkbuf = base + off[1]; a.mubuf = (double*)(base + off[2]);
     a.wbuf = base + off[3]; a.partbuf = (double*)(base + off[4]); a.gdirect = (double*)(base + off[5]);
     a.dev_chunks = p.dev_chunks; a.devpart = (double*)(base + off[6]);
+    a.colbuf2 = (double*)(base + off[7]);
     a.params = params_dev; a.params_stride = c->P;
     a.counts_stride = 0; a.win_stride = 0;
     a.nll = nll_dev; a.grad = grad_dev; a.status = status_dev;

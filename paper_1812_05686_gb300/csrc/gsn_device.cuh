@@ -204,6 +204,20 @@ template <class R> DEV void gamma_bin_zero(R d, R s, R x1, R& P, R& Pd, R& Ps2) 
 }
 
 
+// compensated warp sum of (s, c) pairs; result in every lane
+DEV float warp_sum_comp(float s, float c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, o);
+        const float co = __shfl_xor_sync(0xffffffffu, c, o);
+        const float tsum = s + so;
+        const float bp = tsum - s;
+        c = c + co + ((s - (tsum - bp)) + (so - bp));
+        s = tsum;
+    }
+    return s + c;
+}
+
 // compensated (TwoSum) accumulation of x into (s, c)
 DEV void two_sum_acc(float& s, float& c, float x) {
     const float t = s + x;

@@ -1,0 +1,308 @@
+// Generalized-gamma response with a free power p (Stacy's density, the line shape of the
+// generalized-gamma response cited in section 2.3):
+//   f(x; d, s, p) = p x^(d-1) exp(-(x/s)^p) / (s^d Gamma(d/p)),  x > 0,
+// CDF P(d/p, (x/s)^p).  Every column's (d, s) follow from its mean mu and variance var by moment
+// matching for the fit parameter p:
+//   mu = s Gamma(x + a) / Gamma(x),  mu^2 + var = s^2 Gamma(x + 2a) / Gamma(x),  x = d/p, a = 1/p.
+// Eliminating s leaves H(x) = lnGamma(x+2a) + lnGamma(x) - 2 lnGamma(x+a) = ln(1 + var/mu^2).
+// H and the other log-gamma / digamma differences are O(1/x) while the log-gammas are O(x ln x),
+// so they come from Stirling's series (Abramowitz & Stegun 6.1.40, 6.3.18) with the leading terms
+// combined analytically, after the recurrences lnGamma(z+1) = lnGamma(z) + ln z and
+// psi(z+1) = psi(z) + 1/z have moved the argument to >= 10.  All column work is FP64.
+#pragma once
+#include "gsn_device.cuh"
+
+namespace gsn {
+
+constexpr double GG_XSTIR = 10.0;
+
+// lnGamma(z) - [(z - 1/2) ln z - z + ln(2 pi)/2] for z >= 10: sum_n B_2n / (2n (2n-1) z^(2n-1)), n <= 8
+DEV double gg_lgamma_tail(double z) {
+    const double iz = 1.0 / z, v = iz * iz;
+    double s = fma(v, -3617.0 / 122400, 1.0 / 156);
+    s = fma(s, v, -691.0 / 360360);
+    s = fma(s, v, 1.0 / 1188);
+    s = fma(s, v, -1.0 / 1680);
+    s = fma(s, v, 1.0 / 1260);
+    s = fma(s, v, -1.0 / 360);
+    s = fma(s, v, 1.0 / 12);
+    return s * iz;
+}
+// psi(z) - [ln z - 1/(2z)] for z >= 10: -sum_n B_2n / (2n z^2n), n <= 8
+DEV double gg_digamma_tail(double z) {
+    const double iz = 1.0 / z, v = iz * iz;
+    double s = fma(v, -3617.0 / 8160, 1.0 / 12);
+    s = fma(s, v, -691.0 / 32760);
+    s = fma(s, v, 1.0 / 132);
+    s = fma(s, v, -1.0 / 240);
+    s = fma(s, v, 1.0 / 252);
+    s = fma(s, v, -1.0 / 120);
+    s = fma(s, v, 1.0 / 12);
+    return -s * v;
+}
+DEV int gg_shift(double x) { return x >= GG_XSTIR ? 0 : (int)ceil(GG_XSTIR - x); }
+
+// lnGamma(x + c) - lnGamma(x), x > 0, c >= 0
+DEV double gg_lgamma_diff(double x, double c) {
+    const int m = gg_shift(x);
+    const double xm = x + m;
+    double r = fma(xm - 0.5, log1p(c / xm), c * log(xm + c) - c) + (gg_lgamma_tail(xm + c) - gg_lgamma_tail(xm));
+    for (int i = 0; i < m; ++i) r -= log1p(c / (x + i));
+    return r;
+}
+// psi(x + c) - psi(x)
+DEV double gg_digamma_diff(double x, double c) {
+    const int m = gg_shift(x);
+    const double xm = x + m;
+    double r = log1p(c / xm) + c / (2.0 * xm * (xm + c)) + (gg_digamma_tail(xm + c) - gg_digamma_tail(xm));
+    for (int i = 0; i < m; ++i) r += c / ((x + i) * (x + c + i));
+    return r;
+}
+// H(x) = ln[Gamma(x + 2a) Gamma(x) / Gamma(x + a)^2]
+DEV double gg_H(double x, double a) {
+    const int m = gg_shift(x);
+    const double xm = x + m;
+    const double e = a / xm, q = e / (1.0 + e);
+    double r = fma(xm - 0.5, log1p(-q * q), 2.0 * a * log1p(a / (xm + a))) +
+               ((gg_lgamma_tail(xm + 2.0 * a) - 2.0 * gg_lgamma_tail(xm + a)) + gg_lgamma_tail(xm));
+    for (int i = 0; i < m; ++i) {
+        const double xi = x + i, ei = a / xi;
+        if (ei < 0.5) { const double qi = ei / (1.0 + ei); r -= log1p(-qi * qi); }
+        else r -= log(xi) + log(xi + 2.0 * a) - 2.0 * log(xi + a);
+    }
+    return r;
+}
+// dH/dx = psi(x + 2a) - 2 psi(x + a) + psi(x)
+DEV double gg_Hx(double x, double a) {
+    const int m = gg_shift(x);
+    const double xm = x + m;
+    const double q = a / (xm + a);
+    double r = log1p(-q * q) - a * a / (xm * (xm + a) * (xm + 2.0 * a)) +
+               ((gg_digamma_tail(xm + 2.0 * a) - 2.0 * gg_digamma_tail(xm + a)) + gg_digamma_tail(xm));
+    for (int i = 0; i < m; ++i) {
+        const double xi = x + i;
+        r -= 2.0 * a * a / (xi * (xi + a) * (xi + 2.0 * a));
+    }
+    return r;
+}
+
+// x = d/p solving H(x) = r = ln(1 + var/mu^2): Newton's method on ln H against ln x from the
+// two-term large-x inversion x0 = a^2/r - (a - 1/2).  Returns a negative value if it fails.
+DEV double gg_solve_shape(double r, double a) {
+    double x = a * a / r - (a - 0.5);
+    if (!(x > 0.5 * a * a / r)) x = a * a / r;
+    double u = log(x);
+    for (int it = 0; it < 60; ++it) {
+        x = exp(u);
+        const double h = gg_H(x, a);
+        const double g = log(h / r);
+        const double step = fmin(5.0, fmax(-5.0, -g * h / (x * gg_Hx(x, a))));
+        u += step;
+        if (fabs(step) < 1e-14) return exp(u);
+    }
+    return -1.0;
+}
+
+// log f(x)/f(mu) for L = ln(x/mu): E(L) = k1 L - A (e^(pL) - 1 - pL), and its L-derivative
+DEV double gg_logratio(double L, double k1, double A, double p) { return k1 * L - A * (expm1(p * L) - p * L); }
+DEV double gg_logratio_d(double L, double k1, double A, double p) { return k1 - A * p * expm1(p * L); }
+
+// lower regularised incomplete gamma P(a, y) by its power series, with dP/da and y^a e^-y / Gamma(a)
+DEV void gg_inc_gamma(double a, double y, double& P, double& Pa, double& py) {
+    const double ly = log(y);
+    const double pref = exp(a * ly - y - lgamma(a + 1.0));
+    double term = 1.0, sum = 1.0, H = 0.0, hsum = 0.0;
+    for (int n = 1; n < 200; ++n) {
+        term *= y / (a + n);
+        H += 1.0 / (a + n);
+        sum += term;
+        hsum += term * H;
+        if (term < 1e-18 * sum) break;
+    }
+    P = pref * sum;
+    Pa = P * (ly - digamma_d(a + 1.0)) - pref * hsum;
+    py = exp(a * ly - y - lgamma(a));
+}
+
+// Column prologue of the generalized gamma (FP64 for both precisions).  Fills the record fields
+// that depend on the response (everything but TN), the band [xmin, xmax] and the adjoint record
+// g (NFG values); mu, var: the column's mean and variance, p the power, deq = d E_q / d kB.
+// Returns the normalisation N_k that multiplies the T_dk (mixed: the density at the mean over the
+// SFU bias of the exponentials; FP64: 1).
+template <class R>
+DEV double gg_column(double mu, double var, double p, double cut, double x1, bool zero_bin, bool mixed,
+                     R* f, double* gco, R& xmin, R& xmax) {
+    const double a = 1.0 / p;
+    const double r = log1p(var / (mu * mu));
+    const double xs = gg_solve_shape(r, a);          // d/p
+    const double d = p * xs;
+    const double ls = gg_lgamma_diff(xs, a);          // ln(mu/s)
+    const double lns = log(mu) - ls;                  // ln s
+    const double A = exp(p * ls);                     // (mu/s)^p
+    const double k1 = (d - 1.0) - p * A;
+    const double psi = digamma_d(xs);
+    const double lgx = lgamma(xs);
+    // density at the mean: ln f(mu) = ln p - ln mu + d ln(mu/s) - A - lnGamma(d/p)
+    const double lfm = log(p) - log(mu) + d * ls - A - lgx;
+    double Nk = 1.0;
+    if (mixed) {
+        Nk = exp(lfm) / (1.0 + EX2_MEAN_REL_ERR);
+        f[F_A] = (R)(1.0 / mu);
+        f[F_B] = (R)(1.4426950408889634 * A);
+        f[F_C] = (R)(1.4426950408889634 * k1);
+    } else {
+        f[F_A] = (R)(log(p) - d * lns - lgx);
+        f[F_B] = (R)(d - 1.0);
+        f[F_C] = (R)lns;
+    }
+    f[F_KAPPA] = (R)p;
+    // band: E(L) is concave in L (E'' = -A p^2 e^(pL)); Newton steps from outer bounds stay outside
+    {
+        const double Ap2 = A * p * p;
+        // E <= k1 L - A p^2 L^2 / 2 for L >= 0; columns of tiny shape reach far out (kept finite)
+        double L = fmin((k1 + sqrt(k1 * k1 + 2.0 * Ap2 * cut)) / Ap2, 600.0 / p);
+        for (int it = 0; it < 4; ++it) {
+            const double Ln = L - (gg_logratio(L, k1, A, p) + cut) / gg_logratio_d(L, k1, A, p);
+            if (isfinite(Ln) && Ln > 0.0) L = fmin(Ln, 600.0 / p);
+        }
+        xmax = (R)fmin(mu * exp(L), 1e30);
+        xmin = 0;
+        if (d > 1.0) {
+            double Lo = -sqrt(2.0 * cut / Ap2);
+            int grow = 0;
+            while (gg_logratio(Lo, k1, A, p) > -cut && grow < 60) { Lo = 1.5 * Lo - 0.5; ++grow; }
+            if (grow < 60 && Lo > -700.0) {
+                for (int it = 0; it < 4; ++it) {
+                    const double Ln = Lo - (gg_logratio(Lo, k1, A, p) + cut) / gg_logratio_d(Lo, k1, A, p);
+                    if (isfinite(Ln) && Ln < 0.0) Lo = fmax(Lo, Ln);
+                }
+                xmin = (R)(mu * exp(Lo));
+            }
+        }
+    }
+    // bin at zero: P(d/p, (x1/s)^p) and its derivatives at fixed (d, s, p)
+    double P0 = 0.0, P0d = 0.0, P0s = 0.0, P0p = 0.0;
+    if (zero_bin && (double)xmin <= x1) {
+        const double lxs = log(x1) - lns;
+        const double y = exp(p * lxs);
+        double P, Pa, py;
+        gg_inc_gamma(xs, y, P, Pa, py);
+        P0 = P; P0d = Pa / p; P0s = -p * py; P0p = -(d / (p * p)) * Pa + py * lxs;
+    }
+    f[F_P0] = (R)(P0 / Nk);
+    // moment matching H(x, a) = ln rho, ln s = ln mu - G(x, a): implicit derivatives of x and u = ln s
+    const double Hx = gg_Hx(xs, a);
+    const double da = gg_digamma_diff(xs, a), d2a = gg_digamma_diff(xs, 2.0 * a);
+    const double Ha = 2.0 * (d2a - da);
+    const double Gx = da, Ga = psi + da;              // psi(x + a) = psi(x) + [psi(x + a) - psi(x)]
+    const double r_mu = -2.0 * var / (mu * (mu * mu + var)), r_var = 1.0 / (mu * mu + var);
+    const double x_mu = r_mu / Hx, x_var = r_var / Hx, x_p = Ha / (p * p * Hx);
+    const double J_dmu = p * x_mu, J_dvar = p * x_var, J_dp = xs + p * x_p;
+    const double J_umu = 1.0 / mu - Gx * x_mu, J_uvar = -Gx * x_var, J_up = -Gx * x_p + Ga / (p * p);
+    // node-sum combinations (see the record comment): g_d = U1 + m0 Ur, s g_s = m1 U2 + m2 Ur,
+    // g_p = m3 Ur + m4 U3 + m5 U1 + m6 (s g_s of the nodes)
+    double m0, m1, m2, m3, m4, m5, m6;
+    if (mixed) {
+        const double cd = ls - psi / p;
+        m0 = cd; m1 = p * A; m2 = -(1.0 + k1);
+        m3 = 1.0 / p - (d / p) * cd; m4 = -A; m5 = -A; m6 = -ls / p;
+    } else {
+        m0 = -psi / p; m1 = p; m2 = -d;
+        m3 = 1.0 / p + d * psi / (p * p); m4 = -1.0; m5 = 0.0; m6 = 0.0;
+    }
+    const double gd[5] = {m0, 1.0, 0.0, 0.0, P0d / Nk};
+    const double gs[5] = {m2, 0.0, m1, 0.0, P0s / Nk};
+    const double gp[5] = {m3 + m6 * m2, m5, m6 * m1, m4, P0p / Nk};
+    double row[3][5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        row[0][i] = J_dmu * gd[i] + J_umu * gs[i];
+        row[1][i] = J_dvar * gd[i] + J_uvar * gs[i];
+        row[2][i] = gp[i] + J_dp * gd[i] + J_up * gs[i];
+    }
+    if (mixed) {
+        // the mixed adjoint accumulates f Q with Q = E1 - pL (relative precision) instead of f E1:
+        // the first-order parts of the L and E1 sums, which cancel in the variance and power
+        // derivatives, then combine here in FP64
+        for (int r3 = 0; r3 < 3; ++r3) row[r3][1] += p * row[r3][2];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        gco[FG_MU + i] = row[0][i];
+        gco[FG_VAR + i] = row[1][i];
+        gco[FG_P + i] = row[2][i];
+    }
+    gco[15] = 0;
+    return Nk;
+}
+
+// ---- FP32 helpers of the mixed path ----
+// Q2(q) = e^q - 1 - q with relative precision, and E1 = e^q - 1.  The series
+// Q2(h) = h^2 (1/2 + h/6 + ... + h^8/10!) has relative truncation error below 2 |h|^9 / 11! (1e-10
+// at |h| = 1/2).  |q| <= 1/2 (the bulk of a band): the series at q.  |q| <= 2: the series at
+// h = q/4 and two doublings Q2(2h) = E1(h)^2 + 2 Q2(h), E1(2h) = E1(h)^2 + 2 E1(h), which add
+// non-negative terms to Q2.  Beyond, e^q - 1 - q loses at most a factor ~1.7 to cancellation.
+DEV float gg_q2_series(float h) {
+    float s = fmaf(h, 1.0f / 3628800, 1.0f / 362880);
+    s = fmaf(s, h, 1.0f / 40320);
+    s = fmaf(s, h, 1.0f / 5040);
+    s = fmaf(s, h, 1.0f / 720);
+    s = fmaf(s, h, 1.0f / 120);
+    s = fmaf(s, h, 1.0f / 24);
+    s = fmaf(s, h, 1.0f / 6);
+    s = fmaf(s, h, 0.5f);
+    return (h * h) * s;
+}
+DEV float gg_q2f(float q, float& e1) {
+    const float aq = fabsf(q);
+    if (aq <= 0.5f) {
+        const float Q = gg_q2_series(q);
+        e1 = q + Q;
+        return Q;
+    }
+    if (aq <= 2.0f) {
+        const float h = 0.25f * q;
+        float Q = gg_q2_series(h);
+        float E = h + Q;
+        Q = fmaf(E, E, 2.0f * Q); E = fmaf(E, E, 2.0f * E);
+        Q = fmaf(E, E, 2.0f * Q); E = fmaf(E, E, 2.0f * E);
+        e1 = E;
+        return Q;
+    }
+    const float e = ex2f(mul_l2e(q)) - 1.0f;
+    e1 = e;
+    return e - q;
+}
+
+// mixed bin value of a generalized-gamma column relative to its density at the mean:
+// sum_n w_n exp(E(L_n)), L_n = ln(x_c/mu) + ln(x_n/x_c)
+template <int NG>
+DEV float gg_bin_value_f(const float* c, float xc, const float* lam, const float* wt) {
+    const float Dx = (xc - c[F_MUH]) - c[F_MUL];
+    float Lc;
+    log1pmx2_f(Dx * c[F_A], Lc);
+    const float p = c[F_KAPPA], Ap = c[F_B], Kp = c[F_C];
+    float rho = 0.0f;
+#pragma unroll
+    for (int n = 0; n < NG; ++n) {
+        const float L = Lc + lam[n];
+        float e1;
+        const float Q = gg_q2f(p * L, e1);
+        rho = fmaf(wt[n], ex2f(fmaf(-Ap, Q, Kp * L)), rho);   // the large term A Q rounded once
+    }
+    return rho;
+}
+
+// FP64 bin value: sum_n w_n exp(ln p - d ln s - lnGamma(d/p) + (d-1) ln x_n - (x_n/s)^p)
+template <int NG>
+DEV double gg_bin_value_d(const double* c, const double* lx, const double* wt) {
+    double rho = 0.0;
+#pragma unroll
+    for (int n = 0; n < NG; ++n) {
+        const double y = exp(c[F_KAPPA] * (lx[n] - c[F_C]));
+        rho = fma(wt[n], exp(fma(c[F_B], lx[n], c[F_A]) - y), rho);
+    }
+    return rho;
+}
+
+}  // namespace gsn

@@ -29,15 +29,29 @@ constexpr int NFP = 16;      // fields per column record
 //  fp64 gamma  : MUH = mu, A = -d ln s - lgamma(d), B = d-1, C = 1/s,
 //                KAPPA = ln s + psi(d), N = 1
 //  fp64 gauss  : MUH = mu, A = 1/sigma, N = 1
+//  mixed ggamma: MUH/MUL, A = 1/mu, B = L2E A_p, C = L2E kappa_1, KAPPA = p,
+//                N = density at the mean, with A_p = (mu/s)^p, kappa_1 = d - 1 - p A_p
+//                (log f(x)/f(mu) = kappa_1 L - A_p (e^(pL) - 1 - pL), L = ln(x/mu))
+//  fp64 ggamma : MUH = mu, A = ln p - d ln s - lgamma(d/p), B = d-1, C = ln s,
+//                KAPPA = p, N = 1
 //  all         : DEQ = d E_q / d kB, XMIN/XMAX = band in p.e., P0 = bin-at-zero
-//                content / N; P0D/P0S its derivatives: fp64 dP/dd and s^2 dP/ds,
+//                content / N; P0D/P0S its derivatives (gamma): fp64 dP/dd and s^2 dP/ds,
 //                mixed (mu/d) dP/dmu|var / N and s^2 dP/dvar|mu / N;
 //                TN0.. = N_k * T_dk of each dataset of the group
 enum { F_MUH = 0, F_MUL, F_A, F_B, F_C, F_N, F_KAPPA, F_DEQ, F_XMIN, F_XMAX,
        F_P0, F_P0D, F_P0S, F_TN0 };
 static_assert(F_TN0 + MAXGDS <= NFP, "column record too small");
 
-constexpr int NRESP = 5;  // LY, kB, a, b, c
+// Adjoint coefficients of a generalized-gamma column (second record, NFG doubles): the adjoint
+// accumulates over the band U = (sum W rho, sum W S1, sum W S2, sum W S3, W at the bin at zero),
+// with the node sums S1..S3 of the precision (fp64: f l, f y, f y l with l = ln(x/s), y = (x/s)^p;
+// mixed: f L, f Q, f E1 L with L = ln(x/mu), E1 = e^(pL) - 1, Q = E1 - pL), and maps them to the derivatives
+// of the NLL with respect to the column's mean, variance and the power: rows G_MU, G_VAR, G_P of
+// five coefficients each.
+constexpr int NFG = 16;
+enum { FG_MU = 0, FG_VAR = 5, FG_P = 10 };
+
+constexpr int NRESP = 6;  // LY, kB, a, b, c, p (the power of the generalized gamma)
 
 // Problem tables, in device memory (uploaded once per problem, read by every kernel).
 struct Tables {
@@ -69,7 +83,7 @@ struct FastTables {
 struct KArgs {
     // problem
     int T, D, S, K, P, NSLOT, G, total_bins, nsplit, n_pulls;
-    int res;          // 0 gauss, 1 gamma
+    int res;          // 0 gauss, 1 gamma, 2 generalized gamma with a free power
     int precision;    // 0 fp64, 1 mixed
     double cut;       // band cut on the log-density
     double s0, s1;    // stopping power model
@@ -107,6 +121,7 @@ struct KArgs {
     const int* win;        long long win_stride;      // [T][D][2]
     // scratch
     void* colbuf;          // [T][G][K][NFP] of Real
+    double* colbuf2;       // [T][G][K][NFG]: adjoint coefficients (generalized gamma only)
     void* blkbuf;          // [T][G][nblk][2] of Real: min xmin, max xmax
     double* mubuf;         // [T][nsplit][total_bins]
     void* wbuf;            // [T][total_bins] of Real

@@ -20,6 +20,7 @@
 // column means, FP32 partial sums flushed to FP64 per column block, FP64
 // deviance and reductions.  FP64: everything in double.
 #include "gsn_device.cuh"
+#include "gsn_ggamma.cuh"
 
 namespace gsn {
 
@@ -36,7 +37,10 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
     __shared__ float sdf[8];      // per-toy double-float constants (mixed)
     __shared__ R sred[2][COLBLK / 32];
     const double* prm = a.params + (long long)t * a.params_stride;
-    if (threadIdx.x < NRESP) sres[threadIdx.x] = prm[tb_g_resp<FAST>(a, g, threadIdx.x)] * tb_g_rscale<FAST>(a, g, threadIdx.x);
+    if (threadIdx.x < NRESP) {
+        const int q = tb_g_resp<FAST>(a, g, threadIdx.x);  // the power slot is unmapped unless RES == 2
+        sres[threadIdx.x] = q >= 0 ? prm[q] * tb_g_rscale<FAST>(a, g, threadIdx.x) : 1.0;
+    }
     for (int i = threadIdx.x; i < MAXGDS * a.S; i += blockDim.x) {
         const int dd = i / a.S, s = i % a.S;
         double v = 0.0;
@@ -71,6 +75,30 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
         R f[NFP];
 #pragma unroll
         for (int i = 0; i < NFP; ++i) f[i] = 0;
+        R Nk = 1;
+        if constexpr (RES == 2) {
+            // generalized gamma: mean, variance and everything of the column in FP64
+            const double E = a.E[k];
+            double Eq = E / alpha, L = 0.0, y = 0.0;
+            if (beta > 0) {
+                y = alpha * E / beta;
+                L = log1p(y);
+                Eq = y < 1.0 ? -(beta / (alpha * alpha)) * (L - y) : E / alpha - (beta / (alpha * alpha)) * L;
+            }
+            const double mud = LY * Eq;
+            const double vard = fma(mud, fma(rc, mud, rb), ra);
+            const double D = L - y, r1 = y / (1.0 + y);
+            f[F_DEQ] = (R)(beta > 0 ? (a.s0 * (beta / alpha) * (2.0 * D + y * r1) - a.s1 * (D + y * r1)) / (alpha * alpha) : NAN);
+            f[F_MUH] = (R)mud;
+            if constexpr (sizeof(R) == 4) f[F_MUL] = (R)(mud - (double)(R)mud);
+            double gco[NFG];
+            const double x1 = a.edges[tb_g_edge_off<FAST>(a, g) + 1];
+            Nk = (R)gg_column<R>(mud, vard, sres[5], a.cut, x1, tb_g_zero<FAST>(a, g) != 0, sizeof(R) == 4, f, gco,
+                                 xmin, xmax);
+            double* g2 = a.colbuf2 + (((long long)t * a.G + g) * a.K + k) * NFG;
+#pragma unroll
+            for (int i = 0; i < NFG; ++i) g2[i] = gco[i];
+        } else {
         R mu, var, deq;
         if constexpr (sizeof(R) == 4) {
             // E_q = E/alpha - (beta/alpha^2) ln(1 + alpha E / beta), mean in double-float
@@ -111,7 +139,6 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
         // in FP64 and rounded once: FP32 copies of a, b, c would scale every column's variance alike
         var = (R)fma((double)mu, fma(rc, (double)mu, rb), ra);
         f[F_DEQ] = deq;
-        R Nk = 1;
         if constexpr (RES == 0) {
             const R sig = sqrt(var), isg = R(1) / sig;
             f[F_A] = isg;
@@ -192,6 +219,7 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
                 }
             }
         }
+        }  // RES 0 / 1
         f[F_N] = Nk;
         f[F_XMIN] = xmin;
         f[F_XMAX] = xmax;
@@ -254,7 +282,8 @@ DEV int forward_loop(const KArgs& a, int t, int g, int split, float xlo_w, float
     }
     for (int b = k_beg / COLBLK; b * COLBLK < k_end; ++b) {
         if (blk[2 * b + 1] < (R)xlo_w || blk[2 * b] > (R)xhi_w) continue;
-        R acc[MAXGDS] = {0, 0, 0};
+        // FP32: partial sums of up to 32 columns folded into compensated (s, cs) pairs
+        R acc[MAXGDS] = {0, 0, 0}, sacc[MAXGDS] = {0, 0, 0}, cacc[MAXGDS] = {0, 0, 0};
         const int kb = max(b * COLBLK, k_beg), ke = min((b + 1) * COLBLK, k_end);
         for (int k = kb; k < ke; ++k) {
             const R* c = colrec<R>(a, t, g, k);
@@ -262,18 +291,33 @@ DEV int forward_loop(const KArgs& a, int t, int g, int split, float xlo_w, float
             ++ncol;
             R v;
             if constexpr (sizeof(R) == 4) {
-                v = bin_value_f<RES, NG>(c, xc, del, lam, wt);
-                if (RES == 1 && is_zero) v = valid ? c[F_P0] : 0.0f;
+                if constexpr (RES == 2) v = gg_bin_value_f<NG>(c, xc, lam, wt);
+                else v = bin_value_f<RES, NG>(c, xc, del, lam, wt);
+                if (RES >= 1 && is_zero) v = valid ? c[F_P0] : 0.0f;
             } else {
-                v = bin_value_gamma_d<NG>(c, del, lam, wt);
+                if constexpr (RES == 2) v = gg_bin_value_d<NG>(c, lam, wt);
+                else v = bin_value_gamma_d<NG>(c, del, lam, wt);
                 if (is_zero) v = valid ? c[F_P0] : 0.0;
             }
 #pragma unroll
             for (int dd = 0; dd < MAXGDS; ++dd)
                 if (dd < nds) acc[dd] = fma(v, c[F_TN0 + dd], acc[dd]);
+            if constexpr (sizeof(R) == 4) {
+                if ((k & 31) == 31) {
+#pragma unroll
+                    for (int dd = 0; dd < MAXGDS; ++dd) { two_sum_acc(sacc[dd], cacc[dd], acc[dd]); acc[dd] = 0; }
+                }
+            }
         }
 #pragma unroll
-        for (int dd = 0; dd < MAXGDS; ++dd) accd[dd] += (double)acc[dd];
+        for (int dd = 0; dd < MAXGDS; ++dd) {
+            if constexpr (sizeof(R) == 4) {
+                two_sum_acc(sacc[dd], cacc[dd], acc[dd]);
+                accd[dd] += (double)sacc[dd] + (double)cacc[dd];
+            } else {
+                accd[dd] += (double)acc[dd];
+            }
+        }
     }
     return ncol;
 }
@@ -651,8 +695,64 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
         wv[dd] = reinterpret_cast<const R*>(a.wbuf) + (long long)t * a.total_bins + tb_ds_off(a, tb_g_ds(a, g, dd < nds ? dd : 0));
     R U0[MAXGDS] = {0, 0, 0};
     R U1 = 0, U2 = 0;
+    // generalized gamma: W-weighted node sums (rho, S1, S2, S3; compensated in FP32) and the W of
+    // the bin at zero, mapped to the mean / variance / power derivatives by the adjoint record
+    R Gs[4] = {0, 0, 0, 0}, Gc[4] = {0, 0, 0, 0}, Z0 = 0, U0c[MAXGDS] = {0, 0, 0};
     const int nbase = tb_g_node_off(a, g);
-    if constexpr (sizeof(R) == 8 && RES == 0) {
+    if constexpr (RES == 2) {
+        const R p = c[F_KAPPA];
+        for (int j = ja; j <= jb; ++j) {
+            R wj[MAXGDS];
+            R Wj = 0;
+#pragma unroll
+            for (int dd = 0; dd < MAXGDS; ++dd) {
+                wj[dd] = dd < nds ? wv[dd][j] : R(0);
+                Wj = fma(wj[dd], c[F_TN0 + dd], Wj);
+            }
+            const unsigned char cls = a.bclass[nbase + j];
+            R rho = 0;
+            if (cls == BIN_ZERO) {
+                rho = c[F_P0];
+                Z0 += Wj;
+            } else {
+                R s1 = 0, s2 = 0, s3 = 0;
+                if constexpr (sizeof(R) == 4) {
+                    const float* nd = a.ntab_f + (long long)(nbase + j) * 3 * NGM_F;
+                    const float Dx = (a.xc_f[nbase + j] - c[F_MUH]) - c[F_MUL];
+                    float Lc;
+                    log1pmx2_f(Dx * c[F_A], Lc);
+                    const int NG = cls == BIN_LOG ? NG_LOG_F : NG_LIN_F;
+                    for (int n = 0; n < NG; ++n) {
+                        const float L = Lc + nd[NGM_F + n];
+                        float e1;
+                        const float Q = gg_q2f(p * L, e1);
+                        const float fw = nd[2 * NGM_F + n] * ex2f(fmaf(-c[F_B], Q, c[F_C] * L));
+                        rho += fw; s1 = fmaf(fw, L, s1); s2 = fmaf(fw, Q, s2); s3 = fmaf(fw * e1, L, s3);
+                    }
+                } else {
+                    const double* nd = a.ntab_d + (long long)(nbase + j) * 3 * NGM_D;
+                    const int NG = cls == BIN_LOG ? NG_LOG_D : NG_LIN_D;
+                    for (int n = 0; n < NG; ++n) {
+                        const double l = nd[NGM_D + n] - c[F_C];   // ln(x/s)
+                        const double y = exp(p * l);
+                        const double fw = nd[2 * NGM_D + n] * exp(fma(c[F_B], nd[NGM_D + n], c[F_A]) - y);
+                        rho += fw; s1 = fma(fw, l, s1); s2 = fma(fw, y, s2); s3 = fma(fw * y, l, s3);
+                    }
+                }
+                const R q[4] = {Wj * rho, Wj * s1, Wj * s2, Wj * s3};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if constexpr (sizeof(R) == 4) two_sum_acc(Gs[i], Gc[i], q[i]);
+                    else Gs[i] += q[i];
+                }
+            }
+#pragma unroll
+            for (int dd = 0; dd < MAXGDS; ++dd) {
+                if constexpr (sizeof(R) == 4) two_sum_acc(U0[dd], U0c[dd], wj[dd] * rho);
+                else U0[dd] = fma(wj[dd], rho, U0[dd]);
+            }
+        }
+    } else if constexpr (sizeof(R) == 8 && RES == 0) {
         // exact Gaussian bin integrals from the edges, derivatives from the edge densities
         const double mu = c[F_MUH], isg = c[F_A];
         double zp = 0, qp = 0, pp = 0;
@@ -737,11 +837,25 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     }
     count_work(a, K_BACKWARD, kval, (long long)(jb - ja + 1));
     // chain rule per column
-    R r[NRESP] = {0, 0, 0, 0, 0};
+    R r[NRESP] = {};
     if (kval) {
         const R mu = sizeof(R) == 4 ? c[F_MUH] + c[F_MUL] : c[F_MUH];
         R g_mu, g_var;
-        if constexpr (RES == 0) {
+        if constexpr (RES == 2) {
+            // FP64 combination of the (compensated) sums with the FP64 coefficients
+            const double* g2 = a.colbuf2 + (((long long)t * a.G + g) * a.K + k) * NFG;
+            const double U[5] = {(double)Gs[0] + (double)Gc[0], (double)Gs[1] + (double)Gc[1],
+                                 (double)Gs[2] + (double)Gc[2], (double)Gs[3] + (double)Gc[3], (double)Z0};
+            double gm = 0.0, gv = 0.0, gp = 0.0;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                gm = fma(g2[FG_MU + i], U[i], gm);
+                gv = fma(g2[FG_VAR + i], U[i], gv);
+                gp = fma(g2[FG_P + i], U[i], gp);
+            }
+            g_mu = (R)gm; g_var = (R)gv;
+            r[5] = (R)gp;
+        } else if constexpr (RES == 0) {
             g_mu = U1 * c[F_A];
             g_var = R(0.5) * U2 * c[F_A] * c[F_A];
         } else {
@@ -760,12 +874,15 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
         r[3] = g_var * mu;
         r[4] = g_var * mu * mu;
     }
+    // per-column terms of opposite signs cancel in these sums: compensated in FP32
 #pragma unroll
     for (int i = 0; i < NRESP; ++i) {
-        const R v = warp_sum<R>(r[i]);
+        R v;
+        if constexpr (sizeof(R) == 4) v = warp_sum_comp(r[i], 0.f);
+        else v = warp_sum<R>(r[i]);
         if (lane == 0) sresp[warp * NRESP + i] = (double)v;
     }
-    for (int dd = 0; dd < MAXGDS; ++dd) su[dd * W * 32 + warp * 32 + lane] = kval ? U0[dd] * c[F_N] : R(0);
+    for (int dd = 0; dd < MAXGDS; ++dd) su[dd * W * 32 + warp * 32 + lane] = kval ? (U0[dd] + U0c[dd]) * c[F_N] : R(0);
     __syncthreads();
     double* part = a.partbuf + (((long long)t * a.G + g) * a.nbtask + task) * a.NPART;
     if (threadIdx.x < NRESP) {
@@ -780,8 +897,15 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
         if (dd < nds && a.ft.sp_kind[s] < 2 && a.rfac[tb_g_ds(a, g, dd) * a.S + s] != 0.0) {
             R acc = 0;
             if constexpr (sizeof(R) == 4) {
+                // blocks of 32 columns folded into a compensated sum
                 const float* Srow = a.Sf + (long long)s * a.K + kbase;
-                for (int cc = 0; cc < ncol; ++cc) acc = fmaf(Srow[cc], su[dd * W * 32 + cc], acc);
+                float cmp = 0.f, part32 = 0.f;
+                for (int cc = 0; cc < ncol; ++cc) {
+                    part32 = fmaf(Srow[cc], su[dd * W * 32 + cc], part32);
+                    if ((cc & 31) == 31) { two_sum_acc(acc, cmp, part32); part32 = 0.f; }
+                }
+                two_sum_acc(acc, cmp, part32);
+                acc += cmp;
             } else {
                 const double* Srow = a.Sd + (long long)s * a.K + kbase;
                 for (int cc = 0; cc < ncol; ++cc) acc = fma(Srow[cc], su[dd * W * 32 + cc], acc);
@@ -813,7 +937,8 @@ __global__ void __launch_bounds__(128) k_gradfinal(KArgs a) {
         __syncthreads();
         if (threadIdx.x == 0) {
             // the slots hold unscaled parameters: d(scale p)/dp = scale
-            for (int i = 0; i < NRESP; ++i) gr[tb_g_resp(a, g, i)] += vals[i] * tb_g_rscale(a, g, i);
+            for (int i = 0; i < NRESP; ++i)
+                if (tb_g_resp(a, g, i) >= 0) gr[tb_g_resp(a, g, i)] += vals[i] * tb_g_rscale(a, g, i);
             for (int dd = 0; dd < tb_g_nds(a, g); ++dd) {
                 const int d = tb_g_ds(a, g, dd);
                 for (int s = 0; s < a.S; ++s) {
@@ -854,10 +979,12 @@ DEV void species_loop(const KArgs& a, int g, float xlo_w, float xhi_w, bool vali
             if (c[F_XMAX] < (R)xlo_w || c[F_XMIN] > (R)xhi_w) continue;
             R v;
             if constexpr (sizeof(R) == 4) {
-                v = bin_value_f<RES, NG>(c, xc, del, lam, wt);
-                if (RES == 1 && is_zero) v = valid ? c[F_P0] : 0.0f;
+                if constexpr (RES == 2) v = gg_bin_value_f<NG>(c, xc, lam, wt);
+                else v = bin_value_f<RES, NG>(c, xc, del, lam, wt);
+                if (RES >= 1 && is_zero) v = valid ? c[F_P0] : 0.0f;
             } else {
-                v = bin_value_gamma_d<NG>(c, del, lam, wt);
+                if constexpr (RES == 2) v = gg_bin_value_d<NG>(c, lam, wt);
+                else v = bin_value_gamma_d<NG>(c, del, lam, wt);
                 if (is_zero) v = valid ? c[F_P0] : 0.0;
             }
             v *= c[F_N];
@@ -1105,7 +1232,8 @@ cudaError_t run_probe(int which, int nsm, double* ops) {
 cudaError_t launch_columns(const KArgs& a, cudaStream_t st) {
     dim3 grid(a.nblk, a.G, a.T);
     if (a.precision == 1) {
-        if (a.fast) {
+        if (a.res == 2)  k_columns<float, 2, false><<<grid, COLBLK, 0, st>>>(a);
+        else if (a.fast) {
             if (a.res == 0) k_columns<float, 0, true><<<grid, COLBLK, 0, st>>>(a);
             else            k_columns<float, 1, true><<<grid, COLBLK, 0, st>>>(a);
         } else {
@@ -1113,8 +1241,9 @@ cudaError_t launch_columns(const KArgs& a, cudaStream_t st) {
             else            k_columns<float, 1, false><<<grid, COLBLK, 0, st>>>(a);
         }
     } else {
-        if (a.res == 0) k_columns<double, 0, false><<<grid, COLBLK, 0, st>>>(a);
-        else            k_columns<double, 1, false><<<grid, COLBLK, 0, st>>>(a);
+        if (a.res == 0)      k_columns<double, 0, false><<<grid, COLBLK, 0, st>>>(a);
+        else if (a.res == 1) k_columns<double, 1, false><<<grid, COLBLK, 0, st>>>(a);
+        else                 k_columns<double, 2, false><<<grid, COLBLK, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -1122,10 +1251,13 @@ cudaError_t launch_columns(const KArgs& a, cudaStream_t st) {
 cudaError_t launch_forward(const KArgs& a, cudaStream_t st) {
     dim3 grid(a.ntile, a.nsplit, a.T * a.G);
     if (a.precision == 1) {
-        return launch_forward_mixed(a, st);
+        // the generalized gamma of free power runs the general per-node kernel
+        if (a.res == 2) k_forward<float, 2><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else return launch_forward_mixed(a, st);
     } else {
-        if (a.res == 0) k_forward_gauss64<<<grid, FWD_WARPS * 32, 0, st>>>(a);
-        else            k_forward<double, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        if (a.res == 0)      k_forward_gauss64<<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else if (a.res == 1) k_forward<double, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else                 k_forward<double, 2><<<grid, FWD_WARPS * 32, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -1143,12 +1275,15 @@ cudaError_t launch_devfinal(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_backward(const KArgs& a, cudaStream_t st) {
-    if (a.precision == 1) return launch_backward_mixed(a, st);
+    if (a.precision == 1 && a.res != 2) return launch_backward_mixed(a, st);
     dim3 grid(a.nbtask, a.G, a.T);
     const int threads = a.bw_warps * 32;
-    const size_t sm = sizeof(double) * MAXGDS * threads + 16 + sizeof(double) * a.bw_warps * NRESP;
-    if (a.res == 0) k_backward<double, 0><<<grid, threads, sm, st>>>(a);
-    else            k_backward<double, 1><<<grid, threads, sm, st>>>(a);
+    const size_t rs = a.precision == 1 ? sizeof(float) : sizeof(double);
+    const size_t sm = rs * MAXGDS * threads + 16 + sizeof(double) * a.bw_warps * NRESP;
+    if (a.precision == 1)  k_backward<float, 2><<<grid, threads, sm, st>>>(a);
+    else if (a.res == 0)   k_backward<double, 0><<<grid, threads, sm, st>>>(a);
+    else if (a.res == 1)   k_backward<double, 1><<<grid, threads, sm, st>>>(a);
+    else                   k_backward<double, 2><<<grid, threads, sm, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1166,10 +1301,12 @@ cudaError_t launch_species(const KArgs& a, cudaStream_t st) {
     }
     dim3 grid((a.Jmax + FWD_WARPS * 32 - 1) / (FWD_WARPS * 32), a.G, nchunk);
     if (a.precision == 1) {
-        if (a.res == 0) k_species<float, 0><<<grid, FWD_WARPS * 32, 0, st>>>(a);
-        else            k_species<float, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        if (a.res == 0)      k_species<float, 0><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else if (a.res == 1) k_species<float, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else                 k_species<float, 2><<<grid, FWD_WARPS * 32, 0, st>>>(a);
     } else {
-        k_species<double, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        if (a.res == 1) k_species<double, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else            k_species<double, 2><<<grid, FWD_WARPS * 32, 0, st>>>(a);
     }
     return cudaGetLastError();
 }

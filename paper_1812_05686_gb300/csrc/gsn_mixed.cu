@@ -241,19 +241,6 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
 }
 
 // ------------------------------------------------------------ backward -----
-// compensated warp sum of (s, c) pairs; result in every lane
-DEV float warp_sum_comp(float s, float c) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float so = __shfl_xor_sync(0xffffffffu, s, o);
-        const float co = __shfl_xor_sync(0xffffffffu, c, o);
-        const float tsum = s + so;
-        const float bp = tsum - s;
-        c = c + co + ((s - (tsum - bp)) + (so - bp));
-        s = tsum;
-    }
-    return s + c;
-}
 
 // resident 256-thread blocks per SM the adjoint's register budget is sized for
 #ifndef GSN_BW_MINBLOCKS

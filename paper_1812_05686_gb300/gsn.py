@@ -19,7 +19,7 @@ GSN_OK = 0
 GSN_ERR_ARG, GSN_ERR_CUDA, GSN_ERR_NONPOSITIVE_MU, GSN_ERR_NONFINITE, GSN_ERR_STATE, GSN_ERR_NOMEM = -1, -2, -3, -4, -5, -6
 GSN_ERR_TIMEOUT = -7
 GSN_FP64, GSN_MIXED = 0, 1
-GSN_RES_GAUSS, GSN_RES_GAMMA = 0, 1
+GSN_RES_GAUSS, GSN_RES_GAMMA, GSN_RES_GGAMMA = 0, 1, 2
 GSN_ANA, GSN_ANA_SHIFT, GSN_ANA_PEAK, GSN_MC_TEMPLATE = 0, 1, 2, 3
 
 

@@ -1,0 +1,100 @@
+"""Generalized-gamma response with a free power p (section 2.3) on the GPU against the FP64 oracle.
+
+Stacy's density with (d, s) moment-matched per column for the fit parameter p, through the C ABI.
+FP64 path: 1e-10 relative on the NLL and 1e-8 normwise on the gradient, as for the other responses.
+Mixed path: |dNLL| < 1e-3; gradient 3e-5 normwise.  On this 240-bin workload the worst component is
+always kB: at the perturbed points used here the mixed generalized gamma reaches 2.2e-5 where the
+mixed gamma path reaches 1.1e-5 at the same point (p = 1), so the bound is the gamma path's
+measured error with a factor 3; toy batches of the full problem stay within 1e-5 (see the batch test).
+"""
+import numpy as np
+import pytest
+
+from oracle import gsn_oracle as O
+from paper_1812_05686_gb300 import gsn, inputs as I
+from tests._helpers import norm_rel
+
+pytestmark = pytest.mark.gpu
+FP64, MIXED = gsn.GSN_FP64, gsn.GSN_MIXED
+
+
+def _data(w, seed):
+    mu = [O.expected_counts(w, w["theta0"], d) for d in range(len(w["edges"]))]
+    return mu, np.concatenate([I.poisson_counts(m, seed + d) for d, m in enumerate(mu)])
+
+
+@pytest.fixture(scope="module", params=[0.7, 1.6])
+def problem(request):
+    w = I.with_power(I.borexino_like(n_bins=240, n_fine=2400), request.param, pull_width=0.05)
+    mu, n = _data(w, 501)
+    return w, n
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_eval_grad_against_oracle(problem, precision):
+    w, n = problem
+    ctx = gsn.context_from_workload(w, precision, counts=n)
+    for p in I.perturbed_points(w["theta0"], 2, 502):
+        rc, v, g = ctx.eval_grad(p)
+        assert rc == 0, ctx.last_error()
+        ref, gref = O.nll(w, p, n), O.nll_grad(w, p, n)
+        if precision == FP64:
+            assert abs(v - ref) <= 1e-10 * abs(ref), (v, ref)
+            assert norm_rel(g, gref) < 1e-8, norm_rel(g, gref)
+        else:
+            assert abs(v - ref) < 1e-3, (v, ref)
+            assert norm_rel(g, gref) < 3e-5, norm_rel(g, gref)
+        rc, v2 = ctx.eval(p)
+        assert rc == 0 and abs(v2 - ref) <= (1e-10 * abs(ref) if precision == FP64 else 1e-3)
+
+
+def test_power_one_matches_the_gamma_response():
+    base = I.borexino_like(n_bins=200, n_fine=2000)
+    w = I.with_power(base, 1.0)
+    mu, n = _data(base, 511)
+    p0 = I.perturbed_points(base["theta0"], 1, 512)[0]
+    for precision, tol in ((FP64, 1e-11), (MIXED, 1e-3)):
+        rc0, v0, g0 = gsn.context_from_workload(base, precision, counts=n).eval_grad(p0)
+        rc1, v1, g1 = gsn.context_from_workload(w, precision, counts=n).eval_grad(np.concatenate([p0, [1.0]]))
+        assert rc0 == 0 and rc1 == 0
+        assert abs(v1 - v0) <= tol * (abs(v0) if precision == FP64 else 1.0)
+        assert norm_rel(g1[:-1], g0) < (1e-8 if precision == FP64 else 1e-5)
+
+
+def test_toy_batch_against_oracle():
+    w = I.with_power(I.borexino_like(n_bins=240, n_fine=2400), 1.3)
+    mu, _ = _data(w, 521)
+    b = I.toy_batch(w, mu, n_toys=6, seed0=522, w_min=120, w_max=240)
+    r = {}
+    for precision in (FP64, MIXED):
+        ctx = gsn.context_from_workload(w, precision)
+        rc, nll, g = ctx.eval_grad_batch(b["params"], b["counts"], b["windows"])
+        assert rc == 0, ctx.last_error()
+        r[precision] = (nll, g)
+    for t in (0, 5):
+        ref = O.nll(w, b["params"][t], b["counts"][t], b["windows"][t])
+        gref = O.nll_grad(w, b["params"][t], b["counts"][t], b["windows"][t])
+        assert abs(r[FP64][0][t] - ref) <= 1e-10 * abs(ref)
+        assert norm_rel(r[FP64][1][t], gref) < 1e-8
+    assert np.max(np.abs(r[FP64][0] - r[MIXED][0])) < 1e-3
+    for t in range(6):
+        assert norm_rel(r[MIXED][1][t], r[FP64][1][t]) < 1e-5
+
+
+def test_expected_per_species_against_oracle(problem):
+    w, n = problem
+    p = I.perturbed_points(w["theta0"], 1, 530)[0]
+    for precision, tol in ((FP64, 1e-10), (MIXED, 2e-5)):
+        ctx = gsn.context_from_workload(w, precision, counts=n)
+        for d in range(2):
+            got, ref = ctx.expected(p, d), O.expected_per_species(w, p, d)
+            big = ref > 1e-6 * ref.max()
+            assert np.max(np.abs(got[big] / ref[big] - 1.0)) < tol
+
+
+def test_power_slot_must_be_mapped():
+    w = I.with_power(I.borexino_like(n_bins=100, n_fine=800), 1.2)
+    sm = np.array(w["slot_map"], copy=True)
+    sm[:, I.slot_power(w["spectra"].shape[0])] = -1
+    with pytest.raises(gsn.GsnError):
+        gsn.context_from_workload(dict(w, slot_map=sm), FP64)
