@@ -43,6 +43,13 @@ WORKLOAD = "borexino_like toys: 2 datasets x 1200-bin domain, 16 species x 20000
 #                 + nodes (15) + value / ln / offset-weighted sums (8) + mean / variance
 #                 coefficients (11) + four accumulations (8)
 FLOP_PER_PAIR = {"forward": 44, "backward": 70}
+# The same count for the generalized gamma of free power p (--power), general per-node kernels, linear
+# bins (3 nodes), |p L| <= 1/2 (the bulk of a band):
+#   forward  109 = offset and t (3) + ln(1+t) series (21) + per node [L and pL (2) + e^q-1-q series (19)
+#                  + e1 (1) + exponent (3) + weighted exponential (3)] x 3 + 2-dataset contraction (4)
+#   backward 178 = offset, t and ln(1+t) (24) + per node [the forward's 28 + four node sums (6)] x 3
+#                  + dataset weight (3) + four compensated band sums (28) + three compensated rate sums (21)
+FLOP_PER_PAIR_GG = {"forward": 109, "backward": 178}
 FP32_LANES_PER_SM = 128
 
 
@@ -58,6 +65,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mv-toys", type=int, default=1024, help="toys of the multivariate workload")
     ap.add_argument("--fit-toys", type=int, default=1024, help="toys of the discovery-test workload")
+    ap.add_argument("--power", type=float, default=None,
+                    help="toys workload with the generalized-gamma response of this free power p instead of "
+                         "the gamma response (p is a 24th parameter, perturbed per toy like the others)")
     ap.add_argument("--workload", default="toys",
                     choices=["toys", "single", "species", "multivariate", "templates", "discovery"],
                     help="toys: the batched pseudo-experiments (default); single: sequential single-point "
@@ -69,11 +79,15 @@ def parse():
 
 
 # ------------------------------------------------------------ inputs -------
-def make_inputs(n_toys, seed0):
+def make_inputs(n_toys, seed0, power=None):
+    """Toys of the 1200-bin workload; with a power p, the generalized-gamma response (the counts are
+    still drawn from the gamma response's expectation: only the model evaluated differs)."""
     import numpy as np
 
     from paper_1812_05686_gb300 import inputs as I
     w = I.borexino_like(n_bins=1200)
+    if power is not None:
+        w = I.with_power(w, power)
     mu0 = np.loadtxt(os.path.join(ROOT, "tests", "golden", "borexino_like_1200_mu0.txt"))
     b = I.toy_batch(w, [mu0[:1200], mu0[1200:]], n_toys=n_toys, seed0=seed0)
     return w, b
@@ -252,7 +266,8 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     T = args.toys
-    w, b = make_inputs(T, 1000 + rank * T)
+    w, b = make_inputs(T, 1000 + rank * T, args.power)
+    gg = args.power is not None
     # a dedicated stream: the library launches on it and the timing events are recorded on it
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
@@ -348,13 +363,13 @@ def run_ours(args, rank, world, local_rank):
     dom = max(("forward", "backward"), key=lambda k: prof[k][0])
     kms, kn, kunits = prof[dom]
     per_launch_s = kms * 1e-3 / max(kn, 1)
-    flops = kunits / max(kn, 1) * FLOP_PER_PAIR[dom]
+    flops = kunits / max(kn, 1) * (FLOP_PER_PAIR_GG if gg else FLOP_PER_PAIR)[dom]
     sm_mhz = clk.get("sm_mhz") or 1455.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = nsm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
     achieved = flops / per_launch_s
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(dom), "kernel": dom,
+            "frac": achieved / peak, "traffic": None if gg else ncu_traffic(dom), "kernel": dom,
             "peak_basis": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock {sm_mhz:.0f} MHz",
             "pairs_per_launch": kunits / max(kn, 1), "ms_per_launch": per_launch_s * 1e3}
 
@@ -368,7 +383,10 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32 (f64 deviance and reductions)", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "toys_per_gpu": T, "fine_points": 20000, "bins": 1200,
+                "config": {"workload": WORKLOAD if not gg else
+                           WORKLOAD.replace("gamma response, 23 params",
+                                            f"generalized-gamma response of free power p = {args.power:g}, 24 params"),
+                           "toys_per_gpu": T, "fine_points": 20000, "bins": 1200,
                            "species": 16, "precision": "mixed",
                            "l2": "inputs and scratch per step (GBs) exceed the 129 MB L2"},
                 "fp64_path": fp64,

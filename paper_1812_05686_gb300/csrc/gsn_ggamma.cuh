@@ -86,26 +86,81 @@ DEV double gg_Hx(double x, double a) {
     return r;
 }
 
-// x = d/p solving H(x) = r = ln(1 + var/mu^2): Newton's method on ln H against ln x from the
-// two-term large-x inversion x0 = a^2/r - (a - 1/2).  Returns a negative value if it fails.
-DEV double gg_solve_shape(double r, double a) {
-    double x = a * a / r - (a - 0.5);
-    if (!(x > 0.5 * a * a / r)) x = a * a / r;
+// x = d/p solving H(x) = r = ln(1 + var/mu^2): Newton's method on ln H against ln x, started from
+// the series reversion of the first four terms of H's large-x expansion (Stirling's series with the
+// Bernoulli polynomials B_2..B_5; a = 1 gives ln(1 + 1/x)),
+//   H(x) = a^2/x + a^2 (1/2 - a)/x^2 + a^2 (7a^2 - 6a + 1)/(6 x^3) - a^3 (6a^2 - 7a + 2)/(4 x^4) + O(x^-5),
+// whose relative error is O(x^-4): a column of x >= 100 needs a single step.  Stops once a step is
+// below 1e-7 (the error left is its square).  lnx = ln x; hx = dH/dx at the root (the value at the
+// last point evaluated, moved to the root with dHx/dx = -2 Hx / x of the leading term).  Returns a
+// negative value if it fails.
+DEV double gg_solve_shape(double r, double a, double& lnx, double& hx) {
+    const double b2 = 0.5 - a, b3 = (1.0 + a * (7.0 * a - 6.0)) / 6.0, b4 = -a * (2.0 + a * (6.0 * a - 7.0)) / 4.0;
+    const double y0 = r / (a * a);
+    const double y = y0 * (1.0 + y0 * (-b2 + y0 * ((2.0 * b2 * b2 - b3) + y0 * (b2 * (5.0 * b3 - 5.0 * b2 * b2) - b4))));
+    double x = 1.0 / y;
+    if (!(x > 0.0) || !isfinite(x) || x < 0.5 / y0) x = 1.0 / y0;
     double u = log(x);
     for (int it = 0; it < 60; ++it) {
-        x = exp(u);
         const double h = gg_H(x, a);
-        const double g = log(h / r);
-        const double step = fmin(5.0, fmax(-5.0, -g * h / (x * gg_Hx(x, a))));
+        hx = gg_Hx(x, a);
+        const double step = fmin(5.0, fmax(-5.0, -log(h / r) * h / (x * hx)));
         u += step;
-        if (fabs(step) < 1e-14) return exp(u);
+        x = exp(u);
+        if (fabs(step) < 1e-7) {
+            hx *= exp(-2.0 * step);
+            lnx = u;
+            return x;
+        }
     }
     return -1.0;
 }
 
-// log f(x)/f(mu) for L = ln(x/mu): E(L) = k1 L - A (e^(pL) - 1 - pL), and its L-derivative
-DEV double gg_logratio(double L, double k1, double A, double p) { return k1 * L - A * (expm1(p * L) - p * L); }
-DEV double gg_logratio_d(double L, double k1, double A, double p) { return k1 - A * p * expm1(p * L); }
+// lnGamma(x) and psi(x) from Stirling's series for x >= 10 (lx = ln x), library / recurrence below
+DEV double gg_lgamma(double x, double lx) {
+    return x >= GG_XSTIR ? fma(x - 0.5, lx, -x) + 0.91893853320467274178 + gg_lgamma_tail(x) : lgamma(x);
+}
+DEV double gg_digamma(double x, double lx) {
+    return x >= GG_XSTIR ? lx - 0.5 / x + gg_digamma_tail(x) : digamma_d(x);
+}
+
+// ---- FP32 helpers of the mixed path ----
+// Q2(q) = e^q - 1 - q with relative precision, and E1 = e^q - 1.  The series
+// Q2(h) = h^2 (1/2 + h/6 + ... + h^8/10!) has relative truncation error below 2 |h|^9 / 11! (1e-10
+// at |h| = 1/2).  |q| <= 1/2 (the bulk of a band): the series at q.  |q| <= 2: the series at
+// h = q/4 and two doublings Q2(2h) = E1(h)^2 + 2 Q2(h), E1(2h) = E1(h)^2 + 2 E1(h), which add
+// non-negative terms to Q2.  Beyond, e^q - 1 - q loses at most a factor ~1.7 to cancellation.
+DEV float gg_q2_series(float h) {
+    float s = fmaf(h, 1.0f / 3628800, 1.0f / 362880);
+    s = fmaf(s, h, 1.0f / 40320);
+    s = fmaf(s, h, 1.0f / 5040);
+    s = fmaf(s, h, 1.0f / 720);
+    s = fmaf(s, h, 1.0f / 120);
+    s = fmaf(s, h, 1.0f / 24);
+    s = fmaf(s, h, 1.0f / 6);
+    s = fmaf(s, h, 0.5f);
+    return (h * h) * s;
+}
+DEV float gg_q2f(float q, float& e1) {
+    const float aq = fabsf(q);
+    if (aq <= 0.5f) {
+        const float Q = gg_q2_series(q);
+        e1 = q + Q;
+        return Q;
+    }
+    if (aq <= 2.0f) {
+        const float h = 0.25f * q;
+        float Q = gg_q2_series(h);
+        float E = h + Q;
+        Q = fmaf(E, E, 2.0f * Q); E = fmaf(E, E, 2.0f * E);
+        Q = fmaf(E, E, 2.0f * Q); E = fmaf(E, E, 2.0f * E);
+        e1 = E;
+        return Q;
+    }
+    const float e = ex2f(mul_l2e(q)) - 1.0f;
+    e1 = e;
+    return e - q;
+}
 
 // lower regularised incomplete gamma P(a, y) by its power series, with dP/da and y^a e^-y / Gamma(a)
 DEV void gg_inc_gamma(double a, double y, double& P, double& Pa, double& py) {
@@ -134,14 +189,15 @@ DEV double gg_column(double mu, double var, double p, double cut, double x1, boo
                      R* f, double* gco, R& xmin, R& xmax) {
     const double a = 1.0 / p;
     const double r = log1p(var / (mu * mu));
-    const double xs = gg_solve_shape(r, a);          // d/p
+    double Hx, lxs;                                   // dH/dx at the root, ln(d/p)
+    const double xs = gg_solve_shape(r, a, lxs, Hx);  // d/p
     const double d = p * xs;
     const double ls = gg_lgamma_diff(xs, a);          // ln(mu/s)
     const double lns = log(mu) - ls;                  // ln s
     const double A = exp(p * ls);                     // (mu/s)^p
     const double k1 = (d - 1.0) - p * A;
-    const double psi = digamma_d(xs);
-    const double lgx = lgamma(xs);
+    const double psi = gg_digamma(xs, lxs);
+    const double lgx = gg_lgamma(xs, lxs);
     // density at the mean: ln f(mu) = ln p - ln mu + d ln(mu/s) - A - lnGamma(d/p)
     const double lfm = log(p) - log(mu) + d * ls - A - lgx;
     double Nk = 1.0;
@@ -156,27 +212,40 @@ DEV double gg_column(double mu, double var, double p, double cut, double x1, boo
         f[F_C] = (R)lns;
     }
     f[F_KAPPA] = (R)p;
-    // band: E(L) is concave in L (E'' = -A p^2 e^(pL)); Newton steps from outer bounds stay outside
+    // band [xmin, xmax] where E(L) = log f/f(mu) >= -cut, in FP32 (bounds need only be conservative:
+    // the cut is widened by 0.01 against the FP32 rounding of E).  E is concave in L
+    // (E'' = -A p^2 e^(pL)), so Newton steps started outside the band stay outside.
     {
-        const double Ap2 = A * p * p;
-        // E <= k1 L - A p^2 L^2 / 2 for L >= 0; columns of tiny shape reach far out (kept finite)
-        double L = fmin((k1 + sqrt(k1 * k1 + 2.0 * Ap2 * cut)) / Ap2, 600.0 / p);
-        for (int it = 0; it < 4; ++it) {
-            const double Ln = L - (gg_logratio(L, k1, A, p) + cut) / gg_logratio_d(L, k1, A, p);
-            if (isfinite(Ln) && Ln > 0.0) L = fmin(Ln, 600.0 / p);
+        const float k1f = (float)k1, Af = (float)A, pf = (float)p, cf = (float)cut + 0.01f;
+        const float Lmax = 80.0f / pf;                // e^(pL) stays finite in FP32
+        auto E = [&](float L, float& dE) {
+            float e1;
+            const float Q = gg_q2f(pf * L, e1);
+            dE = fmaf(-Af * pf, e1, k1f);
+            return fmaf(-Af, Q, k1f * L);
+        };
+        const float Ap2 = Af * pf * pf;
+        // E <= k1 L - A p^2 L^2 / 2 for L >= 0: the positive root of that bound is outside the band
+        float L = fminf((k1f + sqrtf(k1f * k1f + 2.0f * Ap2 * cf)) / Ap2, Lmax);
+        for (int it = 0; it < 4 && L < Lmax; ++it) {
+            float dE;
+            const float e = E(L, dE);
+            const float Ln = L - (e + cf) / dE;
+            if (isfinite(Ln) && Ln > 0.0f && Ln < L) L = Ln;
         }
-        xmax = (R)fmin(mu * exp(L), 1e30);
+        xmax = L >= Lmax ? (R)1e30 : (R)(mu * (double)expf(L));
         xmin = 0;
         if (d > 1.0) {
-            double Lo = -sqrt(2.0 * cut / Ap2);
+            float Lo = -sqrtf(2.0f * cf / Ap2), dE;
             int grow = 0;
-            while (gg_logratio(Lo, k1, A, p) > -cut && grow < 60) { Lo = 1.5 * Lo - 0.5; ++grow; }
-            if (grow < 60 && Lo > -700.0) {
+            while (E(Lo, dE) > -cf && grow < 60 && Lo > -Lmax) { Lo = 1.5f * Lo - 0.5f; ++grow; }
+            if (Lo > -Lmax) {
                 for (int it = 0; it < 4; ++it) {
-                    const double Ln = Lo - (gg_logratio(Lo, k1, A, p) + cut) / gg_logratio_d(Lo, k1, A, p);
-                    if (isfinite(Ln) && Ln < 0.0) Lo = fmax(Lo, Ln);
+                    const float e = E(Lo, dE);
+                    const float Ln = Lo - (e + cf) / dE;
+                    if (isfinite(Ln) && Ln < 0.0f && Ln > Lo) Lo = Ln;
                 }
-                xmin = (R)(mu * exp(Lo));
+                xmin = (R)(mu * (double)expf(Lo));
             }
         }
     }
@@ -191,9 +260,9 @@ DEV double gg_column(double mu, double var, double p, double cut, double x1, boo
     }
     f[F_P0] = (R)(P0 / Nk);
     // moment matching H(x, a) = ln rho, ln s = ln mu - G(x, a): implicit derivatives of x and u = ln s
-    const double Hx = gg_Hx(xs, a);
-    const double da = gg_digamma_diff(xs, a), d2a = gg_digamma_diff(xs, 2.0 * a);
-    const double Ha = 2.0 * (d2a - da);
+    // dH/da = 2 [psi(x + 2a) - psi(x + a)] = 2 (dH/dx + [psi(x + a) - psi(x)]): no cancellation
+    const double da = gg_digamma_diff(xs, a);
+    const double Ha = 2.0 * (Hx + da);
     const double Gx = da, Ga = psi + da;              // psi(x + a) = psi(x) + [psi(x + a) - psi(x)]
     const double r_mu = -2.0 * var / (mu * (mu * mu + var)), r_var = 1.0 / (mu * mu + var);
     const double x_mu = r_mu / Hx, x_var = r_var / Hx, x_p = Ha / (p * p * Hx);
@@ -234,44 +303,6 @@ DEV double gg_column(double mu, double var, double p, double cut, double x1, boo
     }
     gco[15] = 0;
     return Nk;
-}
-
-// ---- FP32 helpers of the mixed path ----
-// Q2(q) = e^q - 1 - q with relative precision, and E1 = e^q - 1.  The series
-// Q2(h) = h^2 (1/2 + h/6 + ... + h^8/10!) has relative truncation error below 2 |h|^9 / 11! (1e-10
-// at |h| = 1/2).  |q| <= 1/2 (the bulk of a band): the series at q.  |q| <= 2: the series at
-// h = q/4 and two doublings Q2(2h) = E1(h)^2 + 2 Q2(h), E1(2h) = E1(h)^2 + 2 E1(h), which add
-// non-negative terms to Q2.  Beyond, e^q - 1 - q loses at most a factor ~1.7 to cancellation.
-DEV float gg_q2_series(float h) {
-    float s = fmaf(h, 1.0f / 3628800, 1.0f / 362880);
-    s = fmaf(s, h, 1.0f / 40320);
-    s = fmaf(s, h, 1.0f / 5040);
-    s = fmaf(s, h, 1.0f / 720);
-    s = fmaf(s, h, 1.0f / 120);
-    s = fmaf(s, h, 1.0f / 24);
-    s = fmaf(s, h, 1.0f / 6);
-    s = fmaf(s, h, 0.5f);
-    return (h * h) * s;
-}
-DEV float gg_q2f(float q, float& e1) {
-    const float aq = fabsf(q);
-    if (aq <= 0.5f) {
-        const float Q = gg_q2_series(q);
-        e1 = q + Q;
-        return Q;
-    }
-    if (aq <= 2.0f) {
-        const float h = 0.25f * q;
-        float Q = gg_q2_series(h);
-        float E = h + Q;
-        Q = fmaf(E, E, 2.0f * Q); E = fmaf(E, E, 2.0f * E);
-        Q = fmaf(E, E, 2.0f * Q); E = fmaf(E, E, 2.0f * E);
-        e1 = E;
-        return Q;
-    }
-    const float e = ex2f(mul_l2e(q)) - 1.0f;
-    e1 = e;
-    return e - q;
 }
 
 // mixed bin value of a generalized-gamma column relative to its density at the mean:
