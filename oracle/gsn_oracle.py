@@ -43,6 +43,15 @@ Readings (the paper gives no formula for them):
   in the dataset's own visible bins ("templates" key: [species][dataset] array
   or None), normalised to unit sum; it enters as eps_d f_ds r_s T_dsj with no
   response;
+* multivariate likelihood with a secondary observable (section 2.4, the extra likelihood pieces
+  of MultiVariatePdf; workload key "secondary": per dataset None or dict(slice_start (Q+1,),
+  shapes (S, Q, M), counts (Q, M))): the dataset's energy bins form Q contiguous slices, each with
+  a histogram of a second observable in M bins; species s contributes to slice q its expected
+  counts N_sq = sum_{j in q} mu_j^s spread by a fixed shape P_sqm (each (s, q) row normalised to
+  unit sum, zero rows allowed); every slice inside the fit window adds
+  sum_m [mu_qm - n_qm + n_qm ln(n_qm/mu_qm)], mu_qm = sum_s N_sq P_sqm, to the NLL (an extended
+  Poisson piece: its events also populate the energy histogram, as adding likelihood pieces does);
+  toy counts append each dataset's secondary counts (slices in order, m inner) after the energy bins;
 * NLL = sum_d sum_{j in window} [mu - n + n ln(n/mu)] + 1/2 sum_pulls ((p-c)/sigma)^2,
   i.e. -ln L of Eq. (LL) up to a data-only constant, with the pull term read
   as the usual Gaussian constraint (Eq. (LL) prints its sign/factor garbled).
@@ -421,6 +430,7 @@ def _windows(work, windows):
 
 
 def _split_counts(work, counts):
+    """Energy counts per dataset (a toy's secondary counts, if any, follow them and are ignored here)."""
     if isinstance(counts, (list, tuple)):
         return [np.asarray(c, np.float64) for c in counts]
     c = np.asarray(counts, np.float64)
@@ -431,15 +441,72 @@ def _split_counts(work, counts):
     return out
 
 
+# --------------------------------------------- secondary observable (section 2.4) ----
+def secondary_shapes(work, d):
+    """Normalised secondary shapes P[s, q, m] of dataset d (rows of zero sum stay zero), or None."""
+    sec = work.get("secondary")
+    if sec is None or sec[d] is None:
+        return None
+    P = np.array(sec[d]["shapes"], np.float64, copy=True)
+    tot = P.sum(axis=2, keepdims=True)
+    return np.divide(P, tot, out=np.zeros_like(P), where=tot > 0)
+
+
+def _secondary_counts(work, counts):
+    """Observed secondary counts per dataset ((Q, M) or None): the tail of a toy's counts row after
+    the energy bins when present, else the workload's own."""
+    sec = work.get("secondary")
+    D = len(work["edges"])
+    if sec is None:
+        return [None] * D
+    flat = None
+    if not isinstance(counts, (list, tuple)):
+        c = np.asarray(counts, np.float64)
+        nE = sum(len(e) - 1 for e in work["edges"])
+        if c.size > nE:
+            flat, o = c[nE:], 0
+    out = []
+    for d in range(D):
+        if sec[d] is None:
+            out.append(None)
+            continue
+        Q, M = np.asarray(sec[d]["shapes"]).shape[1:]
+        if flat is not None:
+            out.append(flat[o:o + Q * M].reshape(Q, M)); o += Q * M
+        else:
+            out.append(np.asarray(sec[d]["counts"], np.float64).reshape(Q, M))
+    return out
+
+
+def _active_slices(work, d, lo, hi):
+    st = np.asarray(work["secondary"][d]["slice_start"], np.int64)
+    return [q for q in range(st.size - 1) if st[q] >= lo and st[q + 1] <= hi and st[q + 1] > st[q]]
+
+
+def secondary_expected(work, params, d):
+    """N[s, q] (species' expected counts in every slice) and mu[q, m] = sum_s N[s, q] P[s, q, m]."""
+    P = secondary_shapes(work, d)
+    st = np.asarray(work["secondary"][d]["slice_start"], np.int64)
+    per = expected_per_species(work, params, d)
+    N = np.stack([per[st[q]:st[q + 1]].sum(axis=0) for q in range(st.size - 1)], axis=1)
+    return N, np.einsum("sq,sqm->qm", N, P)
+
+
 def nll(work, params, counts, windows=None):
     """NLL = sum_d sum_{j in window_d} [mu - n + n ln(n/mu)] + 1/2 sum pulls^2 (section 4.1, Eq. LL)."""
     cs = _split_counts(work, counts)
+    sc = _secondary_counts(work, counts)
     total = 0.0
     for d, (lo, hi) in enumerate(_windows(work, windows)):
         if hi <= lo:
             continue
         mu = expected_counts(work, params, d)
         total += float(np.sum(poisson_term(mu[lo:hi], cs[d][lo:hi])))
+        if sc[d] is not None:
+            act = _active_slices(work, d, lo, hi)
+            if act:
+                _, mq = secondary_expected(work, params, d)
+                total += float(np.sum(poisson_term(mq[act], sc[d][act])))
     return total + pull_term(work, params)
 
 
@@ -453,6 +520,7 @@ def nll_grad(work, params, counts, windows=None):
     """
     params = np.asarray(params, np.float64)
     cs = _split_counts(work, counts)
+    seccnt = _secondary_counts(work, counts)
     P = int(work["n_params"])
     g = np.zeros(P)
     Sp = species_spectra(work)
@@ -472,17 +540,34 @@ def nll_grad(work, params, counts, windows=None):
         mu = expected_counts(work, params, d)
         w = np.zeros(edges.size - 1)
         w[lo:hi] = 1.0 - n[lo:hi] / mu[lo:hi]
+        # secondary pieces: dNLL/dmu_j^s = v_{s, q(j)} = sum_m (1 - n_qm/mu_qm) P_sqm on the bins of
+        # every active slice, on top of the energy weight w_j shared by all species
+        V = np.zeros((edges.size - 1, S))
+        if seccnt[d] is not None:
+            act = _active_slices(work, d, lo, hi)
+            if act:
+                Psh = secondary_shapes(work, d)
+                _, mq = secondary_expected(work, params, d)
+                st = np.asarray(work["secondary"][d]["slice_start"], np.int64)
+                for q in act:
+                    V[st[q]:st[q + 1]] = (1.0 - seccnt[d][q] / mq[q]) @ Psh[:, q, :].T
         gs = np.zeros(vals.size)  # gradient wrt the dataset's slots
         # smeared species and the response parameters (datasets of template / peak species only skip this)
         smeared = mask & (np.asarray(work["kind"]) < KIND_ANA_PEAK)
         base = S
         if smeared.any():
             Eq, mu_k, var_k = column_mean_var(work, resp)
-            T = eps * ((frac * rates)[smeared][:, None] * Sp[smeared]).sum(axis=0)
+            Ts = eps * (frac * rates)[smeared][:, None] * Sp[smeared]    # per smeared species
+            T = Ts.sum(axis=0)
+            Vs = V[:, smeared]
+
+            def wsum(dX):
+                """sum_j sum_s (w_j + v_sj) dX_jk T_sk: the weighted derivative per column"""
+                return (w @ dX) * T + ((Vs.T @ dX) * Ts).sum(axis=0)
             R = response_matrix(work, edges, resp)
             u = w @ R  # u_k = sum_j w_j R_jk
             for s in np.nonzero(smeared)[0]:
-                gs[s] += eps * frac[s] * float(Sp[s] @ u)
+                gs[s] += eps * frac[s] * float(Sp[s] @ (u + V[:, s] @ R))
             # response parameters through (mu_k, var_k)
             x = edges[:, None]
             if int(work["resolution"]) == RES_GAUSS:
@@ -491,8 +576,8 @@ def nll_grad(work, params, counts, windows=None):
                 phi = np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
                 dR_dmu = -(phi[1:] - phi[:-1]) / sig[None, :]
                 dR_dsig = -(z[1:] * phi[1:] - z[:-1] * phi[:-1]) / sig[None, :]
-                g_mu = (w @ dR_dmu) * T
-                g_sig = (w @ dR_dsig) * T
+                g_mu = wsum(dR_dmu)
+                g_sig = wsum(dR_dsig)
                 g_var = g_sig / (2.0 * sig)
             elif int(work["resolution"]) == RES_GGAMMA:
                 pw = resp["p"]
@@ -510,9 +595,9 @@ def nll_grad(work, params, counts, windows=None):
                 dR_dd = (Pa[1:] - Pa[:-1]) / pw
                 dR_dlns = -pw * (py[1:] - py[:-1])
                 dR_dp = -(dsh / pw**2)[None, :] * (Pa[1:] - Pa[:-1]) + (pyl[1:] - pyl[:-1])
-                g_d = (w @ dR_dd) * T
-                g_u = (w @ dR_dlns) * T
-                g_pe = (w @ dR_dp) * T
+                g_d = wsum(dR_dd)
+                g_u = wsum(dR_dlns)
+                g_pe = wsum(dR_dp)
                 # moment matching H(x, a) = ln rho, ln s = ln mu - G(x, a), G = lnGamma(x+a) - lnGamma(x):
                 # implicit derivatives of x = d/p and u = ln s with respect to (mu, var, p)
                 Hx = ggamma_log_moment_ratio_dx(xs, a)
@@ -533,8 +618,8 @@ def nll_grad(work, params, counts, windows=None):
                 py = _gamma_pdf_times_y(dd, y)
                 dR_dd = Pd[1:] - Pd[:-1]
                 dR_ds = -(py[1:] - py[:-1]) / sc[None, :]
-                g_d = (w @ dR_dd) * T
-                g_s = (w @ dR_ds) * T
+                g_d = wsum(dR_dd)
+                g_s = wsum(dR_ds)
                 g_mu = g_d * (2.0 * mu_k / var_k) + g_s * (-var_k / mu_k**2)
                 g_var = g_d * (-(mu_k**2) / var_k**2) + g_s / mu_k
             g_mu_tot = g_mu + g_var * (resp["b"] + 2.0 * resp["c"] * mu_k)
@@ -547,16 +632,17 @@ def nll_grad(work, params, counts, windows=None):
             gs[base:base + 5] *= scale
         # template species: mu is linear in the rate
         for s in np.nonzero(mask & (np.asarray(work["kind"]) == KIND_MC_TEMPLATE))[0]:
-            gs[s] += eps * frac[s] * float(w @ template(work, s, d))
+            gs[s] += eps * frac[s] * float((w + V[:, s]) @ template(work, s, d))
         # peak species
         for s in np.nonzero(mask & (np.asarray(work["kind"]) == KIND_ANA_PEAK))[0]:
             m, wd = peaks[s]
             zz = (edges - m) / wd
             ph = np.exp(-0.5 * zz * zz) / math.sqrt(2.0 * math.pi)
             prof = _norm_cdf_diff(zz[:-1], zz[1:])
-            gs[s] += eps * frac[s] * float(w @ prof)
-            gs[base + 5 + 2 * s] += eps * frac[s] * rates[s] * float(w @ (-(ph[1:] - ph[:-1]) / wd))
-            gs[base + 5 + 2 * s + 1] += eps * frac[s] * rates[s] * float(w @ (-(zz[1:] * ph[1:] - zz[:-1] * ph[:-1]) / wd))
+            ws = w + V[:, s]
+            gs[s] += eps * frac[s] * float(ws @ prof)
+            gs[base + 5 + 2 * s] += eps * frac[s] * rates[s] * float(ws @ (-(ph[1:] - ph[:-1]) / wd))
+            gs[base + 5 + 2 * s + 1] += eps * frac[s] * rates[s] * float(ws @ (-(zz[1:] * ph[1:] - zz[:-1] * ph[:-1]) / wd))
         sm = np.asarray(work["slot_map"])[d]
         for slot, pidx in enumerate(sm):
             if pidx >= 0:

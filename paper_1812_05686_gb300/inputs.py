@@ -40,6 +40,10 @@ resp_scale   (D, 5)      optional fixed multipliers of the response slots (LY, k
 rate_factor  (D, S)      optional fixed fraction of each species' rate in each dataset
                          (section 2.4 slices; default 1)
 templates    [S][D]      optional visible-bin histograms of template species (None elsewhere)
+secondary    [D]         optional secondary observable per dataset (section 2.4 multivariate fit):
+                         None or dict(slice_start (Q+1,) energy-bin boundaries of the slices,
+                         shapes (S, Q, M) per-species distributions of the second observable in
+                         every slice (normalised by the consumer), counts (Q, M) observed)
 """
 from __future__ import annotations
 
@@ -398,7 +402,7 @@ def toy_windows(n_toys: int, n_bins: int, w_min: int, w_max: int, seed: int) -> 
 
 
 def toy_batch(work: dict, mu0: list, n_toys: int, seed0: int = 1000,
-              w_min: int = 600, w_max: int = 1200, rel: float = 0.01) -> dict:
+              w_min: int = 600, w_max: int = 1200, rel: float = 0.01, mu_sec=None) -> dict:
     """Batched pseudo-experiments of a workload.
 
     Toy t: counts ~ Poisson(mu0) drawn with seed seed0 + t (all datasets
@@ -412,7 +416,9 @@ def toy_batch(work: dict, mu0: list, n_toys: int, seed0: int = 1000,
     total = int(sum(nb))
     mu_cat = np.concatenate([np.asarray(m, np.float64) for m in mu0])
     assert mu_cat.size == total
-    counts = np.empty((n_toys, total))
+    if mu_sec is not None:  # secondary-observable expectations (datasets, slices, m), appended
+        mu_cat = np.concatenate([mu_cat, np.asarray(mu_sec, np.float64).ravel()])
+    counts = np.empty((n_toys, mu_cat.size))
     for t in range(n_toys):
         counts[t] = poisson_counts(mu_cat, seed0 + t)
     params = perturbed_points(work["theta0"], n_toys, seed0 + n_toys, rel)
@@ -435,4 +441,33 @@ def with_power(work: dict, p: float = 1.3, pull_width: float = 0.0) -> dict:
         out.update(pull_param=np.concatenate([work["pull_param"], [P0]]).astype(np.int32),
                    pull_centre=np.concatenate([work["pull_centre"], [p]]),
                    pull_width=np.concatenate([work["pull_width"], [pull_width]]))
+    return out
+
+
+def with_secondary(work: dict, n_slices: int = 8, n_sec: int = 16, seed: int = 10, datasets=None) -> dict:
+    """A secondary observable for the given datasets (all by default; section 2.4 multivariate fit):
+    the energy histogram split into n_slices contiguous slices of equal width, and per species a
+    smooth distribution of a pulse-shape-like variable in n_sec bins: a Gaussian bump (centre
+    U[0.2, 0.8] of the range, width U[0.08, 0.25]) drifting by up to 5% of the range across the
+    slices, on a 2% flat floor.  Observed counts are zeros (tests draw them from an expectation)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    D, S = len(work["edges"]), work["spectra"].shape[0]
+    m = (np.arange(n_sec) + 0.5) / n_sec
+    sec = []
+    for d in range(D):
+        if datasets is not None and d not in datasets:
+            sec.append(None)
+            continue
+        J = len(work["edges"][d]) - 1
+        start = np.round(np.linspace(0, J, n_slices + 1)).astype(np.int64)
+        c = rng.uniform(0.2, 0.8, S)
+        wd = rng.uniform(0.08, 0.25, S)
+        drift = rng.uniform(-0.05, 0.05, S)
+        shapes = np.empty((S, n_slices, n_sec))
+        for q in range(n_slices):
+            cq = c + drift * (q / max(n_slices - 1, 1) - 0.5)
+            shapes[:, q, :] = 0.02 + np.exp(-0.5 * ((m[None, :] - cq[:, None]) / wd[:, None]) ** 2)
+        sec.append(dict(slice_start=start, shapes=shapes, counts=np.zeros((n_slices, n_sec))))
+    out = dict(work)
+    out.update(name=work.get("name", "workload") + f"+sec{n_slices}x{n_sec}", secondary=sec)
     return out

@@ -659,3 +659,128 @@ def test_planted_ggamma_mistake_is_caught(monkeypatch, name):
         except Exception:
             caught.append(True)
     assert any(caught), f"no pin caught the planted mistake '{name}'"
+
+
+# ------------------- secondary observable: the extra likelihood pieces (section 2.4) --------
+def _sec_small(n_sec=8):
+    w = I.with_secondary(I.borexino_like(n_bins=200, n_fine=800), n_slices=5, n_sec=n_sec)
+    mu = [O.expected_counts(w, w["theta0"], d) for d in range(2)]
+    ms = np.concatenate([O.secondary_expected(w, w["theta0"], d)[1].ravel() for d in range(2)])
+    return w, mu, ms, I.poisson_counts(np.concatenate(mu + [ms]), 71)
+
+
+def pin_secondary_by_hand():
+    """One secondary bin per slice: each slice adds the Poisson term of its total, by hand."""
+    w, mu, ms, n = _sec_small(n_sec=1)
+    p = I.perturbed_points(w["theta0"], 1, 72)[0]
+    J = [len(e) - 1 for e in w["edges"]]
+    base = O.nll(dict(w, secondary=None), p, n[:sum(J)])
+    extra, o = 0.0, sum(J)
+    for d in range(2):
+        m = O.expected_counts(w, p, d)
+        st = w["secondary"][d]["slice_start"]
+        for q in range(len(st) - 1):
+            tot, k = float(m[st[q]:st[q + 1]].sum()), n[o]
+            extra += tot - k + (k * math.log(k / tot) if k > 0 else 0.0)
+            o += 1
+    return abs(O.nll(w, p, n) - (base + extra)) / abs(base + extra)
+
+
+def test_secondary_piece_by_hand():
+    assert pin_secondary_by_hand() < 1e-13
+
+
+def pin_secondary_gradient():
+    w, mu, ms, n = _sec_small()
+    p = I.perturbed_points(w["theta0"], 1, 73, rel=0.02)[0]
+    S = w["spectra"].shape[0]
+    # a line, a beta, the peak rate, every response parameter and the peak position and width
+    which = [6, 3, 14] + list(range(S, S + 7))
+    worst = 0.0
+    for win in (None, np.array([[30, 170], [30, 170]])):
+        g = O.nll_grad(w, p, n, win)
+        gf = O.nll_grad_fd(w, p, n, win, rel=1e-4, which=which)
+        worst = max(worst, float(np.max(np.abs(g[which] - gf[which]) / (np.abs(g[which]) + 1e-3 * np.max(np.abs(g))))))
+    return worst
+
+
+def test_secondary_gradient_matches_finite_differences():
+    assert pin_secondary_gradient() < 2e-6
+
+
+def test_secondary_asimov_and_rate_identity():
+    w, mu, ms, n = _sec_small()
+    asimov = np.concatenate(mu + [ms])
+    assert O.nll(w, w["theta0"], asimov) == pytest.approx(0.0, abs=1e-9)
+    assert np.max(np.abs(O.nll_grad(w, w["theta0"], asimov))) < 1e-8
+    # mu and mu_qm are linear in the rates: sum_s r_s dNLL/dr_s = sum (mu - n) over both pieces
+    w2 = dict(w, pull_param=np.zeros(0, np.int32), pull_centre=np.zeros(0), pull_width=np.zeros(0))
+    p = I.perturbed_points(w["theta0"], 1, 74)[0]
+    g = O.nll_grad(w2, p, n)
+    S = w["spectra"].shape[0]
+    sm = np.asarray(w["slot_map"])[:, :S]
+    idx = np.unique(sm[sm >= 0])
+    rhs, o = 0.0, 400
+    for d in range(2):
+        rhs += float(np.sum(O.expected_counts(w, p, d) - n[200 * d:200 * (d + 1)]))
+        mq = O.secondary_expected(w, p, d)[1]
+        rhs += float(np.sum(mq - n[o:o + mq.size].reshape(mq.shape)))
+        o += mq.size
+    assert abs(float(np.dot(p[idx], g[idx])) - rhs) <= 1e-11 * max(1.0, abs(rhs))
+
+
+def test_secondary_slices_outside_the_window_are_dropped():
+    w, mu, ms, n = _sec_small()
+    p = I.perturbed_points(w["theta0"], 1, 75)[0]
+    st = w["secondary"][0]["slice_start"]
+    # a window from the middle of slice 1 to the end of slice 3: slices 2 and 3 only
+    win = np.array([[st[1] + 5, st[4]], [st[1] + 5, st[4]]])
+    plain = O.nll(dict(w, secondary=None), p, n[:400], win)
+    extra, o = 0.0, 400
+    for d in range(2):
+        mq = O.secondary_expected(w, p, d)[1]
+        nq = n[o:o + mq.size].reshape(mq.shape)
+        extra += float(np.sum(O.poisson_term(mq[2:4], nq[2:4])))
+        o += mq.size
+    assert abs(O.nll(w, p, n, win) - (plain + extra)) <= 1e-12 * abs(plain + extra)
+
+
+SEC_MUTANTS = {
+    "shapes not normalised": ("secondary_shapes", lambda work, d: np.asarray(work["secondary"][d]["shapes"], np.float64)),
+    "slice includes its upper boundary bin": ("_active_slices", lambda work, d, lo, hi: [
+        q for q in range(len(work["secondary"][d]["slice_start"]) - 1)
+        if work["secondary"][d]["slice_start"][q] >= lo and work["secondary"][d]["slice_start"][q + 1] <= hi + 1]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SEC_MUTANTS))
+def test_planted_secondary_mistake_is_caught(monkeypatch, name):
+    attr, fn = SEC_MUTANTS[name]
+    monkeypatch.setattr(O, attr, fn)
+    caught = []
+    for pin, tol in ((pin_secondary_by_hand, 1e-13), (pin_secondary_gradient, 2e-6)):
+        try:
+            caught.append(pin() > tol)
+        except Exception:
+            caught.append(True)
+    try:
+        w, mu, ms, n = _sec_small()
+        st = w["secondary"][0]["slice_start"]
+        win = np.array([[0, st[4] - 1], [0, st[4] - 1]])
+        p = w["theta0"]
+        got = O.nll(w, p, n, win)
+        ref = O.nll(dict(w, secondary=None), p, n[:400], win)
+        extra, o = 0.0, 400
+        for d in range(2):
+            Pn = np.asarray(w["secondary"][d]["shapes"], np.float64)
+            Pn = Pn / Pn.sum(axis=2, keepdims=True)
+            m = O.expected_per_species(w, p, d)
+            for q in range(3):
+                Nq = m[st[q]:st[q + 1]].sum(axis=0)
+                mq = Nq @ Pn[:, q, :]
+                extra += float(np.sum(O.poisson_term(mq, n[o + q * 8:o + q * 8 + 8])))
+            o += 5 * 8
+        caught.append(abs(got - (ref + extra)) > 1e-10 * abs(ref + extra))
+    except Exception:
+        caught.append(True)
+    assert any(caught), f"no pin caught the planted mistake '{name}'"
