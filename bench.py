@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mv-toys", type=int, default=1024, help="toys of the multivariate workload")
     ap.add_argument("--fit-toys", type=int, default=1024, help="toys of the discovery-test workload")
+    ap.add_argument("--secondary", default=None, metavar="QxM",
+                    help="toys workload with a secondary observable on both datasets: Q energy slices with "
+                         "M secondary bins each (section 2.4 multivariate pieces), e.g. 8x16")
     ap.add_argument("--power", type=float, default=None,
                     help="toys workload with the generalized-gamma response of this free power p instead of "
                          "the gamma response (p is a 24th parameter, perturbed per toy like the others)")
@@ -79,9 +82,11 @@ def parse():
 
 
 # ------------------------------------------------------------ inputs -------
-def make_inputs(n_toys, seed0, power=None):
+def make_inputs(n_toys, seed0, power=None, secondary=None):
     """Toys of the 1200-bin workload; with a power p, the generalized-gamma response (the counts are
-    still drawn from the gamma response's expectation: only the model evaluated differs)."""
+    still drawn from the gamma response's expectation: only the model evaluated differs).  With a
+    secondary observable ("QxM"), each toy also carries the secondary histograms, drawn from their
+    expectation at theta0 (per-species slice sums of the FP64 GPU path's expected counts)."""
     import numpy as np
 
     from paper_1812_05686_gb300 import inputs as I
@@ -89,7 +94,22 @@ def make_inputs(n_toys, seed0, power=None):
     if power is not None:
         w = I.with_power(w, power)
     mu0 = np.loadtxt(os.path.join(ROOT, "tests", "golden", "borexino_like_1200_mu0.txt"))
-    b = I.toy_batch(w, [mu0[:1200], mu0[1200:]], n_toys=n_toys, seed0=seed0)
+    ms = None
+    if secondary is not None:
+        from paper_1812_05686_gb300 import gsn
+        Q, M = (int(v) for v in secondary.lower().split("x"))
+        w = I.with_secondary(w, n_slices=Q, n_sec=M)
+        ctx = gsn.context_from_workload(w, gsn.GSN_FP64)
+        parts = []
+        for d in range(2):
+            per = ctx.expected(w["theta0"], d)
+            x = w["secondary"][d]
+            st, P = x["slice_start"], np.asarray(x["shapes"], np.float64)
+            P = P / P.sum(axis=2, keepdims=True)
+            N = np.stack([per[st[q]:st[q + 1]].sum(axis=0) for q in range(Q)], axis=1)
+            parts.append(np.einsum("sq,sqm->qm", N, P).ravel())
+        ms = np.concatenate(parts)
+    b = I.toy_batch(w, [mu0[:1200], mu0[1200:]], n_toys=n_toys, seed0=seed0, mu_sec=ms)
     return w, b
 
 
@@ -266,8 +286,9 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     T = args.toys
-    w, b = make_inputs(T, 1000 + rank * T, args.power)
+    w, b = make_inputs(T, 1000 + rank * T, args.power, args.secondary)
     gg = args.power is not None
+    sec = args.secondary is not None
     # a dedicated stream: the library launches on it and the timing events are recorded on it
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
@@ -363,13 +384,13 @@ def run_ours(args, rank, world, local_rank):
     dom = max(("forward", "backward"), key=lambda k: prof[k][0])
     kms, kn, kunits = prof[dom]
     per_launch_s = kms * 1e-3 / max(kn, 1)
-    flops = kunits / max(kn, 1) * (FLOP_PER_PAIR_GG if gg else FLOP_PER_PAIR)[dom]
+    flops = kunits / max(kn, 1) * (FLOP_PER_PAIR_GG if gg else FLOP_PER_PAIR)[dom] if kunits else 0.0
     sm_mhz = clk.get("sm_mhz") or 1455.0
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = nsm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
     achieved = flops / per_launch_s
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None if gg else ncu_traffic(dom), "kernel": dom,
+            "frac": achieved / peak, "traffic": None if (gg or sec) else ncu_traffic(dom), "kernel": dom,
             "peak_basis": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock {sm_mhz:.0f} MHz",
             "pairs_per_launch": kunits / max(kn, 1), "ms_per_launch": per_launch_s * 1e3}
 
@@ -383,9 +404,10 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32 (f64 deviance and reductions)", "data": "synthetic",
-                "config": {"workload": WORKLOAD if not gg else
+                "config": {"workload": (WORKLOAD if not gg else
                            WORKLOAD.replace("gamma response, 23 params",
-                                            f"generalized-gamma response of free power p = {args.power:g}, 24 params"),
+                                            f"generalized-gamma response of free power p = {args.power:g}, 24 params"))
+                           + (f"; secondary observable {args.secondary} (slices x bins) per dataset" if sec else ""),
                            "toys_per_gpu": T, "fine_points": 20000, "bins": 1200,
                            "species": 16, "precision": "mixed",
                            "l2": "inputs and scratch per step (GBs) exceed the 129 MB L2"},

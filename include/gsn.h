@@ -208,6 +208,33 @@ int gsn_set_dataset_factors(gsn_ctx* ctx, int n_datasets, int n_species, const d
  * Errors: GSN_ERR_ARG, GSN_ERR_STATE. */
 int gsn_set_template(gsn_ctx* ctx, int species, int dataset, const double* hist);
 
+/* Secondary observable of a dataset (section 2.4 multivariate fit: the extra
+ * likelihood pieces of a second observable, e.g. a pulse-shape or radial
+ * variable).  The dataset's energy bins form n_slices contiguous slices; each
+ * slice carries a histogram of the second observable in n_sec bins.  Species s
+ * contributes to slice q its expected counts N_sq (the sum of its expected
+ * energy-bin counts over the slice), spread over the secondary bins by the
+ * fixed shape P_sqm; every slice lying inside the dataset's fit window adds
+ *     sum_m [mu_qm - n_qm + n_qm ln(n_qm / mu_qm)],  mu_qm = sum_s N_sq P_sqm
+ * to the NLL (its events also populate the energy histogram: the pieces are
+ * added, not conditioned).
+ *   slice_start  [n_slices + 1] ascending energy-bin boundaries in [0, n_bins[d]]:
+ *                slice q = bins [slice_start[q], slice_start[q+1])
+ *   shapes       [n_species][n_slices][n_sec] >= 0; the library normalises every
+ *                (s, q) row to unit sum (a zero row: no contribution); NULL removes
+ *                the dataset's secondary observable
+ *   counts       [n_slices][n_sec] observed counts for single-point calls (NULL: 0)
+ * A toy's counts row (the batch calls and the minimiser) then holds gsn_n_counts
+ * values: the energy bins of every dataset, then the secondary bins of every
+ * dataset that has them (datasets, slices and secondary bins in ascending order).
+ * Call after gsn_set_data and gsn_set_species (which clear it).  Not taken by
+ * gsn_eval_grad_noalloc.  Errors: GSN_ERR_ARG, GSN_ERR_STATE. */
+int gsn_set_secondary(gsn_ctx* ctx, int dataset, int n_slices, const int* slice_start, int n_sec,
+                      const double* shapes, const double* counts);
+
+/* Values in a toy's counts row: sum_d n_bins[d] plus every secondary histogram. */
+int gsn_n_counts(gsn_ctx* ctx);
+
 /* NLL at params[n_params] with the counts and windows of gsn_set_data.
  * Keeps the per-species shapes of every response group (section 2.5 value
  * cache, shared with gsn_expected) and recomputes them only when a response
@@ -220,7 +247,7 @@ int gsn_eval_grad(gsn_ctx* ctx, const double* params, double* nll, double* grad)
 
 /* Batched pseudo-experiments: each toy has its own parameters, counts and windows.
  *   params      [n_toys][n_params]
- *   toy_counts  [n_toys][sum_d n_bins[d]] (datasets concatenated)
+ *   toy_counts  [n_toys][gsn_n_counts(ctx)]: energy bins (datasets concatenated), then any secondary bins
  *   toy_win     [n_toys][n_datasets][2] window [lo, hi) per toy and dataset
  *   nll         [n_toys]
  *   grad        [n_toys][n_params], or NULL for the NLL only

@@ -45,16 +45,21 @@ struct gsn_ctx {
                                       // the power of the generalized gamma is not scaled)
     std::vector<double> rfrac;        // [D][S] rate fraction of each species in each dataset
     std::map<std::pair<int, int>, std::vector<double>> tpl;  // (dataset, species) -> normalised template
+    // secondary observable per dataset (section 2.4 multivariate pieces)
+    struct Sec { std::vector<int> start; int Q = 0, M = 0; std::vector<double> P, counts; };
+    std::map<int, Sec> sec;
     std::vector<int> pull_p;
     std::vector<double> pull_c, pull_w;
     bool have_data = false, have_species = false, have_params = false, ready = false;
     // derived
     int G = 0, total_bins = 0, Jmax = 0;
+    int n_counts = 0;                 // values per toy counts row: energy bins, then secondary bins
     KArgs base{};
     Tables tab{};                     // host copy of the device problem tables
     // persistent device buffers
     std::vector<Buf> owned;
     // scratch
+    Buf MbufT, secN_b, secV_b, secW_b, secpart_b, secU_b;  // per-toy buffers of the secondary pieces
     Buf colbuf, colbuf2, blkbuf, mubuf, wbuf, partbuf, gdirect, devbuf, params, counts_b, win_b, nll_b, grad_b, status_b, Mbuf,
         outbuf;
     unsigned long long scratch_gen = 0;  // bumped whenever a buffer is (re)allocated
@@ -423,12 +428,49 @@ int finalize(gsn_ctx* c) {
     if ((rc = upload(c, c->pull_c, &a.pull_c))) return rc;
     if ((rc = upload(c, c->pull_w, &a.pull_w))) return rc;
     // default counts and windows (single-point calls)
+    // secondary observables: per-dataset and per-slice tables, bin -> slice map
+    {
+        std::vector<int> sds, snq, sM, sq0, scoff, sqlo, sqhi, sqsec, sslice(c->total_bins, -1);
+        std::vector<long long> spoff;
+        std::vector<double> sP;
+        int Qtot = 0, nb = 0;
+        for (const auto& kv : c->sec) {
+            const int d = kv.first;
+            const gsn_ctx::Sec& x = kv.second;
+            const int i = (int)sds.size();
+            sds.push_back(d); snq.push_back(x.Q); sM.push_back(x.M); sq0.push_back(Qtot); scoff.push_back(nb);
+            spoff.push_back((long long)sP.size());
+            sP.insert(sP.end(), x.P.begin(), x.P.end());
+            for (int q = 0; q < x.Q; ++q) {
+                sqlo.push_back(x.start[q]); sqhi.push_back(x.start[q + 1]); sqsec.push_back(i);
+                for (int j = x.start[q]; j < x.start[q + 1]; ++j) sslice[tb.ds_off[d] + j] = Qtot + q;
+            }
+            Qtot += x.Q;
+            nb += x.Q * x.M;
+        }
+        a.nsec = (int)sds.size(); a.Qtot = Qtot; a.nsecb = nb;
+        c->n_counts = c->total_bins + nb;
+        if (a.nsec) {
+            if ((rc = upload(c, sds, &a.sec_ds))) return rc;
+            if ((rc = upload(c, snq, &a.sec_nq))) return rc;
+            if ((rc = upload(c, sM, &a.sec_M))) return rc;
+            if ((rc = upload(c, sq0, &a.sec_q0))) return rc;
+            if ((rc = upload(c, scoff, &a.sec_coff))) return rc;
+            if ((rc = upload(c, spoff, &a.sec_poff))) return rc;
+            if ((rc = upload(c, sP, &a.sec_P))) return rc;
+            if ((rc = upload(c, sqlo, &a.sq_lo))) return rc;
+            if ((rc = upload(c, sqhi, &a.sq_hi))) return rc;
+            if ((rc = upload(c, sqsec, &a.sq_sec))) return rc;
+            if ((rc = upload(c, sslice, &a.sec_slice))) return rc;
+        }
+    }
     std::vector<double> cnt;
     std::vector<int> win;
     for (int d = 0; d < c->D; ++d) {
         cnt.insert(cnt.end(), c->counts[d].begin(), c->counts[d].end());
         win.push_back(c->wlo[d]); win.push_back(c->whi[d]);
     }
+    for (const auto& kv : c->sec) cnt.insert(cnt.end(), kv.second.counts.begin(), kv.second.counts.end());
     const double* dc; const int* dw;
     if ((rc = upload(c, cnt, &dc))) return rc;
     if ((rc = upload(c, win, &dw))) return rc;
@@ -454,6 +496,15 @@ int reserve(gsn_ctx* c, int T, const Plan& p) {
     if ((rc = ensure(c, c->partbuf, (size_t)T * c->G * p.nbtask * npart * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->gdirect, (size_t)T * c->P * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->devbuf, (size_t)T * p.dev_chunks * (2 + c->base.ntpl) * sizeof(double)))) return rc;
+    const KArgs& b = c->base;
+    if (b.nsec) {
+        if ((rc = ensure(c, c->MbufT, (size_t)T * c->G * c->S * c->Jmax * sizeof(double)))) return rc;
+        if ((rc = ensure(c, c->secN_b, (size_t)T * b.Qtot * c->S * sizeof(double)))) return rc;
+        if ((rc = ensure(c, c->secV_b, (size_t)T * b.Qtot * c->S * sizeof(double)))) return rc;
+        if ((rc = ensure(c, c->secW_b, (size_t)T * b.nsecb * sizeof(double)))) return rc;
+        if ((rc = ensure(c, c->secpart_b, (size_t)T * b.nsec * (2 + b.NSLOT) * sizeof(double)))) return rc;
+        if ((rc = ensure(c, c->secU_b, (size_t)T * b.Qtot * c->K * rs))) return rc;
+    }
     return GSN_OK;
 }
 
@@ -467,6 +518,12 @@ void fill(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
     a.colbuf = c->colbuf.p; a.colbuf2 = (double*)c->colbuf2.p; a.blkbuf = c->blkbuf.p; a.mubuf = (double*)c->mubuf.p;
     a.wbuf = c->wbuf.p; a.partbuf = (double*)c->partbuf.p; a.gdirect = (double*)c->gdirect.p;
     a.devpart = (double*)c->devbuf.p;
+    if (a.nsec) {
+        a.Mbuf = (double*)c->MbufT.p; a.mstride = (long long)c->G * c->S * c->Jmax;
+        a.secN = (double*)c->secN_b.p; a.secV = (double*)c->secV_b.p; a.secW = (double*)c->secW_b.p;
+        a.secpart = (double*)c->secpart_b.p; a.secU = c->secU_b.p;
+        a.sp_first = 0; a.sp_count = c->S;
+    }
 }
 
 int prepare(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
@@ -522,6 +579,28 @@ int launch(gsn_ctx* c, int kernel, KArgs& a, F fn) {
 
 int run_step(gsn_ctx* c, KArgs& a, bool grad) {
     int rc;
+    if (a.nsec) {
+        // secondary observable: per-species shapes per toy (their slice sums feed the extra pieces),
+        // mu from them, the pieces, then the energy deviance; the adjoint adds the pieces' weights
+        if (a.response) {
+            if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
+            if ((rc = launch(c, K_FORWARD, a, launch_species))) return rc;
+        } else {
+            CUDA_TRY(c, cudaMemsetAsync(a.Mbuf, 0, (size_t)a.T * a.mstride * sizeof(double), c->stream));
+        }
+        if ((rc = launch(c, K_MU, a, launch_mu_from_species))) return rc;
+        if ((rc = launch(c, K_SPECIES, a, launch_secondary))) return rc;
+        if ((rc = launch(c, K_DEVIANCE, a, launch_deviance))) return rc;
+        if ((rc = launch(c, K_DEVFINAL, a, launch_devfinal))) return rc;
+        if (grad) {
+            if (a.response) {
+                if ((rc = launch(c, K_BACKWARD, a, launch_secondary_weights))) return rc;
+                if ((rc = launch(c, K_BACKWARD, a, launch_backward))) return rc;
+            }
+            if ((rc = launch(c, K_GRADFINAL, a, launch_gradfinal))) return rc;
+        }
+        return GSN_OK;
+    }
     if (a.response) {  // a fit of templates and peaks only has no response to build
         if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
         if ((rc = launch(c, K_FORWARD, a, launch_forward))) return rc;
@@ -575,6 +654,11 @@ int choose_plan(gsn_ctx* c, int T, KArgs a, bool grad, Plan& out) {
     if (it != c->tuned.end()) { out = it->second; return GSN_OK; }
     const Plan h = heuristic_plan(c, T);
     out = h;
+    if (c->base.nsec) {  // mu comes from the per-species shapes: one column range, heuristic adjoint split
+        out = plan_with(c, T, 1, h.bw_warps, h.bw_bsplit);
+        c->tuned[key] = out;
+        return GSN_OK;
+    }
     if (stream_capturing(c)) return GSN_OK;  // no timing inside a caller's capture
     if (!c->opt.autotune || !c->base.response || (h.nsplit == 1 && h.bw_bsplit == 1)) { c->tuned[key] = h; return GSN_OK; }
     const cudaStream_t st = c->stream;
@@ -696,7 +780,7 @@ int batch_device(gsn_ctx* c, int n_toys, const double* params, const double* cou
         const int T = std::min(chunk, n_toys - t0);
         KArgs a = c->base;
         a.params = params + (size_t)t0 * c->P; a.params_stride = c->P;
-        a.counts = counts + (size_t)t0 * c->total_bins; a.counts_stride = c->total_bins;
+        a.counts = counts + (size_t)t0 * c->n_counts; a.counts_stride = c->n_counts;
         a.win = win + (size_t)t0 * c->D * 2; a.win_stride = 2 * c->D;
         a.nll = nll + t0;
         a.grad = grad ? grad + (size_t)t0 * c->P : nullptr;
@@ -785,7 +869,8 @@ void gsn_destroy(gsn_ctx* c) {
     free_owned(c);
     for (Buf* b : {&c->fit_ws, &c->fit_cfg, &c->fit_eval, &c->fit_ist})
         if (b->p) cudaFree(b->p);
-    for (Buf* b : {&c->colbuf, &c->colbuf2, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
+    for (Buf* b : {&c->MbufT, &c->secN_b, &c->secV_b, &c->secW_b, &c->secpart_b, &c->secU_b,
+                   &c->colbuf, &c->colbuf2, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
                    &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf, &c->s_hi, &c->s_lo,
                    &c->tc_part, &c->tc_err})
         if (b->p) cudaFree(b->p);
@@ -888,7 +973,7 @@ int gsn_set_data(gsn_ctx* c, int n_datasets, const int* n_bins, const double* co
     }
     if (c->have_species && n_datasets != c->D) c->have_species = c->have_params = false;
     if (n_datasets != c->D) { c->rscale.clear(); c->rfrac.clear(); }
-    if (n_datasets != c->D || nb != c->nb) c->tpl.clear();
+    if (n_datasets != c->D || nb != c->nb) { c->tpl.clear(); c->sec.clear(); }
     c->D = n_datasets; c->nb = nb; c->edges = ed; c->counts = cn; c->eps = ex; c->wlo = lo; c->whi = hi;
     c->have_data = true;
     c->ready = false;
@@ -939,6 +1024,7 @@ int gsn_set_species(gsn_ctx* c, int n_species, int n_fine, const double* fine_ce
     }
     if (n_species != c->S) c->rfrac.clear();
     c->tpl.clear();
+    c->sec.clear();
     c->S = n_species; c->K = n_fine; c->E = E; c->Sn = Sn; c->kind = kd;
     c->mask.assign(dataset_mask, dataset_mask + (size_t)n_species * c->D);
     c->have_species = true;
@@ -979,6 +1065,51 @@ int gsn_set_params(gsn_ctx* c, int n_params, const int* slot_map, int n_pulls, c
     c->have_params = true;
     c->ready = false;
     return GSN_OK;
+}
+
+int gsn_set_secondary(gsn_ctx* c, int dataset, int n_slices, const int* slice_start, int n_sec,
+                      const double* shapes, const double* counts) {
+    if (!c) return GSN_ERR_ARG;
+    if (!c->have_data || !c->have_species)
+        return fail(c, GSN_ERR_STATE, "gsn_set_data and gsn_set_species must come before a secondary observable");
+    if (dataset < 0 || dataset >= c->D) return fail(c, GSN_ERR_ARG, "dataset out of range");
+    c->ready = false;
+    if (!shapes) { c->sec.erase(dataset); return GSN_OK; }
+    if (n_slices < 1 || n_sec < 1 || !slice_start) return fail(c, GSN_ERR_ARG, "n_slices and n_sec must be >= 1");
+    gsn_ctx::Sec x;
+    x.Q = n_slices; x.M = n_sec;
+    x.start.assign(slice_start, slice_start + n_slices + 1);
+    for (int q = 0; q <= n_slices; ++q)
+        if (x.start[q] < 0 || x.start[q] > c->nb[dataset] || (q && x.start[q] < x.start[q - 1]))
+            return fail(c, GSN_ERR_ARG, "slice_start must ascend within the dataset's bins");
+    const size_t nP = (size_t)c->S * n_slices * n_sec;
+    x.P.assign(shapes, shapes + nP);
+    for (int sp = 0; sp < c->S; ++sp)
+        for (int q = 0; q < n_slices; ++q) {
+            double* row = x.P.data() + ((size_t)sp * n_slices + q) * n_sec;
+            double tot = 0.0;
+            for (int m = 0; m < n_sec; ++m) {
+                if (!(row[m] >= 0.0) || !std::isfinite(row[m])) return fail(c, GSN_ERR_ARG, "shapes must be finite and >= 0");
+                tot += row[m];
+            }
+            for (int m = 0; m < n_sec; ++m) row[m] = tot > 0.0 ? row[m] / tot : 0.0;
+        }
+    x.counts.assign((size_t)n_slices * n_sec, 0.0);
+    if (counts)
+        for (size_t i = 0; i < x.counts.size(); ++i) {
+            if (!(counts[i] >= 0.0) || !std::isfinite(counts[i])) return fail(c, GSN_ERR_ARG, "counts must be finite and >= 0");
+            x.counts[i] = counts[i];
+        }
+    c->sec[dataset] = x;
+    return GSN_OK;
+}
+
+int gsn_n_counts(gsn_ctx* c) {
+    if (!c) return GSN_ERR_ARG;
+    int n = 0;
+    for (int d = 0; d < c->D; ++d) n += c->nb[d];
+    for (const auto& kv : c->sec) n += kv.second.Q * kv.second.M;
+    return n;
 }
 
 int gsn_set_template(gsn_ctx* c, int species, int dataset, const double* hist) {
@@ -1175,7 +1306,9 @@ int gsn_eval(gsn_ctx* c, const double* params, double* nll) {
     a.Mbuf = (double*)c->Mbuf.p;
     a.nll = (double*)c->nll_b.p; a.grad = nullptr; a.status = (int*)c->status_b.p;
     a.want_grad = 0;
+    a.Mbuf = (double*)c->Mbuf.p;  // the cached shapes (one parameter point)
     if ((rc = launch(c, K_MU, a, launch_mu_from_species))) return rc;
+    if (a.nsec && (rc = launch(c, K_SPECIES, a, launch_secondary))) return rc;
     if ((rc = launch(c, K_DEVIANCE, a, launch_deviance))) return rc;
     if ((rc = launch(c, K_DEVFINAL, a, launch_devfinal))) return rc;
     int st = 0;
@@ -1313,13 +1446,13 @@ int gsn_eval_grad_batch(gsn_ctx* c, int n_toys, const double* params, const doub
     }
     const size_t TB = (size_t)n_toys;
     if ((rc = ensure(c, c->params, TB * c->P * sizeof(double)))) return rc;
-    if ((rc = ensure(c, c->counts_b, TB * c->total_bins * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->counts_b, TB * c->n_counts * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->win_b, TB * c->D * 2 * sizeof(int)))) return rc;
     if ((rc = ensure(c, c->nll_b, TB * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->grad_b, TB * c->P * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->status_b, TB * sizeof(int)))) return rc;
     CUDA_TRY(c, cudaMemcpyAsync(c->params.p, params, TB * c->P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->counts_b.p, toy_counts, TB * c->total_bins * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->counts_b.p, toy_counts, TB * c->n_counts * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->win_b.p, toy_win, TB * c->D * 2 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     if ((rc = batch_device(c, n_toys, (const double*)c->params.p, (const double*)c->counts_b.p, (const int*)c->win_b.p,
                            (double*)c->nll_b.p, grad ? (double*)c->grad_b.p : nullptr, (int*)c->status_b.p)))
@@ -1373,6 +1506,8 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     if (!params_dev || !nll_dev || !grad_dev) return fail(c, GSN_ERR_ARG, "NULL device pointer");
     if (!c->ready)
         return fail(c, GSN_ERR_STATE, "the problem is not on the device yet: call gsn_eval or gsn_eval_grad once first");
+    if (c->base.nsec)
+        return fail(c, GSN_ERR_ARG, "the no-allocation entry point does not take secondary observables");
     std::string err;
     unsigned char* base = static_cast<unsigned char*>(noalloc_address(c->dev, err));
     if (!base) return fail(c, GSN_ERR_CUDA, err);

@@ -139,11 +139,32 @@ struct KArgs {
     int* status;
     int want_grad;
     // per-species path (eval with response cache, expected counts)
-    double* Mbuf;          // [G][S][J_g max]
+    double* Mbuf;          // [T][G][S][J_g max] (toy stride mstride)
+    long long mstride;
     int Jmax;
     int sp_first, sp_count;
     double* out_species;   // [J][S] for gsn_expected
     int out_dataset, out_bins;
+    // secondary observable (section 2.4 multivariate pieces); nsec = 0: none
+    int nsec;              // datasets with a secondary observable
+    int Qtot;              // their slices
+    int nsecb;             // their secondary bins: a toy's counts row holds total_bins + nsecb values
+    const int* sec_ds;     // [nsec] dataset
+    const int* sec_nq;     // [nsec] slices
+    const int* sec_M;      // [nsec] secondary bins per slice
+    const int* sec_q0;     // [nsec] first global slice
+    const int* sec_coff;   // [nsec] offset of its secondary counts after the energy bins
+    const long long* sec_poff;  // [nsec] offset of its normalised shapes [S][Q][M] in sec_P
+    const double* sec_P;
+    const int* sq_lo;      // [Qtot] energy-bin range [lo, hi) of every slice in its dataset
+    const int* sq_hi;
+    const int* sq_sec;     // [Qtot] secondary dataset index of the slice
+    const int* sec_slice;  // [total_bins] global slice of every energy bin, -1 outside the slices
+    double* secN;          // [T][Qtot][S] unscaled per-species slice sums
+    double* secV;          // [T][Qtot][S] dNLL / dN_sq per unit rate coefficient
+    double* secW;          // [T][nsecb] 1 - n/mu of every secondary bin
+    double* secpart;       // [T][nsec][2 + NSLOT] NLL piece, flags, slot gradient
+    void* secU;            // [T][Qtot][K] of Real: adjoint weight of the secondary pieces
     // statistics: evaluated (bin, column) pairs per kernel class (NULL = off)
     unsigned long long* work;
     // tensor-core per-species contraction
@@ -195,6 +216,8 @@ size_t species_tc_smem_bytes();
 cudaError_t launch_species_tc(const KArgs& a, const void* tm_hi, const void* tm_lo, cudaStream_t st);
 int make_species_tensor_map(void* out, const float* dev, int rows, int cols_pad);
 cudaError_t launch_backward_mixed(const KArgs& a, cudaStream_t st);
+cudaError_t launch_secondary(const KArgs& a, cudaStream_t st);
+cudaError_t launch_secondary_weights(const KArgs& a, cudaStream_t st);
 
 constexpr int K_COLUMNS = 0, K_FORWARD = 1, K_DEVIANCE = 2, K_BACKWARD = 3, K_GRADFINAL = 4,
               K_SPECIES = 5, K_MU = 6, K_DEVFINAL = 7, K_COUNT = 8;

@@ -626,6 +626,19 @@ __global__ void __launch_bounds__(256) k_devfinal(KArgs a) {
                     gdir[p] += a.rfac[d * a.S + s] * g;
                 }
         }
+        // secondary-observable pieces (section 2.4): NLL, flags and slot gradients per dataset
+        for (int i = 0; i < a.nsec; ++i) {
+            const double* sp = a.secpart + ((long long)t * a.nsec + i) * (2 + a.NSLOT);
+            nll += sp[0];
+            flags |= (int)sp[1];
+            if (a.want_grad) {
+                const int d = a.sec_ds[i];
+                for (int sl = 0; sl < a.NSLOT; ++sl) {
+                    const int p = a.slot_map[d * a.NSLOT + sl];
+                    if (p >= 0 && sp[2 + sl] != 0.0) gdir[p] += sp[2 + sl];
+                }
+            }
+        }
         for (int i = 0; i < a.n_pulls; ++i) {
             const int p = a.pull_param[i];
             const double z = (prm[p] - a.pull_c[i]) / a.pull_w[i];
@@ -693,6 +706,17 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     const R* wv[MAXGDS];
     for (int dd = 0; dd < MAXGDS; ++dd)
         wv[dd] = reinterpret_cast<const R*>(a.wbuf) + (long long)t * a.total_bins + tb_ds_off(a, tb_g_ds(a, g, dd < nds ? dd : 0));
+    // secondary pieces: bin j of slice q adds U_qk N_k to the pair's weight (per dataset of the group)
+    const R* secU = a.nsec ? reinterpret_cast<const R*>(a.secU) + (long long)t * a.Qtot * a.K : nullptr;
+    auto sec_weight = [&](int j) -> R {
+        R u = 0;
+        if (secU && kval)
+            for (int dd = 0; dd < nds; ++dd) {
+                const int q = a.sec_slice[tb_ds_off(a, tb_g_ds(a, g, dd)) + j];
+                if (q >= 0) u += secU[(long long)q * a.K + k];
+            }
+        return u * c[F_N];
+    };
     R U0[MAXGDS] = {0, 0, 0};
     R U1 = 0, U2 = 0;
     // generalized gamma: W-weighted node sums (rho, S1, S2, S3; compensated in FP32) and the W of
@@ -709,6 +733,7 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
                 wj[dd] = dd < nds ? wv[dd][j] : R(0);
                 Wj = fma(wj[dd], c[F_TN0 + dd], Wj);
             }
+            if (secU) Wj += sec_weight(j);
             const unsigned char cls = a.bclass[nbase + j];
             R rho = 0;
             if (cls == BIN_ZERO) {
@@ -769,6 +794,7 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
 #pragma unroll
                 for (int dd = 0; dd < MAXGDS; ++dd)
                     if (dd < nds) { const double w = wv[dd][j]; U0[dd] = fma(w, Rv, U0[dd]); Wj = fma(w, c[F_TN0 + dd], Wj); }
+                if (secU) Wj += sec_weight(j);
                 // d R / d mu = U1 / sigma, d R / d sigma = U2 / sigma (applied per column below)
                 U1 = fma(Wj, -(ph - pp), U1);
                 U2 = fma(Wj, -(z * ph - zp * pp), U2);
@@ -784,6 +810,7 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
                 wj[dd] = dd < nds ? wv[dd][j] : R(0);
                 Wj = fma(wj[dd], c[F_TN0 + dd], Wj);
             }
+            if (secU) Wj += sec_weight(j);
             const unsigned char cls = a.bclass[nbase + j];
             R rho = 0;
             if (RES == 1 && cls == BIN_ZERO) {
@@ -799,25 +826,34 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
                     float Z1 = 0.f, Z2 = 0.f;
                     for (int n = 0; n < NG; ++n) {
                         const float zn = fmaf(nd[n], c[F_A], z);
-                        const float fw = nd[2 * NGM_F + n] * ex2f(-0.5f * L2E * zn * zn);
+                        const float qn = zn * zn;
+                        const float fw = nd[2 * NGM_F + n] * ex2f(-fmaf(0.5f * L2E, qn, qn * HALF_L2E_LO));
                         rho += fw; Z1 = fmaf(fw, zn, Z1); Z2 = fmaf(fw, fmaf(zn, zn, -1.0f), Z2);
                     }
                     U1 = fmaf(Wj, Z1, U1);
                     U2 = fmaf(Wj, Z2, U2);
                 } else {
-                    const float tt = Dx * c[F_A];
+                    // the mixed gamma record (B = d, C = -1/s, KAPPA = ln d - psi(d)): sums of
+                    // (mu/d) d ln f/d mu at fixed variance and s^2 d ln f/d var at fixed mean per node
+                    const float A = c[F_A];
+                    const float tt = Dx * A;
                     float L1;
                     const float Dt = log1pmx2_f(tt, L1);
-                    const float B2 = L2E * (c[F_B] - 1.0f), C2 = L2E * c[F_C];
-                    const float Ec = fmaf(L2E * c[F_B], Dt, -L2E * L1);
-                    float L = 0.f, X = 0.f;
+                    const float P2 = mul_l2e(c[F_B]), Q2 = fmaf(L2E, c[F_B], fmaf(L2E_LO, c[F_B] - 1.0f, -L2E));
+                    const float R2 = mul_l2e(c[F_C]);
+                    const float Ec = fmaf(P2, Dt, -L2E * L1);
+                    const float kap = c[F_KAPPA];
+                    float u1 = 0.f, u2 = 0.f;
                     for (int n = 0; n < NG; ++n) {
-                        const float fw = nd[2 * NGM_F + n] * ex2f(Ec + fmaf(C2, nd[n], B2 * nd[NGM_F + n]));
-                        rho += fw; L = fmaf(fw, nd[NGM_F + n], L); X = fmaf(fw, nd[n], X);
+                        const float fw = nd[2 * NGM_F + n] * ex2f(Ec + fmaf(R2, nd[n], Q2 * nd[NGM_F + n]));
+                        const float L1n = L1 + nd[NGM_F + n];
+                        const float tn = fmaf(nd[n], A, tt);
+                        rho += fw;
+                        u1 = fmaf(fw, fmaf(2.0f, L1n + kap, -tn), u1);
+                        u2 = fmaf(fw, -((L1n - tn) + kap), u2);
                     }
-                    const float tau = L1 + c[F_KAPPA];
-                    U1 = fmaf(Wj, fmaf(tau, rho, L), U1);
-                    U2 = fmaf(Wj, fmaf(Dx, rho, X), U2);
+                    U1 = fmaf(Wj, u1, U1);
+                    U2 = fmaf(Wj, u2, U2);
                 }
             } else {
                 // FP64 gamma: f = exp((d-1) ln x - x/s + A); df/dd = f (ln x - ln s - psi(d)); df/ds = f (x - mu)/s^2
@@ -858,8 +894,11 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
         } else if constexpr (RES == 0) {
             g_mu = U1 * c[F_A];
             g_var = R(0.5) * U2 * c[F_A] * c[F_A];
+        } else if constexpr (sizeof(R) == 4) {
+            g_mu = U1 * (c[F_B] * c[F_A]);     // (d / mu) U1
+            g_var = U2 * (c[F_C] * c[F_C]);    // U2 / s^2
         } else {
-            // mixed: B = d, C = -1/s; fp64: C = 1/s, d = mu / s
+            // fp64: C = 1/s, d = mu / s
             const R d = sizeof(R) == 4 ? c[F_B] : mu * c[F_C];
             const R s = sizeof(R) == 4 ? R(-1) / c[F_C] : R(1) / c[F_C];
             const R var = d * s * s;
@@ -961,13 +1000,13 @@ __global__ void __launch_bounds__(128) k_gradfinal(KArgs a) {
 // ---------------------------------------------------- per-species path -----
 // M[g][s][j] = sum_k R_jk S'_sk for species s in [sp_first, sp_first + sp_count)
 template <class R, int RES, int NG>
-DEV void species_loop(const KArgs& a, int g, float xlo_w, float xhi_w, bool valid, bool is_zero,
+DEV void species_loop(const KArgs& a, int t, int g, float xlo_w, float xhi_w, bool valid, bool is_zero,
                       const R* nodes, R xc, double* accd, int nsp) {
     R del[NG], lam[NG], wt[NG];
     constexpr int NGM = sizeof(R) == 4 ? NGM_F : NGM_D;
 #pragma unroll
     for (int n = 0; n < NG; ++n) { del[n] = nodes[n]; lam[n] = nodes[NGM + n]; wt[n] = valid ? nodes[2 * NGM + n] : R(0); }
-    const R* blk = reinterpret_cast<const R*>(a.blkbuf) + (long long)g * a.nblk * 2;
+    const R* blk = reinterpret_cast<const R*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
     for (int b = 0; b < a.nblk; ++b) {
         if (blk[2 * b + 1] < (R)xlo_w || blk[2 * b] > (R)xhi_w) continue;
         R acc[16];
@@ -975,7 +1014,7 @@ DEV void species_loop(const KArgs& a, int g, float xlo_w, float xhi_w, bool vali
         for (int i = 0; i < 16; ++i) acc[i] = 0;
         const int kb = b * COLBLK, ke = min(a.K, kb + COLBLK);
         for (int k = kb; k < ke; ++k) {
-            const R* c = colrec<R>(a, 0, g, k);
+            const R* c = colrec<R>(a, t, g, k);
             if (c[F_XMAX] < (R)xlo_w || c[F_XMIN] > (R)xhi_w) continue;
             R v;
             if constexpr (sizeof(R) == 4) {
@@ -1002,9 +1041,11 @@ DEV void species_loop(const KArgs& a, int g, float xlo_w, float xhi_w, bool vali
     }
 }
 
+// grid (bin tiles, groups, toys x species chunks of 16): M[t][g][s][j] (toy stride a.mstride)
 template <class R, int RES>
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_species(KArgs a) {
     const int tile = blockIdx.x, g = blockIdx.y;
+    const int nchunk = (a.sp_count + 15) / 16, t = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
     if (!tb_g_active(a, g)) return;  // no smeared species in the group
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int J = tb_g_bins(a, g);
@@ -1019,29 +1060,30 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_species(KArgs a) {
     const float xhi_w = (float)a.edges[tb_g_edge_off(a, g) + jl + 1];
     const unsigned char cls = a.bclass[nb];
     const bool low = __any_sync(0xffffffffu, cls != BIN_LIN);
-    const int nsp = min(16, a.sp_count - blockIdx.z * 16);
+    const int nsp = min(16, a.sp_count - chunk * 16);
     KArgs b = a;
-    b.sp_first = a.sp_first + blockIdx.z * 16;
+    b.sp_first = a.sp_first + chunk * 16;
     double accd[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) accd[i] = 0.0;
     if constexpr (sizeof(R) == 4) {
         const float* nodes = a.ntab_f + (long long)nb * 3 * NGM_F;
         const float xc = a.xc_f[nb];
-        if (low) species_loop<float, RES, NG_LOG_F>(b, g, xlo_w, xhi_w, valid, cls == BIN_ZERO, nodes, xc, accd, nsp);
-        else     species_loop<float, RES, NG_LIN_F>(b, g, xlo_w, xhi_w, valid, false, nodes, xc, accd, nsp);
+        if (low) species_loop<float, RES, NG_LOG_F>(b, t, g, xlo_w, xhi_w, valid, cls == BIN_ZERO, nodes, xc, accd, nsp);
+        else     species_loop<float, RES, NG_LIN_F>(b, t, g, xlo_w, xhi_w, valid, false, nodes, xc, accd, nsp);
     } else {
         const double* nodes = a.ntab_d + (long long)nb * 3 * NGM_D;
-        if (low) species_loop<double, RES, NG_LOG_D>(b, g, xlo_w, xhi_w, valid, cls == BIN_ZERO, nodes, 0.0, accd, nsp);
-        else     species_loop<double, RES, NG_LIN_D>(b, g, xlo_w, xhi_w, valid, false, nodes, 0.0, accd, nsp);
+        if (low) species_loop<double, RES, NG_LOG_D>(b, t, g, xlo_w, xhi_w, valid, cls == BIN_ZERO, nodes, 0.0, accd, nsp);
+        else     species_loop<double, RES, NG_LIN_D>(b, t, g, xlo_w, xhi_w, valid, false, nodes, 0.0, accd, nsp);
     }
     if (valid)
-        for (int i = 0; i < nsp; ++i) a.Mbuf[((long long)g * a.S + b.sp_first + i) * a.Jmax + j] = accd[i];
+        for (int i = 0; i < nsp; ++i) a.Mbuf[(long long)t * a.mstride + ((long long)g * a.S + b.sp_first + i) * a.Jmax + j] = accd[i];
 }
 
 // FP64 Gaussian per-species path: exact erfc bin integrals (lanes <-> edges, 31 bins per warp)
 __global__ void __launch_bounds__(FWD_WARPS * 32) k_species_gauss64(KArgs a) {
     const int tile = blockIdx.x, g = blockIdx.y;
+    const int nchunk = (a.sp_count + 15) / 16, t = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
     if (!tb_g_active(a, g)) return;  // no smeared species in the group
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int J = tb_g_bins(a, g);
@@ -1052,9 +1094,9 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_species_gauss64(KArgs a) {
     const double xe = a.edges[tb_g_edge_off(a, g) + min(j, J)];
     const int jl = min(j0 + 30, J - 1);
     const double xlo_w = a.edges[tb_g_edge_off(a, g) + j0], xhi_w = a.edges[tb_g_edge_off(a, g) + jl + 1];
-    const int sp0 = a.sp_first + blockIdx.z * 16;
-    const int nsp = min(16, a.sp_count - blockIdx.z * 16);
-    const double* blk = reinterpret_cast<const double*>(a.blkbuf) + (long long)g * a.nblk * 2;
+    const int sp0 = a.sp_first + chunk * 16;
+    const int nsp = min(16, a.sp_count - chunk * 16);
+    const double* blk = reinterpret_cast<const double*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
     double acc[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) acc[i] = 0.0;
@@ -1062,7 +1104,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_species_gauss64(KArgs a) {
         if (blk[2 * b + 1] < xlo_w || blk[2 * b] > xhi_w) continue;
         const int kb = b * COLBLK, ke = min(a.K, kb + COLBLK);
         for (int k = kb; k < ke; ++k) {
-            const double* c = colrec<double>(a, 0, g, k);
+            const double* c = colrec<double>(a, t, g, k);
             if (c[F_XMAX] < xlo_w || c[F_XMIN] > xhi_w) continue;
             const double z = (xe - c[F_MUH]) * c[F_A];
             const bool up = z >= 0.0;
@@ -1077,28 +1119,30 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_species_gauss64(KArgs a) {
         }
     }
     if (valid)
-        for (int i = 0; i < nsp; ++i) a.Mbuf[((long long)g * a.S + sp0 + i) * a.Jmax + j] = acc[i];
+        for (int i = 0; i < nsp; ++i) a.Mbuf[(long long)t * a.mstride + ((long long)g * a.S + sp0 + i) * a.Jmax + j] = acc[i];
 }
 
 // mu_dj = sum_s eps_d f_ds r_s M[g][s][j] (smeared species; peaks are added by k_deviance)
+// grid (bins, toys): mu of toy t from its per-species shapes (one column split)
 __global__ void k_mu_from_species(KArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y;
     if (i >= a.total_bins) return;
     int lo = 0, hi = a.D - 1;  // last dataset whose first bin is <= i
     while (lo < hi) { const int m = (lo + hi + 1) >> 1; if (tb_ds_off(a, m) <= i) lo = m; else hi = m - 1; }
     const int d = lo;
     const int j = i - tb_ds_off(a, d);
     const int g = tb_ds_group(a, d);
-    const double* prm = a.params;
+    const double* prm = a.params + (long long)t * a.params_stride;
+    const double* M = a.Mbuf + (long long)t * a.mstride;
     double mu = 0.0;
     for (int s = 0; s < a.S; ++s) {
         const double f = a.rfac[d * a.S + s];
         if (a.ft.sp_kind[s] >= 2 || f == 0.0) continue;
         const int p = a.slot_map[d * a.NSLOT + s];
         if (p < 0) continue;
-        mu = fma(f * prm[p], a.Mbuf[((long long)g * a.S + s) * a.Jmax + j], mu);
+        mu = fma(f * prm[p], M[((long long)g * a.S + s) * a.Jmax + j], mu);
     }
-    a.mubuf[i] = mu;
+    a.mubuf[(long long)t * a.total_bins + i] = mu;
 }
 
 // expected counts per bin and species of one dataset
@@ -1275,12 +1319,15 @@ cudaError_t launch_devfinal(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_backward(const KArgs& a, cudaStream_t st) {
-    if (a.precision == 1 && a.res != 2) return launch_backward_mixed(a, st);
+    // the tuned mixed adjoint serves the Gaussian and gamma responses without a secondary observable
+    if (a.precision == 1 && a.res != 2 && a.nsec == 0) return launch_backward_mixed(a, st);
     dim3 grid(a.nbtask, a.G, a.T);
     const int threads = a.bw_warps * 32;
     const size_t rs = a.precision == 1 ? sizeof(float) : sizeof(double);
     const size_t sm = rs * MAXGDS * threads + 16 + sizeof(double) * a.bw_warps * NRESP;
-    if (a.precision == 1)  k_backward<float, 2><<<grid, threads, sm, st>>>(a);
+    if (a.precision == 1 && a.res == 0)      k_backward<float, 0><<<grid, threads, sm, st>>>(a);
+    else if (a.precision == 1 && a.res == 1) k_backward<float, 1><<<grid, threads, sm, st>>>(a);
+    else if (a.precision == 1)               k_backward<float, 2><<<grid, threads, sm, st>>>(a);
     else if (a.res == 0)   k_backward<double, 0><<<grid, threads, sm, st>>>(a);
     else if (a.res == 1)   k_backward<double, 1><<<grid, threads, sm, st>>>(a);
     else                   k_backward<double, 2><<<grid, threads, sm, st>>>(a);
@@ -1295,11 +1342,11 @@ cudaError_t launch_gradfinal(const KArgs& a, cudaStream_t st) {
 cudaError_t launch_species(const KArgs& a, cudaStream_t st) {
     const int nchunk = (a.sp_count + 15) / 16;
     if (a.precision == 0 && a.res == 0) {
-        dim3 grid((a.Jmax + FWD_WARPS * 31 - 1) / (FWD_WARPS * 31), a.G, nchunk);
+        dim3 grid((a.Jmax + FWD_WARPS * 31 - 1) / (FWD_WARPS * 31), a.G, nchunk * a.T);
         k_species_gauss64<<<grid, FWD_WARPS * 32, 0, st>>>(a);
         return cudaGetLastError();
     }
-    dim3 grid((a.Jmax + FWD_WARPS * 32 - 1) / (FWD_WARPS * 32), a.G, nchunk);
+    dim3 grid((a.Jmax + FWD_WARPS * 32 - 1) / (FWD_WARPS * 32), a.G, nchunk * a.T);
     if (a.precision == 1) {
         if (a.res == 0)      k_species<float, 0><<<grid, FWD_WARPS * 32, 0, st>>>(a);
         else if (a.res == 1) k_species<float, 1><<<grid, FWD_WARPS * 32, 0, st>>>(a);
@@ -1312,7 +1359,7 @@ cudaError_t launch_species(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_mu_from_species(const KArgs& a, cudaStream_t st) {
-    k_mu_from_species<<<(a.total_bins + 255) / 256, 256, 0, st>>>(a);
+    k_mu_from_species<<<dim3((a.total_bins + 255) / 256, a.T), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

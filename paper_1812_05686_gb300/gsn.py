@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH):
         "gsn_set_template": (C.c_int, [vp, C.c_int, C.c_int, _DP]),
         "gsn_minimize_batch_dev": (C.c_int, [vp, C.c_int, vp, vp, vp, C.POINTER(C.c_ubyte), _DP, _DP, _DP,
                                              C.c_int, C.c_double, C.c_double, vp, vp, vp]),
+        "gsn_set_secondary": (C.c_int, [vp, C.c_int, C.c_int, _IP, C.c_int, _DP, _DP]),
+        "gsn_n_counts": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -91,7 +93,8 @@ def exported_symbols():
             "gsn_set_data", "gsn_set_species", "gsn_set_params", "gsn_eval", "gsn_eval_grad",
             "gsn_eval_grad_batch", "gsn_eval_grad_batch_dev", "gsn_expected", "gsn_stream",
             "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe", "gsn_eval_grad_noalloc",
-            "gsn_plan_info", "gsn_set_dataset_factors", "gsn_set_template", "gsn_minimize_batch_dev"]
+            "gsn_plan_info", "gsn_set_dataset_factors", "gsn_set_template", "gsn_minimize_batch_dev",
+            "gsn_set_secondary", "gsn_n_counts"]
 
 
 GSN_K_COUNT = 8
@@ -271,6 +274,24 @@ class Context:
             C.c_void_p(status.data_ptr())))
         return nll, evals, status
 
+    def set_secondary(self, dataset, slice_start, shapes, counts=None):
+        """Secondary observable of a dataset: slice boundaries (Q+1,), shapes (S, Q, M), counts (Q, M)."""
+        if shapes is None:
+            self._check(self.lib.gsn_set_secondary(self.h, int(dataset), 0, None, 0, None, None))
+            return
+        shapes = np.ascontiguousarray(shapes, np.float64)
+        st, pst = _i(np.asarray(slice_start, np.int32))
+        sh, psh = _d(shapes)
+        Q, M = shapes.shape[1], shapes.shape[2]
+        cn = pcn = None
+        if counts is not None:
+            cn, pcn = _d(np.asarray(counts, np.float64).reshape(-1))
+        self._check(self.lib.gsn_set_secondary(self.h, int(dataset), Q, pst, M, psh, pcn))
+
+    def n_counts(self):
+        """Values in a toy's counts row (energy bins, then secondary bins)."""
+        return self.lib.gsn_n_counts(self.h)
+
     def set_template(self, species, dataset, hist):
         """Monte Carlo template (visible-bin histogram) of a GSN_MC_TEMPLATE species in one dataset."""
         if hist is None:
@@ -304,6 +325,8 @@ def context_from_workload(work: dict, precision=GSN_FP64, counts=None, **kw) -> 
     ctx = Context(precision=precision, resolution=int(work["resolution"]),
                   birks_s0=work["birks_s0"], birks_s1=work["birks_s1"], **kw)
     edges = work["edges"]
+    sec = work.get("secondary")
+    sec_counts = [None] * len(edges)
     if counts is None:
         counts = [np.zeros(len(e) - 1) for e in edges]
     elif not isinstance(counts, (list, tuple)):
@@ -311,6 +334,10 @@ def context_from_workload(work: dict, precision=GSN_FP64, counts=None, **kw) -> 
         counts, o = [], 0
         for e in edges:
             counts.append(flat[o:o + len(e) - 1]); o += len(e) - 1
+        for d, x in enumerate(sec or []):  # a secondary tail after the energy bins
+            if x is not None and flat.size > o:
+                n = int(np.prod(np.asarray(x["shapes"]).shape[1:]))
+                sec_counts[d] = flat[o:o + n]; o += n
     ctx.set_data(edges, counts, work["exposure"], work["win_lo"], work["win_hi"])
     ctx.set_species(work["fine_centres"], work["spectra"], work["kind"], work["shift"], work["mask"])
     ctx.set_params(int(work["n_params"]), work["slot_map"], work["pull_param"], work["pull_centre"], work["pull_width"])
@@ -320,6 +347,10 @@ def context_from_workload(work: dict, precision=GSN_FP64, counts=None, **kw) -> 
         for d, hist in enumerate(row or []):
             if hist is not None:
                 ctx.set_template(s, d, hist)
+    for d, x in enumerate(sec or []):
+        if x is not None:
+            ctx.set_secondary(d, x["slice_start"], x["shapes"],
+                              sec_counts[d] if sec_counts[d] is not None else x.get("counts"))
     return ctx
 
 
