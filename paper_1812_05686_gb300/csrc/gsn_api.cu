@@ -59,7 +59,7 @@ struct gsn_ctx {
     // persistent device buffers
     std::vector<Buf> owned;
     // scratch
-    Buf MbufT, secN_b, secV_b, secW_b, secpart_b, secU_b;  // per-toy buffers of the secondary pieces
+    Buf secRq_b, secN_b, secV_b, secW_b, secpart_b, secU_b;  // per-toy buffers of the secondary pieces
     Buf colbuf, colbuf2, blkbuf, mubuf, wbuf, partbuf, gdirect, devbuf, params, counts_b, win_b, nll_b, grad_b, status_b, Mbuf,
         outbuf;
     unsigned long long scratch_gen = 0;  // bumped whenever a buffer is (re)allocated
@@ -498,7 +498,7 @@ int reserve(gsn_ctx* c, int T, const Plan& p) {
     if ((rc = ensure(c, c->devbuf, (size_t)T * p.dev_chunks * (2 + c->base.ntpl) * sizeof(double)))) return rc;
     const KArgs& b = c->base;
     if (b.nsec) {
-        if ((rc = ensure(c, c->MbufT, (size_t)T * c->G * c->S * c->Jmax * sizeof(double)))) return rc;
+        if ((rc = ensure(c, c->secRq_b, (size_t)T * b.Qtot * c->K * rs))) return rc;
         if ((rc = ensure(c, c->secN_b, (size_t)T * b.Qtot * c->S * sizeof(double)))) return rc;
         if ((rc = ensure(c, c->secV_b, (size_t)T * b.Qtot * c->S * sizeof(double)))) return rc;
         if ((rc = ensure(c, c->secW_b, (size_t)T * b.nsecb * sizeof(double)))) return rc;
@@ -519,7 +519,7 @@ void fill(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
     a.wbuf = c->wbuf.p; a.partbuf = (double*)c->partbuf.p; a.gdirect = (double*)c->gdirect.p;
     a.devpart = (double*)c->devbuf.p;
     if (a.nsec) {
-        a.Mbuf = (double*)c->MbufT.p; a.mstride = (long long)c->G * c->S * c->Jmax;
+        a.secRq = c->secRq_b.p;
         a.secN = (double*)c->secN_b.p; a.secV = (double*)c->secV_b.p; a.secW = (double*)c->secW_b.p;
         a.secpart = (double*)c->secpart_b.p; a.secU = c->secU_b.p;
         a.sp_first = 0; a.sp_count = c->S;
@@ -580,15 +580,13 @@ int launch(gsn_ctx* c, int kernel, KArgs& a, F fn) {
 int run_step(gsn_ctx* c, KArgs& a, bool grad) {
     int rc;
     if (a.nsec) {
-        // secondary observable: per-species shapes per toy (their slice sums feed the extra pieces),
-        // mu from them, the pieces, then the energy deviance; the adjoint adds the pieces' weights
+        // secondary observable: the regular forward for mu, the response's slice sums for the
+        // extra pieces, the pieces, then the energy deviance; the adjoint adds the pieces' weights
         if (a.response) {
             if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
-            if ((rc = launch(c, K_FORWARD, a, launch_species))) return rc;
-        } else {
-            CUDA_TRY(c, cudaMemsetAsync(a.Mbuf, 0, (size_t)a.T * a.mstride * sizeof(double), c->stream));
+            if ((rc = launch(c, K_FORWARD, a, launch_forward))) return rc;
+            if ((rc = launch(c, K_MU, a, launch_slice_sums))) return rc;
         }
-        if ((rc = launch(c, K_MU, a, launch_mu_from_species))) return rc;
         if ((rc = launch(c, K_SPECIES, a, launch_secondary))) return rc;
         if ((rc = launch(c, K_DEVIANCE, a, launch_deviance))) return rc;
         if ((rc = launch(c, K_DEVFINAL, a, launch_devfinal))) return rc;
@@ -654,11 +652,6 @@ int choose_plan(gsn_ctx* c, int T, KArgs a, bool grad, Plan& out) {
     if (it != c->tuned.end()) { out = it->second; return GSN_OK; }
     const Plan h = heuristic_plan(c, T);
     out = h;
-    if (c->base.nsec) {  // mu comes from the per-species shapes: one column range, heuristic adjoint split
-        out = plan_with(c, T, 1, h.bw_warps, h.bw_bsplit);
-        c->tuned[key] = out;
-        return GSN_OK;
-    }
     if (stream_capturing(c)) return GSN_OK;  // no timing inside a caller's capture
     if (!c->opt.autotune || !c->base.response || (h.nsplit == 1 && h.bw_bsplit == 1)) { c->tuned[key] = h; return GSN_OK; }
     const cudaStream_t st = c->stream;
@@ -869,7 +862,7 @@ void gsn_destroy(gsn_ctx* c) {
     free_owned(c);
     for (Buf* b : {&c->fit_ws, &c->fit_cfg, &c->fit_eval, &c->fit_ist})
         if (b->p) cudaFree(b->p);
-    for (Buf* b : {&c->MbufT, &c->secN_b, &c->secV_b, &c->secW_b, &c->secpart_b, &c->secU_b,
+    for (Buf* b : {&c->secRq_b, &c->secN_b, &c->secV_b, &c->secW_b, &c->secpart_b, &c->secU_b,
                    &c->colbuf, &c->colbuf2, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
                    &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf, &c->s_hi, &c->s_lo,
                    &c->tc_part, &c->tc_err})
@@ -1307,6 +1300,7 @@ int gsn_eval(gsn_ctx* c, const double* params, double* nll) {
     a.nll = (double*)c->nll_b.p; a.grad = nullptr; a.status = (int*)c->status_b.p;
     a.want_grad = 0;
     a.Mbuf = (double*)c->Mbuf.p;  // the cached shapes (one parameter point)
+    a.secRq = nullptr;            // the secondary pieces take their slice sums from them
     if ((rc = launch(c, K_MU, a, launch_mu_from_species))) return rc;
     if (a.nsec && (rc = launch(c, K_SPECIES, a, launch_secondary))) return rc;
     if ((rc = launch(c, K_DEVIANCE, a, launch_deviance))) return rc;

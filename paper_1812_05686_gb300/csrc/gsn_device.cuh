@@ -258,4 +258,13 @@ DEV float bin_value_f(const float* c, float xc, const float* del, const float* l
     return rho;
 }
 
+// FP64 gamma: sum_n w_n exp((d-1) ln x_n - x_n/s - d ln s - lgamma(d))
+template <int NG>
+DEV double bin_value_gamma_d(const double* c, const double* x, const double* lx, const double* wt) {
+    double rho = 0.0;
+#pragma unroll
+    for (int n = 0; n < NG; ++n) rho = fma(wt[n], exp(fma(c[F_B], lx[n], fma(-c[F_C], x[n], c[F_A]))), rho);
+    return rho;
+}
+
 }  // namespace gsn

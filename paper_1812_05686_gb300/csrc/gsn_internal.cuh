@@ -165,6 +165,7 @@ struct KArgs {
     double* secW;          // [T][nsecb] 1 - n/mu of every secondary bin
     double* secpart;       // [T][nsec][2 + NSLOT] NLL piece, flags, slot gradient
     void* secU;            // [T][Qtot][K] of Real: adjoint weight of the secondary pieces
+    void* secRq;           // [T][Qtot][K] of Real: N_k sum_{j in q} R_jk (NULL: slice sums from Mbuf)
     // statistics: evaluated (bin, column) pairs per kernel class (NULL = off)
     unsigned long long* work;
     // tensor-core per-species contraction
@@ -218,6 +219,7 @@ int make_species_tensor_map(void* out, const float* dev, int rows, int cols_pad)
 cudaError_t launch_backward_mixed(const KArgs& a, cudaStream_t st);
 cudaError_t launch_secondary(const KArgs& a, cudaStream_t st);
 cudaError_t launch_secondary_weights(const KArgs& a, cudaStream_t st);
+cudaError_t launch_slice_sums(const KArgs& a, cudaStream_t st);
 
 constexpr int K_COLUMNS = 0, K_FORWARD = 1, K_DEVIANCE = 2, K_BACKWARD = 3, K_GRADFINAL = 4,
               K_SPECIES = 5, K_MU = 6, K_DEVFINAL = 7, K_COUNT = 8;

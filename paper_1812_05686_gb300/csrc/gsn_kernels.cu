@@ -250,15 +250,6 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
     }
 }
 
-// FP64 gamma: sum_n w_n exp((d-1) ln x_n - x_n/s - d ln s - lgamma(d))
-template <int NG>
-DEV double bin_value_gamma_d(const double* c, const double* x, const double* lx, const double* wt) {
-    double rho = 0.0;
-#pragma unroll
-    for (int n = 0; n < NG; ++n) rho = fma(wt[n], exp(fma(c[F_B], lx[n], fma(-c[F_C], x[n], c[F_A]))), rho);
-    return rho;
-}
-
 // ------------------------------------------------------------- forward -----
 template <class R, int RES, int NG>
 DEV int forward_loop(const KArgs& a, int t, int g, int split, float xlo_w, float xhi_w, bool valid,

@@ -7,12 +7,16 @@
 // integrated over the slice (AnaPeak), and spreads them over the secondary bins with the fixed
 // shape P_sqm.  Every slice inside the toy's window adds the Poisson term of
 // mu_qm = sum_s N_sq P_sqm to the NLL.
+//   k_slice_sums         Rq[t][q][k] = N_k sum_{j in q} R_jk over the bins of every slice inside the
+//                        toy's window (lanes <-> columns), so that U_sq = sum_k Rq_qk S'_sk: the
+//                        pieces need slice sums only, and mu comes from the regular forward
 //   k_secondary          one block per (toy, dataset with a secondary observable): U, the terms,
 //                        omega_qm = 1 - n_qm / mu_qm, v_sq = sum_m omega_qm P_sqm and the direct
 //                        gradient terms of the rate and peak slots (fixed-order sums)
 //   k_secondary_weights  U_qk = sum_s v_sq eps f_ds r_s S'_sk per fine column: the adjoint adds
 //                        U_{q(j) k} N_k to the weight of every (bin j, column k) pair of slice q
 #include "gsn_device.cuh"
+#include "gsn_ggamma.cuh"
 
 namespace gsn {
 
@@ -53,7 +57,8 @@ __global__ void __launch_bounds__(256) k_secondary(KArgs a) {
             const int jl = a.sq_lo[q0 + q], jh = a.sq_hi[q0 + q];
             const int kind = a.ft.sp_kind[s];
             if (kind < 2) {
-                for (int j = jl; j < jh; ++j) u += Mg[(long long)s * a.Jmax + j];
+                if (!a.secRq)  // per-species shapes of one point (the value cache of gsn_eval)
+                    for (int j = jl; j < jh; ++j) u += Mg[(long long)s * a.Jmax + j];
             } else if (kind == 3) {
                 for (int gq = a.tb->ds_tpl0[d]; gq < a.tb->ds_tpl0[d] + a.tb->ds_ntpl[d]; ++gq)
                     if (a.tpl_s[gq] == s)
@@ -69,6 +74,35 @@ __global__ void __launch_bounds__(256) k_secondary(KArgs a) {
         U[e] = u;
     }
     __syncthreads();
+    if (a.secRq) {
+        // smeared species from the slice sums: U_sq = sum_k Rq_qk S'_sk, one warp per (q, s), lanes
+        // striding over the columns, fixed-order warp sum
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int e = warp; e < Q * S; e += nw) {
+            const int q = e / S, s = e % S;
+            if (a.ft.sp_kind[s] >= 2 || a.rfac[d * S + s] == 0.0 || !active(q)) continue;
+            double u = 0.0;
+            if (a.precision == 1) {
+                // FP32 products in compensated (TwoSum) lane sums: the FP64 rate would bound this
+                const float* Rq = reinterpret_cast<const float*>(a.secRq) + ((long long)t * a.Qtot + q0 + q) * a.K;
+                const float* Sr = a.Sf + (long long)s * a.K;
+                float us = 0.f, uc = 0.f;
+                for (int k = lane; k < a.K; k += 32) {
+                    const float pr = Rq[k] * Sr[k];
+                    two_sum_acc(us, uc, pr);
+                    uc = fmaf(Rq[k], Sr[k], -pr) + uc;   // the product's rounding error
+                }
+                u = (double)us + (double)uc;
+            } else {
+                const double* Rq = reinterpret_cast<const double*>(a.secRq) + ((long long)t * a.Qtot + q0 + q) * a.K;
+                const double* Sr = a.Sd + (long long)s * a.K;
+                for (int k = lane; k < a.K; k += 32) u = fma(Rq[k], Sr[k], u);
+            }
+            u = warp_sum<double>(u);
+            if (lane == 0) U[e] = u;
+        }
+        __syncthreads();
+    }
     // 2) expected secondary counts, Poisson terms, omega
     double part = 0.0;
     int flags = 0;
@@ -145,6 +179,85 @@ __global__ void __launch_bounds__(256) k_secondary(KArgs a) {
     }
 }
 
+// grid (column blocks of 256, groups, toys); lanes <-> columns.  Every warp walks the bins of its
+// columns' band (the warp's union) inside each active slice of the group's datasets.
+template <class R, int RES>
+__global__ void __launch_bounds__(256) k_slice_sums(KArgs a) {
+    const int g = blockIdx.y, t = blockIdx.z;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool kval = k < a.K;
+    if (!tb_g_active(a, g)) return;
+    R c[NFP];
+    {
+        const R* cr = colrec<R>(a, t, g, kval ? k : a.K - 1);
+#pragma unroll
+        for (int i = 0; i < NFP; ++i) c[i] = cr[i];
+    }
+    const int J = tb_g_bins(a, g), nbase = tb_g_node_off(a, g);
+    const double* ed = a.edges + tb_g_edge_off(a, g);
+    const R xmn = warp_min<R>(kval ? c[F_XMIN] : (R)INFINITY);
+    const R xmx = warp_max<R>(kval ? c[F_XMAX] : (R)-INFINITY);
+    int ja = 0, jb = -1;
+    if (xmx >= xmn) {
+        int lo = 0, hi = J;
+        while (lo < hi) { const int m = (lo + hi) >> 1; if (ed[m + 1] <= (double)xmn) lo = m + 1; else hi = m; }
+        ja = lo;
+        lo = 0; hi = J;
+        while (lo < hi) { const int m = (lo + hi) >> 1; if (ed[m] < (double)xmx) lo = m + 1; else hi = m; }
+        jb = lo - 1;
+    }
+    R* out = reinterpret_cast<R*>(a.secRq) + (long long)t * a.Qtot * a.K;
+    for (int dd = 0; dd < tb_g_nds(a, g); ++dd) {
+        const int d = tb_g_ds(a, g, dd);
+        int i = -1;
+        for (int x = 0; x < a.nsec; ++x) if (a.sec_ds[x] == d) i = x;
+        if (i < 0) continue;
+        int wlo, whi;
+        toy_window(a, t, d, wlo, whi);
+        for (int q = 0; q < a.sec_nq[i]; ++q) {
+            const int qg = a.sec_q0[i] + q, jl = a.sq_lo[qg], jh = a.sq_hi[qg];
+            if (!(jl >= wlo && jh <= whi && jh > jl)) continue;
+            double sum = 0.0;
+            if constexpr (sizeof(R) == 8 && RES == 0) {
+                // FP64 Gaussian: the exact integral over the slice
+                if (kval) sum = ncdf_diff((ed[jl] - c[F_MUH]) * c[F_A], (ed[jh] - c[F_MUH]) * c[F_A]);
+            } else {
+                const int j0 = max(jl, ja), j1 = min(jh - 1, jb);
+                R acc = 0;
+                for (int j = j0; j <= j1; ++j) {
+                    const unsigned char cls = a.bclass[nbase + j];
+                    R v;
+                    if (RES >= 1 && cls == BIN_ZERO) {
+                        v = c[F_P0];
+                    } else if constexpr (sizeof(R) == 4) {
+                        const float* nd = a.ntab_f + (long long)(nbase + j) * 3 * NGM_F;
+                        const float xc = a.xc_f[nbase + j];
+                        if (cls == BIN_LOG) {
+                            if constexpr (RES == 2) v = gg_bin_value_f<NG_LOG_F>(c, xc, nd + NGM_F, nd + 2 * NGM_F);
+                            else v = bin_value_f<RES, NG_LOG_F>(c, xc, nd, nd + NGM_F, nd + 2 * NGM_F);
+                        } else {
+                            if constexpr (RES == 2) v = gg_bin_value_f<NG_LIN_F>(c, xc, nd + NGM_F, nd + 2 * NGM_F);
+                            else v = bin_value_f<RES, NG_LIN_F>(c, xc, nd, nd + NGM_F, nd + 2 * NGM_F);
+                        }
+                    } else {
+                        const double* nd = a.ntab_d + (long long)(nbase + j) * 3 * NGM_D;
+                        if (cls == BIN_LOG) {
+                            if constexpr (RES == 2) v = gg_bin_value_d<NG_LOG_D>(c, nd + NGM_D, nd + 2 * NGM_D);
+                            else v = bin_value_gamma_d<NG_LOG_D>(c, nd, nd + NGM_D, nd + 2 * NGM_D);
+                        } else {
+                            if constexpr (RES == 2) v = gg_bin_value_d<NG_LIN_D>(c, nd + NGM_D, nd + 2 * NGM_D);
+                            else v = bin_value_gamma_d<NG_LIN_D>(c, nd, nd + NGM_D, nd + 2 * NGM_D);
+                        }
+                    }
+                    acc += v;
+                }
+                sum = (double)acc * (double)c[F_N];
+            }
+            if (kval) out[(long long)qg * a.K + k] = (R)sum;
+        }
+    }
+}
+
 // grid (column blocks, slices, toys)
 template <class R>
 __global__ void __launch_bounds__(256) k_secondary_weights(KArgs a) {
@@ -166,6 +279,20 @@ __global__ void __launch_bounds__(256) k_secondary_weights(KArgs a) {
 
 cudaError_t launch_secondary(const KArgs& a, cudaStream_t st) {
     k_secondary<<<dim3(a.T, a.nsec), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slice_sums(const KArgs& a, cudaStream_t st) {
+    const dim3 grid((a.K + 255) / 256, a.G, a.T);
+    if (a.precision == 1) {
+        if (a.res == 0)      k_slice_sums<float, 0><<<grid, 256, 0, st>>>(a);
+        else if (a.res == 1) k_slice_sums<float, 1><<<grid, 256, 0, st>>>(a);
+        else                 k_slice_sums<float, 2><<<grid, 256, 0, st>>>(a);
+    } else {
+        if (a.res == 0)      k_slice_sums<double, 0><<<grid, 256, 0, st>>>(a);
+        else if (a.res == 1) k_slice_sums<double, 1><<<grid, 256, 0, st>>>(a);
+        else                 k_slice_sums<double, 2><<<grid, 256, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
