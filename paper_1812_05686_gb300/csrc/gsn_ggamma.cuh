@@ -324,6 +324,34 @@ DEV float gg_bin_value_f(const float* c, float xc, const float* lam, const float
     return rho;
 }
 
+// Linear bins, 3-node rule (nodes left, centre, right): the side nodes from the centre node by
+// Q(q + e) = Q(q) + Q(e) + E1(q) E1(e), E1 = e^q - 1 (exact), with e = p ln(x_n / x_c) fixed per
+// bin and toy.  The terms are O(q^2, e^2, q e): where they cancel (a side node at the mean) the
+// result is O(e^2) with an absolute error of a few ulp of it, far below the exponent's rounding.
+struct GGSides { float dlam0, dlam2, Q0, Q2, E0, E2; };
+DEV GGSides gg_sides(float p, const float* lam) {
+    GGSides g;
+    g.dlam0 = lam[0] - lam[1];
+    g.dlam2 = lam[2] - lam[1];
+    g.Q0 = gg_q2f(p * g.dlam0, g.E0);
+    g.Q2 = gg_q2f(p * g.dlam2, g.E2);
+    return g;
+}
+DEV float gg_bin_value_f3(const float* c, float xc, const float* lam, const float* wt, const GGSides& sd) {
+    const float Dx = (xc - c[F_MUH]) - c[F_MUL];
+    float Lc;
+    log1pmx2_f(Dx * c[F_A], Lc);
+    const float p = c[F_KAPPA], Ap = c[F_B], Kp = c[F_C];
+    const float L1 = Lc + lam[1];
+    float e1;
+    const float Q = gg_q2f(p * L1, e1);
+    const float Ql = fmaf(e1, sd.E0, Q + sd.Q0), Qr = fmaf(e1, sd.E2, Q + sd.Q2);
+    const float vl = ex2f(fmaf(-Ap, Ql, Kp * (L1 + sd.dlam0)));
+    const float vc = ex2f(fmaf(-Ap, Q, Kp * L1));
+    const float vr = ex2f(fmaf(-Ap, Qr, Kp * (L1 + sd.dlam2)));
+    return fmaf(wt[0], vl, fmaf(wt[1], vc, wt[2] * vr));
+}
+
 // FP64 bin value: sum_n w_n exp(ln p - d ln s - lnGamma(d/p) + (d-1) ln x_n - (x_n/s)^p)
 template <int NG>
 DEV double gg_bin_value_d(const double* c, const double* lx, const double* wt) {

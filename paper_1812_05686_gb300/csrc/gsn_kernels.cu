@@ -260,10 +260,17 @@ DEV int forward_loop(const KArgs& a, int t, int g, int split, float xlo_w, float
     const int k_beg = split * kchunk, k_end = min(a.K, k_beg + kchunk);
     const R* blk = reinterpret_cast<const R*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
     R del[NG], lam[NG], wt[NG];
+    [[maybe_unused]] GGSides sides{};
     if constexpr (sizeof(R) == 4) {
 #pragma unroll
         for (int n = 0; n < NG; ++n) {
             del[n] = nodes[n]; lam[n] = nodes[NGM_F + n]; wt[n] = valid ? nodes[2 * NGM_F + n] : R(0);
+        }
+        if constexpr (RES == 2 && NG == 3) {
+            // the toy's power (the value every column record of the toy carries)
+            const int q = tb_g_resp(a, g, 5);
+            const float pw = (float)(a.params[(long long)t * a.params_stride + q] * tb_g_rscale(a, g, 5));
+            sides = gg_sides(pw, lam);
         }
     } else {
 #pragma unroll
@@ -282,7 +289,8 @@ DEV int forward_loop(const KArgs& a, int t, int g, int split, float xlo_w, float
             ++ncol;
             R v;
             if constexpr (sizeof(R) == 4) {
-                if constexpr (RES == 2) v = gg_bin_value_f<NG>(c, xc, lam, wt);
+                if constexpr (RES == 2 && NG == 3) v = gg_bin_value_f3(c, xc, lam, wt, sides);
+                else if constexpr (RES == 2) v = gg_bin_value_f<NG>(c, xc, lam, wt);
                 else v = bin_value_f<RES, NG>(c, xc, del, lam, wt);
                 if (RES >= 1 && is_zero) v = valid ? c[F_P0] : 0.0f;
             } else {
