@@ -44,12 +44,14 @@ WORKLOAD = "borexino_like toys: 2 datasets x 1200-bin domain, 16 species x 20000
 #                 coefficients (11) + four accumulations (8)
 FLOP_PER_PAIR = {"forward": 44, "backward": 70}
 # The same count for the generalized gamma of free power p (--power), general per-node kernels, linear
-# bins (3 nodes), |p L| <= 1/2 (the bulk of a band):
-#   forward  109 = offset and t (3) + ln(1+t) series (21) + per node [L and pL (2) + e^q-1-q series (19)
-#                  + e1 (1) + exponent (3) + weighted exponential (3)] x 3 + 2-dataset contraction (4)
-#   backward 178 = offset, t and ln(1+t) (24) + per node [the forward's 28 + four node sums (6)] x 3
-#                  + dataset weight (3) + four compensated band sums (28) + three compensated rate sums (21)
-FLOP_PER_PAIR_GG = {"forward": 109, "backward": 178}
+# bins (3 nodes; the side nodes from the centre by the addition formula of e^q-1-q), |p L| <= 1/2:
+#   forward   75 = offset and t (3) + ln(1+t) series (21) + centre L, pL, series and e1 (22)
+#                  + side-node L and Q (8) + three exponents (9) + 3 exp2 (3) + weighted sum (5)
+#                  + 2-dataset contraction (4)
+#   backward 152 = offset, t and ln(1+t) (24) + centre (21) + side-node L, Q and e1 (16)
+#                  + per node [exponent, exp2, weight and four node sums (13)] x 3 + dataset weight (3)
+#                  + four compensated band sums (28) + three compensated rate sums (21)
+FLOP_PER_PAIR_GG = {"forward": 75, "backward": 152}
 FP32_LANES_PER_SM = 128
 
 

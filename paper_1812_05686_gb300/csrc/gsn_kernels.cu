@@ -724,7 +724,22 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
     const int nbase = tb_g_node_off(a, g);
     if constexpr (RES == 2) {
         const R p = c[F_KAPPA];
+        // FP32, linear bins: side-node terms Q(e), E1(e), e = p ln(x_n/x_c), of the bins of the
+        // current 32-bin batch, one bin per lane, handed to every lane by shuffle (the lanes share
+        // the toy and so p); the nodes then follow from the centre by the addition formula
+        [[maybe_unused]] float sQ0 = 0.f, sE0 = 0.f, sQ2 = 0.f, sE2 = 0.f;
         for (int j = ja; j <= jb; ++j) {
+            if constexpr (sizeof(R) == 4) {
+                if (((j - ja) & 31) == 0) {
+                    const int jj = j + (threadIdx.x & 31);
+                    sQ0 = sE0 = sQ2 = sE2 = 0.f;
+                    if (jj <= jb && a.bclass[nbase + jj] == BIN_LIN) {
+                        const float* ndj = a.ntab_f + (long long)(nbase + jj) * 3 * NGM_F;
+                        sQ0 = gg_q2f(p * (ndj[NGM_F] - ndj[NGM_F + 1]), sE0);
+                        sQ2 = gg_q2f(p * (ndj[NGM_F + 2] - ndj[NGM_F + 1]), sE2);
+                    }
+                }
+            }
             R wj[MAXGDS];
             R Wj = 0;
 #pragma unroll
@@ -745,13 +760,29 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
                     const float Dx = (a.xc_f[nbase + j] - c[F_MUH]) - c[F_MUL];
                     float Lc;
                     log1pmx2_f(Dx * c[F_A], Lc);
-                    const int NG = cls == BIN_LOG ? NG_LOG_F : NG_LIN_F;
-                    for (int n = 0; n < NG; ++n) {
-                        const float L = Lc + nd[NGM_F + n];
+                    if (cls == BIN_LIN) {
+                        const int src = (j - ja) & 31;
+                        const float Q0 = __shfl_sync(0xffffffffu, sQ0, src), E0 = __shfl_sync(0xffffffffu, sE0, src);
+                        const float Q2 = __shfl_sync(0xffffffffu, sQ2, src), E2 = __shfl_sync(0xffffffffu, sE2, src);
+                        const float L1 = Lc + nd[NGM_F + 1];
                         float e1;
-                        const float Q = gg_q2f(p * L, e1);
-                        const float fw = nd[2 * NGM_F + n] * ex2f(fmaf(-c[F_B], Q, c[F_C] * L));
-                        rho += fw; s1 = fmaf(fw, L, s1); s2 = fmaf(fw, Q, s2); s3 = fmaf(fw * e1, L, s3);
+                        const float Qc = gg_q2f(p * L1, e1);
+                        const float Ln[3] = {L1 + (nd[NGM_F] - nd[NGM_F + 1]), L1, L1 + (nd[NGM_F + 2] - nd[NGM_F + 1])};
+                        const float Qn[3] = {fmaf(e1, E0, Qc + Q0), Qc, fmaf(e1, E2, Qc + Q2)};
+                        const float En[3] = {fmaf(e1, E0, e1 + E0), e1, fmaf(e1, E2, e1 + E2)};
+#pragma unroll
+                        for (int n = 0; n < 3; ++n) {
+                            const float fw = nd[2 * NGM_F + n] * ex2f(fmaf(-c[F_B], Qn[n], c[F_C] * Ln[n]));
+                            rho += fw; s1 = fmaf(fw, Ln[n], s1); s2 = fmaf(fw, Qn[n], s2); s3 = fmaf(fw * En[n], Ln[n], s3);
+                        }
+                    } else {
+                        for (int n = 0; n < NG_LOG_F; ++n) {
+                            const float L = Lc + nd[NGM_F + n];
+                            float e1;
+                            const float Q = gg_q2f(p * L, e1);
+                            const float fw = nd[2 * NGM_F + n] * ex2f(fmaf(-c[F_B], Q, c[F_C] * L));
+                            rho += fw; s1 = fmaf(fw, L, s1); s2 = fmaf(fw, Q, s2); s3 = fmaf(fw * e1, L, s3);
+                        }
                     }
                 } else {
                     const double* nd = a.ntab_d + (long long)(nbase + j) * 3 * NGM_D;
