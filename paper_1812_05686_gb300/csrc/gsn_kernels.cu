@@ -99,126 +99,126 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
 #pragma unroll
             for (int i = 0; i < NFG; ++i) g2[i] = gco[i];
         } else {
-        R mu, var, deq;
-        if constexpr (sizeof(R) == 4) {
-            // E_q = E/alpha - (beta/alpha^2) ln(1 + alpha E / beta), mean in double-float
-            const float Eh = a.E_hi[k], El = a.E_lo[k];
-            float qh, ql;
-            df_mul(Eh, El, sdf[0], sdf[1], qh, ql);
-            float Dy = 0.f, y = 0.f, Ly = 0.f;
-            if (beta > 0) {
-                y = Eh * sdf[5];
-                Dy = log1pmx2_f(y, Ly);
-                if (y < 1.0f) { qh = -sdf[4] * Dy; ql = 0.f; }
-                else df_add(qh, ql, -sdf[4] * Ly, qh, ql);
-            }
-            float muh, mul;
-            df_mul(qh, ql, sdf[2], sdf[3], muh, mul);
-            f[F_MUH] = muh; f[F_MUL] = mul;
-            mu = muh;
-            // dE_q/dkB = (1/alpha^2) [ s0 (beta/alpha) (2 D + y r) - s1 (D + y r) ], r = y/(1+y);
-            // for y >= 1 the same terms as 2 ln(1+y) - y (2 - r) and ln(1+y) - r (no cancellation)
-            const float r1 = y / (1.0f + y);
-            const float ta = y < 1.0f ? fmaf(2.0f, Dy, y * r1) : fmaf(2.0f, Ly, -y * (2.0f - r1));
-            const float tb = y < 1.0f ? fmaf(y, r1, Dy) : Ly - r1;
-            deq = beta > 0 ? sdf[7] * (sdf[6] * ta - (float)a.s1 * tb) : (float)NAN;
-        } else {
-            const double E = a.E[k];
-            double Eq = E / alpha;
-            double L = 0, y = 0;
-            if (beta > 0) {
-                y = alpha * E / beta;
-                L = log1p(y);
-                Eq = y < 1.0 ? -(beta / (alpha * alpha)) * (L - y) : E / alpha - (beta / (alpha * alpha)) * L;
-            }
-            mu = LY * Eq;
-            f[F_MUH] = mu;
-            const double D = L - y, r1 = y / (1.0 + y);
-            deq = beta > 0 ? (a.s0 * (beta / alpha) * (2.0 * D + y * r1) - a.s1 * (D + y * r1)) / (alpha * alpha) : NAN;
-        }
-        // in FP64 and rounded once: FP32 copies of a, b, c would scale every column's variance alike
-        var = (R)fma((double)mu, fma(rc, (double)mu, rb), ra);
-        f[F_DEQ] = deq;
-        if constexpr (RES == 0) {
-            const R sig = sqrt(var), isg = R(1) / sig;
-            f[F_A] = isg;
-            if constexpr (sizeof(R) == 4) Nk = fmaf(isg, NORM_HI, isg * NORM_LO);
-            const R zc = sqrt(R(2) * (R)a.cut);
-            xmin = mu - zc * sig;
-            xmax = mu + zc * sig;
-        } else {
-            const R d = mu * mu / var, s = var / mu;
+            R mu, var, deq;
             if constexpr (sizeof(R) == 4) {
-                f[F_A] = 1.0f / mu;
-                f[F_B] = d;
-                f[F_C] = -1.0f / s;
-                if (d >= 8.0f) {
-                    // density at the mean: exp(-corr(d)) / (sigma sqrt(2 pi)), corr = Stirling remainder
-                    const float id = 1.0f / d, id2 = id * id;
-                    const float corr = id * (1.0f / 12 - id2 * (1.0f / 360 - id2 * (1.0f / 1260 - id2 * (1.0f / 1680))));
-                    const float nq = expf(-corr) * rsqrtf(var);
-                    Nk = fmaf(nq, NORM_HI, nq * NORM_LO);
-                    f[F_KAPPA] = 0.5f * id + id2 * (1.0f / 12 - id2 * (1.0f / 120 - id2 * (1.0f / 252 - id2 * (1.0f / 240))));
-                } else {
-                    const double dd = (double)mu * (double)mu / (double)var, sd = (double)var / (double)mu;
-                    Nk = (float)(exp((dd - 1.0) * log((double)mu) - (double)mu / sd - dd * log(sd) - lgamma(dd)) /
-                                 (1.0 + EX2_MEAN_REL_ERR));
-                    f[F_KAPPA] = (float)(log(dd) - digamma_d(dd));
+                // E_q = E/alpha - (beta/alpha^2) ln(1 + alpha E / beta), mean in double-float
+                const float Eh = a.E_hi[k], El = a.E_lo[k];
+                float qh, ql;
+                df_mul(Eh, El, sdf[0], sdf[1], qh, ql);
+                float Dy = 0.f, y = 0.f, Ly = 0.f;
+                if (beta > 0) {
+                    y = Eh * sdf[5];
+                    Dy = log1pmx2_f(y, Ly);
+                    if (y < 1.0f) { qh = -sdf[4] * Dy; ql = 0.f; }
+                    else df_add(qh, ql, -sdf[4] * Ly, qh, ql);
                 }
+                float muh, mul;
+                df_mul(qh, ql, sdf[2], sdf[3], muh, mul);
+                f[F_MUH] = muh; f[F_MUL] = mul;
+                mu = muh;
+                // dE_q/dkB = (1/alpha^2) [ s0 (beta/alpha) (2 D + y r) - s1 (D + y r) ], r = y/(1+y);
+                // for y >= 1 the same terms as 2 ln(1+y) - y (2 - r) and ln(1+y) - r (no cancellation)
+                const float r1 = y / (1.0f + y);
+                const float ta = y < 1.0f ? fmaf(2.0f, Dy, y * r1) : fmaf(2.0f, Ly, -y * (2.0f - r1));
+                const float tb = y < 1.0f ? fmaf(y, r1, Dy) : Ly - r1;
+                deq = beta > 0 ? sdf[7] * (sdf[6] * ta - (float)a.s1 * tb) : (float)NAN;
             } else {
-                f[F_A] = -d * log(s) - lgamma(d);
-                f[F_B] = d - 1.0;
-                f[F_C] = 1.0 / s;
-                f[F_KAPPA] = log(s) + digamma_d(d);
+                const double E = a.E[k];
+                double Eq = E / alpha;
+                double L = 0, y = 0;
+                if (beta > 0) {
+                    y = alpha * E / beta;
+                    L = log1p(y);
+                    Eq = y < 1.0 ? -(beta / (alpha * alpha)) * (L - y) : E / alpha - (beta / (alpha * alpha)) * L;
+                }
+                mu = LY * Eq;
+                f[F_MUH] = mu;
+                const double D = L - y, r1 = y / (1.0 + y);
+                deq = beta > 0 ? (a.s0 * (beta / alpha) * (2.0 * D + y * r1) - a.s1 * (D + y * r1)) / (alpha * alpha) : NAN;
             }
-            // conservative band from bounds on h(t) = (d-1) D(t) - t, x = mu (1 + t)
-            const R c = (R)a.cut;
-            R thi;
-            if (d >= R(1)) {
-                const R bq = R(2) - R(2) * c;
-                thi = (-bq + sqrt(bq * bq + R(8) * c * (d + R(1)))) / (R(2) * (d + R(1)));
+            // in FP64 and rounded once: FP32 copies of a, b, c would scale every column's variance alike
+            var = (R)fma((double)mu, fma(rc, (double)mu, rb), ra);
+            f[F_DEQ] = deq;
+            if constexpr (RES == 0) {
+                const R sig = sqrt(var), isg = R(1) / sig;
+                f[F_A] = isg;
+                if constexpr (sizeof(R) == 4) Nk = fmaf(isg, NORM_HI, isg * NORM_LO);
+                const R zc = sqrt(R(2) * (R)a.cut);
+                xmin = mu - zc * sig;
+                xmax = mu + zc * sig;
             } else {
-                thi = c / d;
-            }
-            // for d > 1, h + cut is concave: Newton steps from these outer bounds stay outside the band
-            if (d > R(1)) {
-                for (int it = 0; it < 3; ++it) {
-                    const R L1 = log1p(thi);
-                    const R h = (d - R(1)) * (L1 - thi) - thi + c;
-                    const R hp = -(d - R(1)) * thi / (R(1) + thi) - R(1);
-                    thi = thi - h / hp;
-                }
-            }
-            xmax = mu * (R(1) + thi);
-            xmin = 0;
-            if (d > R(1)) {
-                R tlo = -(R(1) + sqrt(R(1) + R(2) * c * (d - R(1)))) / (d - R(1));
-                if (tlo > R(-1)) {
-                    for (int it = 0; it < 3; ++it) {
-                        const R L1 = log1p(tlo);
-                        const R h = (d - R(1)) * (L1 - tlo) - tlo + c;
-                        const R hp = -(d - R(1)) * tlo / (R(1) + tlo) - R(1);
-                        tlo = fmax(tlo - h / hp, tlo);
-                    }
-                    xmin = mu * (R(1) + tlo);
-                }
-            }
-            if (tb_g_zero<FAST>(a, g)) {
-                const R x1 = (R)a.edges[tb_g_edge_off<FAST>(a, g) + 1];
-                if (xmin <= x1) {
-                    R P, Pd, Ps2;
-                    gamma_bin_zero<R>(d, s, x1, P, Pd, Ps2);
-                    f[F_P0] = P / Nk;
-                    if constexpr (sizeof(R) == 4) {
-                        // mixed adjoint: (mu/d) dP/dmu at fixed variance, s^2 dP/dvar at fixed mean
-                        f[F_P0D] = (R(2) * Pd - Ps2 / mu) / Nk;
-                        f[F_P0S] = (Ps2 / mu - Pd) / Nk;
+                const R d = mu * mu / var, s = var / mu;
+                if constexpr (sizeof(R) == 4) {
+                    f[F_A] = 1.0f / mu;
+                    f[F_B] = d;
+                    f[F_C] = -1.0f / s;
+                    if (d >= 8.0f) {
+                        // density at the mean: exp(-corr(d)) / (sigma sqrt(2 pi)), corr = Stirling remainder
+                        const float id = 1.0f / d, id2 = id * id;
+                        const float corr = id * (1.0f / 12 - id2 * (1.0f / 360 - id2 * (1.0f / 1260 - id2 * (1.0f / 1680))));
+                        const float nq = expf(-corr) * rsqrtf(var);
+                        Nk = fmaf(nq, NORM_HI, nq * NORM_LO);
+                        f[F_KAPPA] = 0.5f * id + id2 * (1.0f / 12 - id2 * (1.0f / 120 - id2 * (1.0f / 252 - id2 * (1.0f / 240))));
                     } else {
-                        f[F_P0D] = Pd; f[F_P0S] = Ps2;
+                        const double dd = (double)mu * (double)mu / (double)var, sd = (double)var / (double)mu;
+                        Nk = (float)(exp((dd - 1.0) * log((double)mu) - (double)mu / sd - dd * log(sd) - lgamma(dd)) /
+                                     (1.0 + EX2_MEAN_REL_ERR));
+                        f[F_KAPPA] = (float)(log(dd) - digamma_d(dd));
+                    }
+                } else {
+                    f[F_A] = -d * log(s) - lgamma(d);
+                    f[F_B] = d - 1.0;
+                    f[F_C] = 1.0 / s;
+                    f[F_KAPPA] = log(s) + digamma_d(d);
+                }
+                // conservative band from bounds on h(t) = (d-1) D(t) - t, x = mu (1 + t)
+                const R c = (R)a.cut;
+                R thi;
+                if (d >= R(1)) {
+                    const R bq = R(2) - R(2) * c;
+                    thi = (-bq + sqrt(bq * bq + R(8) * c * (d + R(1)))) / (R(2) * (d + R(1)));
+                } else {
+                    thi = c / d;
+                }
+                // for d > 1, h + cut is concave: Newton steps from these outer bounds stay outside the band
+                if (d > R(1)) {
+                    for (int it = 0; it < 3; ++it) {
+                        const R L1 = log1p(thi);
+                        const R h = (d - R(1)) * (L1 - thi) - thi + c;
+                        const R hp = -(d - R(1)) * thi / (R(1) + thi) - R(1);
+                        thi = thi - h / hp;
+                    }
+                }
+                xmax = mu * (R(1) + thi);
+                xmin = 0;
+                if (d > R(1)) {
+                    R tlo = -(R(1) + sqrt(R(1) + R(2) * c * (d - R(1)))) / (d - R(1));
+                    if (tlo > R(-1)) {
+                        for (int it = 0; it < 3; ++it) {
+                            const R L1 = log1p(tlo);
+                            const R h = (d - R(1)) * (L1 - tlo) - tlo + c;
+                            const R hp = -(d - R(1)) * tlo / (R(1) + tlo) - R(1);
+                            tlo = fmax(tlo - h / hp, tlo);
+                        }
+                        xmin = mu * (R(1) + tlo);
+                    }
+                }
+                if (tb_g_zero<FAST>(a, g)) {
+                    const R x1 = (R)a.edges[tb_g_edge_off<FAST>(a, g) + 1];
+                    if (xmin <= x1) {
+                        R P, Pd, Ps2;
+                        gamma_bin_zero<R>(d, s, x1, P, Pd, Ps2);
+                        f[F_P0] = P / Nk;
+                        if constexpr (sizeof(R) == 4) {
+                            // mixed adjoint: (mu/d) dP/dmu at fixed variance, s^2 dP/dvar at fixed mean
+                            f[F_P0D] = (R(2) * Pd - Ps2 / mu) / Nk;
+                            f[F_P0S] = (Ps2 / mu - Pd) / Nk;
+                        } else {
+                            f[F_P0D] = Pd; f[F_P0S] = Ps2;
+                        }
                     }
                 }
             }
-        }
         }  // RES 0 / 1
         f[F_N] = Nk;
         f[F_XMIN] = xmin;
