@@ -60,10 +60,11 @@ Parity status of the gradient of the gamma and generalized-gamma responses with
 respect to the shape: the derivative of the regularised incomplete gamma function
 with respect to its shape has no library routine, so it is taken by fourth-order
 central differences in the shape (pinned against arbitrary-precision values in
-the tests).  The generalized gamma's moment matching is solved by Newton's method
-on Stirling-series differences of log-gamma functions (pinned against 40-digit
-moments).  Everything else is evaluated from closed forms or library special
-functions.
+the tests).  The generalized gamma's moment matching is solved by bracketed
+Newton iteration on its defining equation, with the log-gamma differences taken
+from their integral forms over the trigamma function where the log-gammas
+themselves would cancel (pinned against 40-digit moments).  Everything else is
+evaluated from closed forms or library special functions.
 """
 from __future__ import annotations
 
@@ -188,97 +189,114 @@ def _gamma_pdf_times_y(d, y):
 # every column's (d, s) follow from its mean and variance by moment matching,
 #     mu = s Gamma(x + a) / Gamma(x),   mu^2 + var = s^2 Gamma(x + 2a) / Gamma(x),   x = d/p, a = 1/p;
 # p = 1 is the gamma reading.  Eliminating s leaves one equation for x,
-#     H(x) = lnGamma(x + 2a) + lnGamma(x) - 2 lnGamma(x + a) = ln(1 + var/mu^2),
-# whose two sides are O(1/x): the log-gamma values themselves (O(x ln x)) cancel, so H and the other
-# log-gamma / digamma differences are evaluated from Stirling's series (Abramowitz & Stegun 6.1.40,
-# 6.3.18) with the leading terms combined analytically, after the recurrences lnGamma(z+1) =
-# lnGamma(z) + ln z and psi(z+1) = psi(z) + 1/z have moved the argument to >= 10.
-
-_BERNOULLI = (1.0 / 6, -1.0 / 30, 1.0 / 42, -1.0 / 30, 5.0 / 66, -691.0 / 2730, 7.0 / 6, -3617.0 / 510)  # B_2..B_16
-_X_STIRLING = 10.0
-
-
-def _lgamma_tail(z):
-    """lnGamma(z) - [(z - 1/2) ln z - z + ln(2 pi)/2] by the asymptotic series (z >= 10)."""
-    return sum(b / (2 * n * (2 * n - 1) * z ** (2 * n - 1)) for n, b in enumerate(_BERNOULLI, 1))
-
-
-def _digamma_tail(z):
-    """psi(z) - [ln z - 1/(2z)] by the asymptotic series (z >= 10)."""
-    return -sum(b / (2 * n * z ** (2 * n)) for n, b in enumerate(_BERNOULLI, 1))
+#     H(x) = lnGamma(x + 2a) + lnGamma(x) - 2 lnGamma(x + a) = ln(1 + var/mu^2).
+#
+# H and the other differences below are O(1/x) (or O(ln x)) while each log-gamma is O(x ln x), so
+# for large x the library log-gammas would cancel.  There they are taken from the textbook integral
+# forms of the differences instead (lnGamma' = psi, psi' = psi_1, psi_1' = psi_2):
+#     lnGamma(x + c) - lnGamma(x) = int_0^c psi(x + t) dt,
+#     psi(x + c) - psi(x)         = int_0^c psi_1(x + t) dt,
+#     H(x, a) = int_0^a int_0^a psi_1(x + t + u) du dt = int_0^2a psi_1(x + v) min(v, 2a - v) dv,
+#     dH/dx   = int_0^2a psi_2(x + v) min(v, 2a - v) dv,
+# with positive, smooth integrands (the nearest pole, at v = -x, lies well outside [0, 2a]),
+# integrated by Gauss-Legendre quadrature on [0, a] and [a, 2a] where the kernel is linear.  Below
+# _X_DIRECT every term is O(1) and the library differences are used as they stand.
+_X_DIRECT = 2.0
+_GL_X, _GL_W = np.polynomial.legendre.leggauss(12)
 
 
-def _shift(x):
+def _trigamma(z):
+    return special.polygamma(1, z)
+
+
+def _tetragamma(z):
+    return special.polygamma(2, z)
+
+
+def _gl(f, x, lo, hi, kernel=None):
+    """int_lo^hi f(x + t) k(t) dt for every element of x (Gauss-Legendre; k = 1 if kernel is None)."""
+    t = 0.5 * (hi - lo) * _GL_X + 0.5 * (hi + lo)
+    w = 0.5 * (hi - lo) * _GL_W * (1.0 if kernel is None else kernel(t))
+    return np.sum(f(x[..., None] + t) * w, axis=-1)
+
+
+def _second_difference(f, x, a):
+    """int_0^2a f(x + v) min(v, 2a - v) dv."""
+    return _gl(f, x, 0.0, a, lambda t: t) + _gl(f, x, a, 2.0 * a, lambda t: 2.0 * a - t)
+
+
+def _by_size(x, direct, integral):
+    """direct(x) below _X_DIRECT, integral(x) from it on (elementwise)."""
     x = np.asarray(x, np.float64)
-    m = np.ceil(np.maximum(0.0, _X_STIRLING - x))
-    return x, m, x + m, int(m.max()) if m.size else 0
+    out = np.empty_like(x)
+    small = x < _X_DIRECT
+    if np.any(small):
+        out[small] = direct(x[small])
+    if np.any(~small):
+        out[~small] = integral(x[~small])
+    return out
 
 
 def lgamma_diff(x, c):
-    """lnGamma(x + c) - lnGamma(x) for x > 0, c >= 0, without the cancellation of two log-gammas."""
-    x, m, xm, mmax = _shift(x)
-    out = (xm - 0.5) * np.log1p(c / xm) + c * np.log(xm + c) - c + _lgamma_tail(xm + c) - _lgamma_tail(xm)
-    for i in range(mmax):
-        out = out - np.where(i < m, np.log1p(c / (x + i)), 0.0)
-    return out
+    """lnGamma(x + c) - lnGamma(x) for x > 0, c >= 0."""
+    return _by_size(x, lambda v: special.gammaln(v + c) - special.gammaln(v),
+                    lambda v: _gl(special.digamma, v, 0.0, c))
 
 
 def digamma_diff(x, c):
     """psi(x + c) - psi(x) for x > 0, c >= 0."""
-    x, m, xm, mmax = _shift(x)
-    out = np.log1p(c / xm) + c / (2.0 * xm * (xm + c)) + _digamma_tail(xm + c) - _digamma_tail(xm)
-    for i in range(mmax):
-        out = out + np.where(i < m, c / ((x + i) * (x + c + i)), 0.0)
-    return out
+    return _by_size(x, lambda v: special.digamma(v + c) - special.digamma(v),
+                    lambda v: _gl(_trigamma, v, 0.0, c))
 
 
 def ggamma_log_moment_ratio(x, a):
     """H(x) = ln[Gamma(x + 2a) Gamma(x) / Gamma(x + a)^2] = ln(E[Y^2a] / E[Y^a]^2), Y ~ Gamma(x, 1)."""
-    x, m, xm, mmax = _shift(x)
-    e = a / xm
-    out = ((xm - 0.5) * np.log1p(-(e / (1.0 + e)) ** 2) + 2.0 * a * np.log1p(a / (xm + a))
-           + _lgamma_tail(xm + 2 * a) - 2.0 * _lgamma_tail(xm + a) + _lgamma_tail(xm))
-    for i in range(mmax):
-        xi = x + i
-        ei = a / xi
-        with np.errstate(divide="ignore", invalid="ignore"):
-            t = np.where(ei < 0.5, np.log1p(-(ei / (1.0 + ei)) ** 2),
-                         np.log(xi) + np.log(xi + 2 * a) - 2.0 * np.log(xi + a))
-        out = out - np.where(i < m, t, 0.0)
-    return out
+    return _by_size(x, lambda v: special.gammaln(v + 2 * a) + special.gammaln(v) - 2.0 * special.gammaln(v + a),
+                    lambda v: _second_difference(_trigamma, v, a))
 
 
 def ggamma_log_moment_ratio_dx(x, a):
-    """dH/dx = psi(x + 2a) - 2 psi(x + a) + psi(x)."""
-    x, m, xm, mmax = _shift(x)
-    out = (np.log1p(-(a / (xm + a)) ** 2) - a * a / (xm * (xm + a) * (xm + 2 * a))
-           + _digamma_tail(xm + 2 * a) - 2.0 * _digamma_tail(xm + a) + _digamma_tail(xm))
-    for i in range(mmax):
-        xi = x + i
-        out = out - np.where(i < m, 2.0 * a * a / (xi * (xi + a) * (xi + 2 * a)), 0.0)
-    return out
+    """dH/dx = psi(x + 2a) - 2 psi(x + a) + psi(x) (negative: H falls as x grows)."""
+    return _by_size(x, lambda v: special.digamma(v + 2 * a) - 2.0 * special.digamma(v + a) + special.digamma(v),
+                    lambda v: _second_difference(_tetragamma, v, a))
 
 
 def ggamma_shape_scale(mu, var, p):
     """Moment matching for the generalized gamma of power p: shape d and scale s with mean mu and
-    variance var.  H(x) = ln(1 + var/mu^2) is solved for x = d/p by Newton's method on ln H against
-    ln x (H falls monotonically from +inf to 0); s = mu Gamma(x) / Gamma(x + 1/p)."""
+    variance var.  H(x) = r, r = ln(1 + var/mu^2), is solved for x = d/p column by column by
+    Newton's method in x, safeguarded by a bracket: H falls monotonically from +inf (x -> 0) to 0
+    (x -> inf), so every evaluation moves one end of the bracket, and a Newton step that leaves the
+    bracket is replaced by its geometric midpoint (or by a factor-4 move while one end is open).
+    The start is the large-x limit H ~ a^2/x for r <= 1, else the small-x limit
+    H ~ lnGamma(2a) - 2 lnGamma(a) - ln x.  Then s = mu Gamma(x) / Gamma(x + 1/p)."""
     mu = np.asarray(mu, np.float64)
     var = np.asarray(var, np.float64)
     a = 1.0 / p
     r = np.log1p(var / (mu * mu))
-    u = np.log(a * a / r)  # large-x limit H ~ a^2 / x
-    for _ in range(80):
-        x = np.exp(u)
-        h = ggamma_log_moment_ratio(x, a)
-        g = np.log(h) - np.log(r)
-        step = np.clip(-g * h / (x * ggamma_log_moment_ratio_dx(x, a)), -5.0, 5.0)
-        u = u + step
-        if np.all(np.abs(g) < 1e-14):
+    x = np.where(r <= 1.0, a * a / r, np.exp(special.gammaln(2 * a) - 2.0 * special.gammaln(a) - r))
+    lo = np.zeros_like(x)
+    hi = np.full_like(x, np.inf)
+    active = np.ones(x.shape, bool)
+    for _ in range(400):
+        i = np.nonzero(active)
+        xi = x[i]
+        h = ggamma_log_moment_ratio(xi, a) - r[i]
+        lo[i] = np.where(h > 0.0, xi, lo[i])
+        hi[i] = np.where(h <= 0.0, xi, hi[i])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            step = h / ggamma_log_moment_ratio_dx(xi, a)
+        xn = xi - step
+        # quadratic convergence: once the Newton step is below 1e-12 x, the point it reaches is at
+        # rounding level
+        conv = np.abs(step) <= 1e-12 * xi
+        inside = (xn > lo[i]) & (xn < hi[i])
+        fallback = np.where(np.isinf(hi[i]), 4.0 * xi, np.where(lo[i] > 0.0, np.sqrt(lo[i] * hi[i]), 0.25 * hi[i]))
+        x[i] = np.where(inside | conv, xn, fallback)
+        active[i] = ~conv
+        if not np.any(active):
             break
     else:
         raise FloatingPointError("generalized-gamma moment matching did not converge")
-    x = np.exp(u)
     return p * x, mu * np.exp(-lgamma_diff(x, a))
 
 
@@ -668,6 +686,66 @@ def nll_grad_fd(work, params, counts, windows=None, rel=1e-5, which=None):
         d2 = (f(2 * h) - f(-2 * h)) / (4 * h)
         g[i] = (4.0 * d1 - d2) / 3.0
     return g
+
+
+def fisher_diagonal(work, params, windows=None, rel=1e-4):
+    """Diagonal of the Fisher information of the likelihood (Eq. LL) at params,
+
+        F_ii = sum_d sum_{j in window_d} (d mu_dj / d theta_i)^2 / mu_dj  [+ secondary pieces]
+               + 1 / sigma_i^2 for a pulled parameter,
+
+    the variance of dNLL/dtheta_i under Poisson fluctuations of the counts, i.e. the statistical
+    scale of each gradient component.  The expected counts are linear in the rates, so a parameter
+    that fills only rate slots has d mu / d theta_i = (its species' expected counts) / theta_i; the
+    derivatives for the other parameters are central differences with step rel * |theta_i| (a
+    scale needs no more precision than that).  Secondary pieces (section 2.4) add
+    (d mu_qm / d theta_i)^2 / mu_qm over the slices inside the window.
+    """
+    params = np.asarray(params, np.float64)
+    wins = _windows(work, windows)
+    sec = work.get("secondary")
+    S = np.asarray(work["spectra"]).shape[0]
+    sm = np.asarray(work["slot_map"])
+
+    def per_species(p):
+        """expected counts per species over the window bins and active secondary bins: (bins, S)"""
+        out = []
+        for d, (lo, hi) in enumerate(wins):
+            out.append(expected_per_species(work, p, d)[lo:hi])
+            if sec is not None and sec[d] is not None:
+                act = _active_slices(work, d, lo, hi)
+                if act:
+                    N, _ = secondary_expected(work, p, d)
+                    P = secondary_shapes(work, d)
+                    out.append(np.einsum("sq,sqm->qms", N[:, act], P[:, act, :]).reshape(-1, S))
+        return out
+    base = per_species(params)
+    mu = np.concatenate([b.sum(axis=1) for b in base])
+    ok = mu > 0
+    F = np.zeros(params.size)
+    for i in range(params.size):
+        slots = np.argwhere(sm == i)
+        if slots.size and np.all(slots[:, 1] < S) and params[i] != 0.0:
+            # rate: mu is linear in it; blocks follow the datasets, a secondary block after its dataset
+            parts, k = [], 0
+            for d, (lo, hi) in enumerate(wins):
+                rows = [s for dd, s in slots if dd == d]
+                for blk in ([0, 1] if (sec is not None and sec[d] is not None and
+                                       _active_slices(work, d, lo, hi)) else [0]):
+                    b = base[k]; k += 1
+                    parts.append(b[:, rows].sum(axis=1) / params[i] if rows else np.zeros(b.shape[0]))
+            dm = np.concatenate(parts)
+        else:
+            h = rel * (abs(params[i]) if params[i] != 0 else 1e-3)
+            pp, pm = params.copy(), params.copy()
+            pp[i] += h
+            pm[i] -= h
+            dm = (np.concatenate([b.sum(axis=1) for b in per_species(pp)])
+                  - np.concatenate([b.sum(axis=1) for b in per_species(pm)])) / (2.0 * h)
+        F[i] = float(np.sum(dm[ok] ** 2 / mu[ok]))
+    for k, p in enumerate(np.asarray(work["pull_param"], np.int64)):
+        F[p] += 1.0 / work["pull_width"][k] ** 2
+    return F
 
 
 # ----------------------------------------------------------------- batch ----
