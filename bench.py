@@ -225,50 +225,101 @@ def gradient_errors(gm, g64, F):
 
 
 # ------------------------------------------------------------- oracle ------
-ORACLE_FINE = 2500     # fine columns of the oracle sample (the workload has 20000)
-ORACLE_SCALE = 20000 / ORACLE_FINE
-ORACLE_SAMPLE = ("1 toy (toy 0 of the batch: 2 datasets x 1200 bins, its own window), NLL + full gradient, "
-                 "FP64 oracle, one thread, on a 2500-point fine grid; time scaled x8 to 20000 points "
-                 "(the oracle's cost is linear in the fine columns)")
+ORACLE_FINE = 2500     # fine columns of the oracle sample (the timed GPU workload has 20000)
+ORACLE_SAMPLE = ("NLL + full gradient of one toy per process and step (toys of the batched workload: 2 datasets x "
+                 "1200 bins, 16 species, each toy its own counts, window and parameters), FP64 oracle, on a "
+                 "2500-point fine grid (the GPU workload has 20000 points)")
+ORACLE_FULL_GRID = ("x 2500/20000: the oracle's cost is linear in the fine columns (every (bin, column) pair is "
+                    "evaluated); an estimate, not a measurement")
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+_ORACLE = {}
 
 
-def oracle_step_seconds(n_steps):
-    """Time the oracle in a child process (single-threaded BLAS), one toy per step."""
-    code = r"""
-import json, os, sys, time
-sys.path.insert(0, %r)
-import numpy as np
-from oracle import gsn_oracle as O
-from paper_1812_05686_gb300 import inputs as I
-w = I.borexino_like(n_bins=1200, n_fine=%d)
-mu0 = np.loadtxt(os.path.join(%r, "tests", "golden", "borexino_like_1200_mu0.txt"))
-b = I.toy_batch(w, [mu0[:1200], mu0[1200:]], n_toys=1, seed0=1000)
-ts = []
-for i in range(%d):
-    t = time.time()
-    O.nll(w, b["params"][0], b["counts"][0], b["windows"][0])
-    O.nll_grad(w, b["params"][0], b["counts"][0], b["windows"][0])
-    ts.append(time.time() - t)
-print(json.dumps(ts))
-""" % (ROOT, ORACLE_FINE, ROOT, n_steps)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    return [t * ORACLE_SCALE for t in json.loads(r.stdout.strip().splitlines()[-1])]
+def _oracle_setup():
+    import numpy as np
+
+    from oracle import gsn_oracle as O
+    from paper_1812_05686_gb300 import inputs as I
+    if not _ORACLE:
+        w = I.borexino_like(n_bins=1200, n_fine=ORACLE_FINE)
+        mu0 = np.loadtxt(os.path.join(ROOT, "tests", "golden", "borexino_like_1200_mu0.txt"))
+        _ORACLE.update(O=O, I=I, w=w, mu=[mu0[:1200], mu0[1200:]])
+    return _ORACLE
+
+
+def _oracle_warm(_):
+    """Pool job: import the oracle and build the sample workload (untimed); the pause lets every
+    process of the pool take one of these jobs."""
+    _oracle_setup()
+    time.sleep(1.0)
+    return os.getpid()
+
+
+def _oracle_toy(t):
+    """Pool job: the oracle's NLL and gradient of toy t of the sample workload; returns seconds."""
+    o = _oracle_setup()
+    b = o["I"].toy_batch(o["w"], o["mu"], n_toys=1, seed0=1000 + t)
+    t0 = time.perf_counter()
+    o["O"].nll(o["w"], b["params"][0], b["counts"][0], b["windows"][0])
+    o["O"].nll_grad(o["w"], b["params"][0], b["counts"][0], b["windows"][0])
+    return time.perf_counter() - t0
+
+
+def oracle_steps(n_steps, procs):
+    """Wall seconds of n_steps oracle steps; a step is one toy on each of `procs` processes at once
+    (spawn pool, one BLAS thread per process)."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+    os.environ.update({k: "1" for k in _THREAD_VARS})
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            pool.map(_oracle_warm, range(procs), chunksize=1)
+            out = []
+            for s in range(n_steps):
+                t0 = time.perf_counter()
+                pool.map(_oracle_toy, [s * procs + i for i in range(procs)], chunksize=1)
+                out.append(time.perf_counter() - t0)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return out
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_baseline_record():
+    """The oracle on this host: one process per core over toys (the baseline value) and one process
+    alone, both measured on the 2500-point sample; the full-grid figure is a separate estimate."""
+    cores = host_cores()
+    single = oracle_steps(1, 1)[0]
+    allc = oracle_steps(1, cores)[0]
+    return {"value": cores / allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": ORACLE_SAMPLE + f"; {cores} processes, one toy each, timed together",
+            "fine_points": ORACLE_FINE,
+            "single_thread": {"value": 1.0 / single, "unit": UNIT, "cores": 1, "seconds_per_toy": single},
+            "full_grid_estimate": {"value": cores / allc * ORACLE_FINE / 20000, "unit": UNIT, "basis": ORACLE_FULL_GRID}}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    ts = oracle_step_seconds(args.warmup + args.steps)[args.warmup:]
+    cores = host_cores()
+    ts = oracle_steps(args.warmup + args.steps, cores)[args.warmup:]
     sec = sum(ts) / len(ts)
-    value = 1.0 / sec
+    value = cores / sec
+    sample = ORACLE_SAMPLE + f"; {cores} processes, one toy each per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "toys_per_step": 1, "sample": ORACLE_SAMPLE},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE},
+            "config": {"workload": WORKLOAD.replace("20000 fine points", f"{ORACLE_FINE} fine points"),
+                       "toys_per_step": cores, "fine_points": ORACLE_FINE, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "full_grid_estimate": {"value": value * ORACLE_FINE / 20000, "unit": UNIT, "basis": ORACLE_FULL_GRID},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -335,24 +386,33 @@ def run_ours(args, rank, world, local_rank):
     nll_mixed = nll.cpu().numpy()
     value = world * T / (ms * 1e-3)
 
-    # FP64 path on the first toys: throughput and |dNLL| against the mixed path (--fp64-toys 0: skipped)
+    # FP64 path on a stride of toys over the whole batch (every launch chunk): throughput and the
+    # mixed path's errors against it (--fp64-toys 0: skipped)
     nf = min(args.fp64_toys, T)
     fp64 = None
     if nf > 0:
+        idx = (np.arange(nf) * T) // nf
+        sel = torch.from_numpy(idx).to(dev)
+        p_s, c_s, w_s = params[sel].contiguous(), counts[sel].contiguous(), wins[sel].contiguous()
         ctx64 = gsn.context_from_workload(w, gsn.GSN_FP64, device=local_rank, stream=stream.cuda_stream)
         nll64 = torch.empty(nf, dtype=torch.float64, device=dev)
         grad64 = torch.empty(nf, P, dtype=torch.float64, device=dev)
-        ctx64.eval_grad_batch_dev(params[:nf], counts[:nf], wins[:nf], nll64, grad64, None)
+        torch.cuda.synchronize(dev)
+        ctx64.eval_grad_batch_dev(p_s, c_s, w_s, nll64, grad64, None)
         torch.cuda.synchronize(dev)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        ctx64.eval_grad_batch_dev(params[:nf], counts[:nf], wins[:nf], nll64, grad64, None)
+        ctx64.eval_grad_batch_dev(p_s, c_s, w_s, nll64, grad64, None)
         f1.record(stream)
         torch.cuda.synchronize(dev)
         fp64_value = nf / (f0.elapsed_time(f1) * 1e-3)
-        dnll = float(np.max(np.abs(nll64.cpu().numpy() - nll_mixed[:nf])))
-        gerrs = gradient_errors(grad[:nf].cpu().numpy(), grad64.cpu().numpy(), fisher_diagonal(ctx64, w, w["theta0"]))
-        fp64 = {"value": fp64_value, "unit": UNIT, "toys": nf, "speedup_mixed_over_fp64": value / world / fp64_value,
+        dnll = float(np.max(np.abs(nll64.cpu().numpy() - nll_mixed[idx])))
+        gerrs = gradient_errors(grad.cpu().numpy()[idx], grad64.cpu().numpy(), fisher_diagonal(ctx64, w, w["theta0"]))
+        chunk = 4096
+        fp64 = {"value": fp64_value, "unit": UNIT, "toys": nf,
+                "toy_sample": f"every {T // nf}th toy of the {T} (toys {int(idx[0])}..{int(idx[-1])}; launch chunks "
+                              f"of {chunk}: {sorted(set(int(i) // chunk for i in idx))})",
+                "speedup_mixed_over_fp64": value / world / fp64_value,
                 "max_abs_dnll_mixed_vs_fp64": dnll, "grad_normwise_err_mixed_vs_fp64": gerrs["normwise_max"],
                 "grad_err_mixed_vs_fp64": gerrs}
 
@@ -398,8 +458,7 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        ts = oracle_step_seconds(1)
-        cpu = {"value": 1.0 / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE}
+        cpu = cpu_baseline_record()
 
     launches = sum(v[1] for v in prof.values())
     if rank == 0:

@@ -316,7 +316,11 @@ void* gsn_stream(gsn_ctx* ctx);
  *   status_dev  [1] device output (0 or a GSN_ERR_* code of the step), or NULL
  * Counts and windows are those of gsn_set_data.  The context's problem must
  * already be on the device: call gsn_eval or gsn_eval_grad once during set-up
- * (else GSN_ERR_STATE).  The first call on a device looks up the array's
+ * (else GSN_ERR_STATE), and the context's device must be the current device
+ * (else GSN_ERR_STATE; the call does not switch devices).  The work is split
+ * by the untuned occupancy plan, so in the mixed-precision mode the result may
+ * differ from gsn_eval_grad's (which may use an autotuned plan) in the last
+ * FP32 bits of its partial sums.  The first call on a device looks up the array's
  * device address; make that first call before any stream capture.  Problems
  * needing more scratch than the array holds are rejected with GSN_ERR_ARG and
  * a message giving the size needed.  Enqueued on the context's stream without

@@ -1502,6 +1502,12 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
         return fail(c, GSN_ERR_STATE, "the problem is not on the device yet: call gsn_eval or gsn_eval_grad once first");
     if (c->base.nsec)
         return fail(c, GSN_ERR_ARG, "the no-allocation entry point does not take secondary observables");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != c->dev) {
+        cudaGetLastError();
+        return fail(c, GSN_ERR_STATE, "the context's device (" + std::to_string(c->dev) + ") must be the current "
+                    "device (" + std::to_string(cur) + ") when gsn_eval_grad_noalloc is called");
+    }
     std::string err;
     unsigned char* base = static_cast<unsigned char*>(noalloc_address(c->dev, err));
     if (!base) return fail(c, GSN_ERR_CUDA, err);

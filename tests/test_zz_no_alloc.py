@@ -24,10 +24,23 @@ def _normwise(g, ref):
     return float(np.max(np.abs(g - ref)) / max(float(np.max(np.abs(ref))), 1.0))
 
 
+def _workload(kind):
+    """The two-dataset gamma workload; with a free-power generalized gamma (its scratch holds the
+    adjoint's per-column coefficient records); or with Monte Carlo template species (their rate
+    partials go through the deviance scratch)."""
+    base = I.borexino_like(n_bins=320, n_fine=3000)
+    if kind == "ggamma":
+        return I.with_power(base, 1.3)
+    if kind == "templates":
+        return I.with_templates(base, 2)
+    return base
+
+
+@pytest.mark.parametrize("kind", ["gamma", "ggamma", "templates"])
 @pytest.mark.parametrize("precision", [gsn.GSN_FP64, gsn.GSN_MIXED])
-def test_noalloc_matches_allocating_entry_point(precision):
+def test_noalloc_matches_allocating_entry_point(precision, kind):
     torch = pytest.importorskip("torch")
-    w = I.borexino_like(n_bins=320, n_fine=3000)
+    w = _workload(kind)
     mu = [O.expected_counts(w, w["theta0"], d) for d in range(2)]
     n = np.concatenate([I.poisson_counts(m, 41 + d) for d, m in enumerate(mu)])
     ctx = gsn.context_from_workload(w, precision, counts=n)
