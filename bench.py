@@ -211,17 +211,21 @@ def fisher_diagonal(ctx64, w, theta):
     return F
 
 
-def gradient_errors(gm, g64, F):
+def gradient_errors(gm, g64, F, names=None):
     """Mixed-vs-FP64 gradient errors per toy: normwise and per component on the Fisher scale."""
     import numpy as np
     norm = np.max(np.abs(gm - g64), axis=1) / np.maximum(np.max(np.abs(g64), axis=1), 1.0)
-    fish = np.max(np.abs(gm - g64) / (np.abs(g64) + np.sqrt(F)[None, :]), axis=1)
+    comp = np.abs(gm - g64) / np.maximum(np.abs(g64) + np.sqrt(F)[None, :], 1.0)
+    fish = np.max(comp, axis=1)
+    worst = int(np.argmax(np.max(comp, axis=0)))
     return {"normwise_max": float(norm.max()), "normwise_median": float(np.median(norm)),
             "normwise_p99": float(np.percentile(norm, 99)), "toys_normwise_above_1e-5": int(np.sum(norm >= 1e-5)),
             "fisher_scaled_max": float(fish.max()), "fisher_scaled_median": float(np.median(fish)),
             "toys_fisher_scaled_above_1e-5": int(np.sum(fish >= 1e-5)),
+            "fisher_scaled_worst_parameter": names[worst] if names else worst,
             "definition": "normwise: ||g - g64||_inf / max(||g64||_inf, 1); fisher_scaled: "
-                          "max_i |g_i - g64_i| / (|g64_i| + sqrt(F_ii)), F the Fisher diagonal at theta0"}
+                          "max_i |g_i - g64_i| / max(|g64_i| + sqrt(F_ii), 1), F the Fisher diagonal at theta0 "
+                          "over the whole histograms"}
 
 
 # ------------------------------------------------------------- oracle ------
@@ -407,7 +411,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         fp64_value = nf / (f0.elapsed_time(f1) * 1e-3)
         dnll = float(np.max(np.abs(nll64.cpu().numpy() - nll_mixed[idx])))
-        gerrs = gradient_errors(grad.cpu().numpy()[idx], grad64.cpu().numpy(), fisher_diagonal(ctx64, w, w["theta0"]))
+        gerrs = gradient_errors(grad.cpu().numpy()[idx], grad64.cpu().numpy(), fisher_diagonal(ctx64, w, w["theta0"]),
+                               w.get("param_names"))
         chunk = 4096
         fp64 = {"value": fp64_value, "unit": UNIT, "toys": nf,
                 "toy_sample": f"every {T // nf}th toy of the {T} (toys {int(idx[0])}..{int(idx[-1])}; launch chunks "
@@ -460,7 +465,8 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_record()
 
-    launches = sum(v[1] for v in prof.values())
+    # the gamma forward's launcher also runs its one-block segment prefix (not a traced kernel class)
+    launches = sum(v[1] for v in prof.values()) + (0 if gg else prof["forward"][1])
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -736,9 +742,11 @@ def run_templates(args):
 
 
 def run_discovery(args):
-    """Toy Monte Carlo discovery test on full histograms: per toy two batched L-BFGS fits of the
-    rates of the dominant species (the smallest of them free, then fixed at 0 as the signal),
-    q0 = 2 (NLL_fixed - NLL_free)."""
+    """Toy Monte Carlo discovery test on the batched pseudo-experiment workload: every toy in its own
+    window (600..1200 bins), two batched L-BFGS fits per toy with all 16 rates free (>= 0), the
+    second with the signal rate fixed at 0; q0 = 2 (NLL_fixed - NLL_free).  Per-toy scales: the
+    rates' 1/sqrt(Fisher) over the whole histograms at theta0, widened per toy by
+    gsn_window_scales_dev for the part of each species outside the toy's window."""
     import numpy as np
     import torch
 
@@ -751,14 +759,11 @@ def run_discovery(args):
     w, b = make_inputs(T, 1000)
     P, D, S = w["n_params"], 2, w["spectra"].shape[0]
     ctx = gsn.context_from_workload(w, gsn.GSN_MIXED, stream=stream.cuda_stream)
-    # rates of the species with more than 2% of the counts are fitted (>= 0), the rest held: nearly
-    # degenerate minor species only slow every fit down
     tot = sum(ctx.expected(w["theta0"], d).sum(axis=0) for d in range(D))
-    fitted = [s for s in range(S) if tot[s] > 0.02 * tot.max()]
-    rates = np.unique(w["slot_map"][:, fitted][w["slot_map"][:, fitted] >= 0])
+    rates = np.unique(w["slot_map"][:, :S][w["slot_map"][:, :S] >= 0])
     free = np.zeros(P, bool)
     free[rates] = True
-    # scales 1 / sqrt(Fisher diagonal) of the rates at theta0 (d mu / d r_s = mu_s / r_s)
+    # scales 1 / sqrt(Fisher diagonal) of the rates at theta0 over the whole histograms (d mu / d r_s = mu_s / r_s)
     fis = np.zeros(P)
     for d in range(D):
         per = ctx.expected(w["theta0"], d)
@@ -770,22 +775,27 @@ def run_discovery(args):
                 fis[p] += float(np.sum((per[ok, s] / w["theta0"][p]) ** 2 / m[ok]))
     scale = np.where(free & (fis > 0), 1.0 / np.sqrt(np.where(fis > 0, fis, 1.0)), 1.0)
     lo = np.where(free, 0.0, -np.inf)
-    # the fitted species with the fewest counts plays the signal
+    # the species with the fewest counts among those with more than 2% of the largest plays the signal
+    fitted = [s for s in range(S) if tot[s] > 0.02 * tot.max()]
     sig = int(w["slot_map"][0, min(fitted, key=lambda s: tot[s])])
     counts = torch.from_numpy(b["counts"]).to(dev)
-    wins = torch.zeros(T, D, 2, dtype=torch.int32, device=dev)  # full histograms
-    wins[:, :, 1] = len(w["edges"][0]) - 1
+    wins = torch.from_numpy(b["windows"].astype(np.int32)).to(dev)
     start = np.repeat(w["theta0"][None, :], T, axis=0)
     start0 = start.copy()
     start0[:, sig] = 0.0
     free0 = free.copy()
     free0[sig] = False
+    torch.cuda.synchronize(dev)
+    EDM = 1e-5  # stop at an estimated distance to the minimum of 1e-5 in NLL (q0 to 2e-5)
 
     def fits():
         x1 = torch.from_numpy(start.copy()).to(dev)
-        f1, e1, s1 = ctx.minimize_batch_dev(x1, counts, wins, free=free, lo=lo, scale=scale, max_evals=300)
+        sc1 = ctx.window_scales_dev(x1, wins, scale=scale)
+        f1, e1, s1 = ctx.minimize_batch_dev(x1, counts, wins, free=free, lo=lo, max_evals=300, scale_dev=sc1,
+                                            edm=EDM)
         x0 = torch.from_numpy(start0.copy()).to(dev)
-        f0, e0, s0 = ctx.minimize_batch_dev(x0, counts, wins, free=free0, lo=lo, scale=scale, max_evals=300)
+        f0, e0, s0 = ctx.minimize_batch_dev(x0, counts, wins, free=free0, lo=lo, max_evals=300, scale_dev=sc1,
+                                            edm=EDM)
         return f1, e1, s1, f0, e0, s0
 
     fits()  # warm-up: plans, graphs
@@ -803,9 +813,10 @@ def run_discovery(args):
     line = {"metric": "profile-likelihood fits/sec (batched toys, discovery test) on 1 GB300", "value": 2 * T / dt,
             "unit": "fits/s", "n_gpus": 1, "ms_total": dt * 1e3, "higher_is_better": True,
             "dtype": "f32 response, f64 deviance and minimiser state", "data": "synthetic",
-            "config": {"workload": WORKLOAD + "; full histograms", "toys": T,
+            "config": {"workload": WORKLOAD + "; every toy in its own window (600..1200 bins)", "toys": T,
                        "free": [w["param_names"][i] for i in np.nonzero(free)[0]], "signal": w["param_names"][sig],
-                       "minimiser": "projected L-BFGS per toy, history 8, gtol 1e-4 scaled"},
+                       "minimiser": "projected L-BFGS per toy, history 16, per-toy window scales, stop at "
+                                    "gtol 1e-4 (scaled) or an estimated distance to the minimum below 1e-5"},
             "evals_per_fit": {"mean": float(ev.mean()), "max": int(ev.max())},
             "status_counts": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
             "q0": {"median": float(np.median(q0)), "p90": float(np.percentile(q0, 90)), "max": float(q0.max())},

@@ -268,7 +268,7 @@ int gsn_eval_grad_batch_dev(gsn_ctx* ctx, int n_toys, const double* params_dev,
 /* Batched minimisation of the NLL of every toy (the profile likelihood of
  * section 4.2; the toy Monte Carlo discovery test takes two calls, with the
  * signal rate free and fixed at 0, and q0 = 2 (NLL_fixed - NLL_free)).  Each
- * toy runs its own projected L-BFGS (FP64 state, history of 8 pairs,
+ * toy runs its own projected L-BFGS (FP64 state, history of 16 pairs,
  * backtracking Armijo line search) in scaled variables u = x / scale; every
  * iteration is one batched NLL + gradient evaluation (as in
  * gsn_eval_grad_batch_dev, with the context's precision) and one update.
@@ -292,6 +292,38 @@ int gsn_minimize_batch_dev(gsn_ctx* ctx, int n_toys, double* params_dev, const d
                            const int* toy_win_dev, const unsigned char* free_mask, const double* lo,
                            const double* hi, const double* scale, int max_evals, double gtol, double ftol,
                            double* nll_dev, int* evals_dev, int* status_dev);
+
+/* gsn_minimize_batch_dev with per-toy scales and an optional distance-to-minimum stopping rule.
+ *   scale_dev  [n_toys][n_params] device (every free parameter's scale finite and > 0, else that
+ *              toy ends with status -1); gsn_window_scales_dev makes such scales for toys fitted
+ *              in windows of their own
+ *   edm        a toy also converges (status 0) once its estimated distance to the minimum,
+ *              -g.d / 2 with d = -H^-1 g the L-BFGS step (the stopping rule of MINUIT's MIGRAD,
+ *              the minimiser the paper's fits use), falls below edm (NLL units; <= 0: not used)
+ * Otherwise as gsn_minimize_batch_dev. */
+int gsn_minimize_batch_scaled_dev(gsn_ctx* ctx, int n_toys, double* params_dev, const double* toy_counts_dev,
+                                  const int* toy_win_dev, const unsigned char* free_mask, const double* lo,
+                                  const double* hi, const double* scale_dev, int max_evals, double gtol, double ftol,
+                                  double edm, double* nll_dev, int* evals_dev, int* status_dev);
+
+/* Per-toy minimiser scales for fits in windows of the toys' own (section 4.2 toy Monte Carlo with
+ * uneven fit ranges).  A toy's window holds part of each species' spectrum, and the rate of a
+ * species that lies mostly outside it is less constrained than scales taken from the whole
+ * histograms (1/sqrt of the Fisher diagonal at theta0, say) assume; a minimiser conditioned with
+ * those reaches its evaluation limit on such toys.  For every toy t:
+ *     scale_dev[t][i] = scale[i] * min(max(sqrt(N_i,whole / N_i,window), 1), max_factor)
+ * for every parameter i that fills only rate slots, with N_i the expected counts of its species at
+ * the toy's parameters (params_dev [n_toys][n_params]) over the whole histograms and inside the
+ * toy's windows (toy_win_dev [n_toys][n_datasets][2]); scale_dev[t][i] = scale[i] for the other
+ * parameters.  The counts of smeared species use a Gaussian response of each column's mean and
+ * variance (a scale needs no better); peaks and templates use their own shapes.
+ *   scale       [n_params] host, > 0 (NULL: 1)
+ *   max_factor  largest factor (<= 0: 100; otherwise >= 1)
+ *   scale_dev   [n_toys][n_params] device output
+ * Synchronous.  Not in the paper, whose fits run one toy at a time with MINUIT.
+ * Errors: GSN_ERR_ARG, GSN_ERR_STATE, GSN_ERR_CUDA. */
+int gsn_window_scales_dev(gsn_ctx* ctx, int n_toys, const double* params_dev, const int* toy_win_dev,
+                          const double* scale, double max_factor, double* scale_dev);
 
 /* Expected counts per bin and species of one dataset (the validation quantity
  * of section 3.1): mu_per_species[n_bins[d]][n_species]; columns of species

@@ -25,6 +25,8 @@ struct Buf {
 struct gsn_ctx {
     gsn_options opt{};
     int dev = 0;
+    double ex2_bias = 0.0;   // measured mean relative error of the SFU exponential on this device
+    Buf wscale_b;            // gsn_window_scales_dev: [T][D][S] counts in the window and whole, scales [P]
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int nsm = 1;
@@ -60,6 +62,7 @@ struct gsn_ctx {
     std::vector<Buf> owned;
     // scratch
     Buf secRq_b, secN_b, secV_b, secW_b, secpart_b, secU_b;  // per-toy buffers of the secondary pieces
+    Buf segbuf;              // forward segment prefix [T*G + 1]
     Buf colbuf, colbuf2, blkbuf, mubuf, wbuf, partbuf, gdirect, devbuf, params, counts_b, win_b, nll_b, grad_b, status_b, Mbuf,
         outbuf;
     unsigned long long scratch_gen = 0;  // bumped whenever a buffer is (re)allocated
@@ -196,6 +199,28 @@ void drop_graphs(gsn_ctx* c) {
     c->graphs.clear();
 }
 
+constexpr double INV_SQRT2PI_H = 0.39894228040143267794;  // 1 / sqrt(2 pi)
+
+// Mean relative error of the SFU exponential over a Gaussian profile on device dev (the bias the
+// mixed column normalisation divides out), measured once per device and process.  Rounded to
+// 1e-13 absolute so that the order of the probe's floating-point atomics cannot change it.
+cudaError_t device_ex2_bias(int dev, double& out) {
+    static std::mutex mu;
+    static double bias[64];
+    static bool have[64] = {false};
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!have[dev]) {
+        double b = 0.0;
+        const cudaError_t e = run_probe(4, 1, &b);
+        if (e != cudaSuccess) return e;
+        bias[dev] = std::nearbyint(b * 1e13) * 1e-13;
+        have[dev] = true;
+    }
+    out = bias[dev];
+    return cudaSuccess;
+}
+
 int finalize(gsn_ctx* c) {
     if (c->ready) return GSN_OK;
     if (!c->have_data || !c->have_species || !c->have_params)
@@ -218,6 +243,12 @@ int finalize(gsn_ctx* c) {
     a.precision = mixed ? 1 : 0;
     a.cut = c->opt.band_cut;
     a.s0 = c->opt.birks_s0; a.s1 = c->opt.birks_s1;
+    {
+        const double norm = INV_SQRT2PI_H / (1.0 + c->ex2_bias);
+        a.norm_hi = (float)norm;
+        a.norm_lo = (float)(norm - (double)a.norm_hi);
+        a.ex2_scale = 1.0 / (1.0 + c->ex2_bias);
+    }
     a.n_pulls = (int)c->pull_p.size();
     if (c->rscale.size() != (size_t)c->D * NRESP) c->rscale.assign((size_t)c->D * NRESP, 1.0);
     if (c->rfrac.size() != (size_t)c->D * c->S) c->rfrac.assign((size_t)c->D * c->S, 1.0);
@@ -491,6 +522,7 @@ int reserve(gsn_ctx* c, int T, const Plan& p) {
     if (c->opt.resolution == GSN_RES_GGAMMA &&
         (rc = ensure(c, c->colbuf2, (size_t)T * c->G * c->K * NFG * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->blkbuf, (size_t)T * c->G * nblk * 2 * rs))) return rc;
+    if ((rc = ensure(c, c->segbuf, ((size_t)T * c->G + 1) * sizeof(int)))) return rc;
     if ((rc = ensure(c, c->mubuf, (size_t)T * p.nsplit * c->total_bins * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->wbuf, (size_t)T * c->total_bins * rs))) return rc;
     if ((rc = ensure(c, c->partbuf, (size_t)T * c->G * p.nbtask * npart * sizeof(double)))) return rc;
@@ -516,6 +548,7 @@ void fill(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
     a.bw_warps = p.bw_warps; a.bw_bsplit = p.bw_bsplit; a.nbtask = p.nbtask;
     a.dev_chunks = p.dev_chunks;
     a.colbuf = c->colbuf.p; a.colbuf2 = (double*)c->colbuf2.p; a.blkbuf = c->blkbuf.p; a.mubuf = (double*)c->mubuf.p;
+    a.segoff = (int*)c->segbuf.p;
     a.wbuf = c->wbuf.p; a.partbuf = (double*)c->partbuf.p; a.gdirect = (double*)c->gdirect.p;
     a.devpart = (double*)c->devbuf.p;
     if (a.nsec) {
@@ -850,6 +883,12 @@ int gsn_create(gsn_ctx** out, const gsn_options* opt) {
     }
     cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
     if (c->nsm <= 0) c->nsm = 1;
+    if (o.precision == GSN_MIXED && device_ex2_bias(c->dev, c->ex2_bias) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return GSN_ERR_CUDA;
+    }
     *out = c;
     return GSN_OK;
 }
@@ -860,10 +899,10 @@ void gsn_destroy(gsn_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     free_owned(c);
-    for (Buf* b : {&c->fit_ws, &c->fit_cfg, &c->fit_eval, &c->fit_ist})
+    for (Buf* b : {&c->fit_ws, &c->fit_cfg, &c->fit_eval, &c->fit_ist, &c->wscale_b})
         if (b->p) cudaFree(b->p);
     for (Buf* b : {&c->secRq_b, &c->secN_b, &c->secV_b, &c->secW_b, &c->secpart_b, &c->secU_b,
-                   &c->colbuf, &c->colbuf2, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
+                   &c->segbuf, &c->colbuf, &c->colbuf2, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
                    &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf, &c->s_hi, &c->s_lo,
                    &c->tc_part, &c->tc_err})
         if (b->p) cudaFree(b->p);
@@ -1347,10 +1386,16 @@ int gsn_eval_grad_batch_dev(gsn_ctx* c, int n_toys, const double* params_dev, co
     return batch_device(c, n_toys, params_dev, toy_counts_dev, toy_win_dev, nll_dev, grad_dev, status_dev);
 }
 
-int gsn_minimize_batch_dev(gsn_ctx* c, int n_toys, double* params_dev, const double* toy_counts_dev,
-                           const int* toy_win_dev, const unsigned char* free_mask, const double* lo, const double* hi,
-                           const double* scale, int max_evals, double gtol, double ftol, double* nll_dev,
-                           int* evals_dev, int* status_dev) {
+}  // extern "C"
+
+namespace {
+
+// the batched minimiser; scale_dev: per-toy scales [T][P] on the device, or NULL for the shared
+// host scales `scale` ([P], NULL: 1)
+int minimize_batch(gsn_ctx* c, int n_toys, double* params_dev, const double* toy_counts_dev, const int* toy_win_dev,
+                   const unsigned char* free_mask, const double* lo, const double* hi, const double* scale,
+                   const double* scale_dev, int max_evals, double gtol, double ftol, double edm, double* nll_dev,
+                   int* evals_dev, int* status_dev) {
     if (!c) return GSN_ERR_ARG;
     int rc;
     if ((rc = finalize(c))) return rc;
@@ -1382,13 +1427,15 @@ int gsn_minimize_batch_dev(gsn_ctx* c, int n_toys, double* params_dev, const dou
     if ((rc = ensure(c, c->fit_ist, ((size_t)T * 8 + 1) * sizeof(int)))) return rc;
     double* ws = (double*)c->fit_ws.p;
     FitArgs f{};
-    f.T = T; f.P = P; f.max_evals = max_evals; f.gtol = gtol; f.ftol = ftol;
+    f.T = T; f.P = P; f.max_evals = max_evals; f.gtol = gtol; f.ftol = ftol; f.edm = edm;
     f.fnoise = c->opt.precision == GSN_MIXED ? 1e-7 : 1e-13;
     f.X = ws; f.G = ws + (size_t)T * P; f.D = ws + (size_t)2 * T * P; f.XT = ws + (size_t)3 * T * P;
     f.S = ws + (size_t)4 * T * P; f.Y = f.S + (size_t)T * M * P; f.RHO = f.Y + (size_t)T * M * P;
     f.dstate = f.RHO + (size_t)T * M;
     double* cf = (double*)c->fit_cfg.p;
-    f.lo = cf; f.hi = cf + P; f.scale = cf + 2 * P;
+    f.lo = cf; f.hi = cf + P;
+    if (scale_dev) { f.scale = scale_dev; f.scale_stride = P; }
+    else { f.scale = cf + 2 * P; f.scale_stride = 0; }
     f.free = (const unsigned char*)(cf + 3 * P);
     double* ev = (double*)c->fit_eval.p;
     f.nll = ev; f.grad = ev + T;
@@ -1420,6 +1467,62 @@ int gsn_minimize_batch_dev(gsn_ctx* c, int n_toys, double* params_dev, const dou
     if (status_dev)
         CUDA_TRY(c, cudaMemcpy2DAsync(status_dev, sizeof(int), f.istate + 4, 8 * sizeof(int), sizeof(int), T,
                                       cudaMemcpyDeviceToDevice, c->stream));
+    return GSN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gsn_minimize_batch_dev(gsn_ctx* c, int n_toys, double* params_dev, const double* toy_counts_dev,
+                           const int* toy_win_dev, const unsigned char* free_mask, const double* lo, const double* hi,
+                           const double* scale, int max_evals, double gtol, double ftol, double* nll_dev,
+                           int* evals_dev, int* status_dev) {
+    return minimize_batch(c, n_toys, params_dev, toy_counts_dev, toy_win_dev, free_mask, lo, hi, scale, nullptr,
+                          max_evals, gtol, ftol, 0.0, nll_dev, evals_dev, status_dev);
+}
+
+int gsn_minimize_batch_scaled_dev(gsn_ctx* c, int n_toys, double* params_dev, const double* toy_counts_dev,
+                                  const int* toy_win_dev, const unsigned char* free_mask, const double* lo,
+                                  const double* hi, const double* scale_dev, int max_evals, double gtol, double ftol,
+                                  double edm, double* nll_dev, int* evals_dev, int* status_dev) {
+    if (!c) return GSN_ERR_ARG;
+    if (!scale_dev) return fail(c, GSN_ERR_ARG, "scale_dev is NULL");
+    if (std::isnan(edm)) return fail(c, GSN_ERR_ARG, "edm is NaN");
+    return minimize_batch(c, n_toys, params_dev, toy_counts_dev, toy_win_dev, free_mask, lo, hi, nullptr, scale_dev,
+                          max_evals, gtol, ftol, edm, nll_dev, evals_dev, status_dev);
+}
+
+int gsn_window_scales_dev(gsn_ctx* c, int n_toys, const double* params_dev, const int* toy_win_dev,
+                          const double* scale, double max_factor, double* scale_dev) {
+    if (!c) return GSN_ERR_ARG;
+    int rc;
+    if ((rc = finalize(c))) return rc;
+    if (n_toys < 0) return fail(c, GSN_ERR_ARG, "n_toys must be >= 0");
+    if (n_toys == 0) return GSN_OK;
+    if (!params_dev || !toy_win_dev || !scale_dev) return fail(c, GSN_ERR_ARG, "NULL argument");
+    if (!(max_factor > 0.0)) max_factor = 100.0;
+    if (max_factor < 1.0 || !std::isfinite(max_factor)) return fail(c, GSN_ERR_ARG, "max_factor must be >= 1 and finite");
+    const int T = n_toys, P = c->P;
+    std::vector<double> sc(P, 1.0);
+    for (int i = 0; i < P && scale; ++i) {
+        if (!(scale[i] > 0.0) || !std::isfinite(scale[i]))
+            return fail(c, GSN_ERR_ARG, "bad scale of parameter " + std::to_string(i));
+        sc[i] = scale[i];
+    }
+    const size_t nds = (size_t)T * c->D * c->S;
+    if ((rc = ensure(c, c->wscale_b, (2 * nds + P) * sizeof(double)))) return rc;
+    double* nwin = (double*)c->wscale_b.p;
+    double* nfull = nwin + nds;
+    double* scd = nfull + nds;
+    CUDA_TRY(c, cudaMemcpyAsync(scd, sc.data(), P * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    KArgs a = c->base;
+    a.T = T;
+    a.params = params_dev; a.params_stride = P;
+    a.win = toy_win_dev; a.win_stride = 2 * c->D;
+    CUDA_TRY(c, launch_window_scales(a, nwin, nfull, scd, max_factor, scale_dev, c->stream));
+    // the host buffer sc must outlive the copy
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return GSN_OK;
 }
 
@@ -1514,7 +1617,7 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     KArgs a = c->base;
     const Plan p = make_plan(c, 1);
     const size_t rs = c->opt.precision == GSN_MIXED ? sizeof(float) : sizeof(double);
-    const size_t sizes[8] = {
+    const size_t sizes[9] = {
         (size_t)c->G * c->K * NFP * rs,                         // column records
         (size_t)c->G * a.nblk * 2 * rs,                         // band summaries
         (size_t)p.nsplit * c->total_bins * sizeof(double),      // partial mu
@@ -1522,9 +1625,10 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
         (size_t)c->G * p.nbtask * a.NPART * sizeof(double),     // partial gradients
         (size_t)c->P * sizeof(double),                          // direct gradient terms
         (size_t)p.dev_chunks * (2 + c->base.ntpl) * sizeof(double),   // deviance and template partials
-        c->opt.resolution == GSN_RES_GGAMMA ? (size_t)c->G * c->K * NFG * sizeof(double) : 0};  // adjoint coefficients
-    size_t off[8], total = 0;
-    for (int i = 0; i < 8; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
+        c->opt.resolution == GSN_RES_GGAMMA ? (size_t)c->G * c->K * NFG * sizeof(double) : 0,  // adjoint coefficients
+        ((size_t)c->G + 1) * sizeof(int)};                      // forward segment prefix
+    size_t off[9], total = 0;
+    for (int i = 0; i < 9; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
     if (total > GSN_NOALLOC_SCRATCH_BYTES)
         return fail(c, GSN_ERR_ARG, "this problem needs " + std::to_string(total) + " bytes of scratch; the "
                     "no-allocation entry point holds " + std::to_string((size_t)GSN_NOALLOC_SCRATCH_BYTES));
@@ -1535,6 +1639,7 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     a.wbuf = base + off[3]; a.partbuf = (double*)(base + off[4]); a.gdirect = (double*)(base + off[5]);
     a.dev_chunks = p.dev_chunks; a.devpart = (double*)(base + off[6]);
     a.colbuf2 = (double*)(base + off[7]);
+    a.segoff = (int*)(base + off[8]);
     a.params = params_dev; a.params_stride = c->P;
     a.counts_stride = 0; a.win_stride = 0;
     a.nll = nll_dev; a.grad = grad_dev; a.status = status_dev;

@@ -13,17 +13,10 @@ constexpr float L2E_LO = (float)(1.4426950408889634 - (double)L2E);
 constexpr float HALF_L2E_LO = (float)(0.72134752044448170 - 0.5 * (double)L2E);
 constexpr double INV_SQRT2 = 0.70710678118654752440;
 constexpr double INV_SQRT2PI = 0.39894228040143267794;
-// Mean relative error of the SFU exponential ex2.approx.ftz.f32 over the arguments of a Gaussian
-// profile, weighted by the profile (gsn_peak_probe(GSN_PROBE_EX2_BIAS) measures it).  Every
-// mixed-precision response value is N_k times a sum of such exponentials, so a bias of the SFU
-// would scale all expected counts alike; the column normalisation divides it out.
-constexpr double EX2_MEAN_REL_ERR = -2.749454e-8;  // measured on GB300 (sm_103a)
-// Column normalisation constant 1/(sqrt(2 pi) (1 + bias)) as an FP32 pair, applied as
-// fmaf(x, NORM_HI, x * NORM_LO): the exact product enters the single rounding, so the FP32
-// rounding of the constant does not scale every column by the same factor
-constexpr double NORM_D = INV_SQRT2PI / (1.0 + EX2_MEAN_REL_ERR);
-constexpr float NORM_HI = (float)NORM_D;
-constexpr float NORM_LO = (float)(NORM_D - (double)NORM_HI);
+// The mixed column normalisation 1/(sqrt(2 pi) (1 + b)), b the measured mean relative error of the
+// SFU exponential ex2.approx.ftz.f32 over a Gaussian profile, is a kernel argument (KArgs::norm_hi,
+// norm_lo, ex2_scale): applied as fmaf(x, norm_hi, x * norm_lo), the exact product enters the
+// single rounding, so the FP32 rounding of the constant does not scale every column alike.
 constexpr int FWD_WARPS = 8;
 
 // problem-table reads: the kernel-parameter copy for the first groups / datasets, else device memory;

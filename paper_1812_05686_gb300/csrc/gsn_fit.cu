@@ -36,9 +36,9 @@ DEV bool movable(const FitArgs& f, int i, double x, double g) {
     if (x >= f.hi[i] && g < 0.0) return false;
     return true;
 }
-// projected gradient in scaled units (0 for variables that do not move)
-DEV double proj_grad(const FitArgs& f, int i, double x, double g) {
-    return movable(f, i, x, g) ? g * f.scale[i] : 0.0;
+// projected gradient in scaled units (0 for variables that do not move); scl: the toy's scales
+DEV double proj_grad(const FitArgs& f, const double* scl, int i, double x, double g) {
+    return movable(f, i, x, g) ? g * scl[i] : 0.0;
 }
 
 }  // namespace
@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(128) k_lbfgs(FitArgs f) {
     double* Y = f.Y + (long long)t * FIT_M * P;
     double* RHO = f.RHO + (long long)t * FIT_M;
     double* sc = f.dstate + (long long)t * 4;  // F, alpha, gd, unused
+    const double* scl = f.scale + (long long)t * f.scale_stride;
     const double ft = f.nll[t];
     const double* gt = f.grad + (long long)t * P;
     const int i0 = lane, i1 = lane + 32;
@@ -72,7 +73,11 @@ __global__ void __launch_bounds__(128) k_lbfgs(FitArgs f) {
         if (h0) { X[i0] = XT[i0]; G[i0] = gt[i0]; }
         if (h1) { X[i1] = XT[i1]; G[i1] = gt[i1]; }
         F = ft;
-        if (!isfinite(ft) || f.estatus[t] != 0) { status = -4; done = true; }
+        // every free variable needs a finite positive scale (per-toy scales come from the caller)
+        const bool bad = (h0 && f.free[i0] && !(scl[i0] > 0.0 && isfinite(scl[i0]))) ||
+                         (h1 && f.free[i1] && !(scl[i1] > 0.0 && isfinite(scl[i1])));
+        if (__any_sync(0xffffffffu, bad)) { status = -1; done = true; }
+        else if (!isfinite(ft) || f.estatus[t] != 0) { status = -4; done = true; }
         else set_dir = true;
     } else {  // ST_SEARCH: the trial point XT was evaluated
         double st = 0.0;  // predicted change g . (x_t - x) of the projected step
@@ -93,8 +98,8 @@ __global__ void __launch_bounds__(128) k_lbfgs(FitArgs f) {
             // curvature pair in scaled units, on the free variables only: the gradient of a held
             // parameter changes too, but belongs to no direction the search can take
             double s0 = 0.0, s1 = 0.0, y0 = 0.0, y1 = 0.0;
-            if (h0 && f.free[i0]) { s0 = (XT[i0] - X[i0]) / f.scale[i0]; y0 = (gt[i0] - G[i0]) * f.scale[i0]; }
-            if (h1 && f.free[i1]) { s1 = (XT[i1] - X[i1]) / f.scale[i1]; y1 = (gt[i1] - G[i1]) * f.scale[i1]; }
+            if (h0 && f.free[i0]) { s0 = (XT[i0] - X[i0]) / scl[i0]; y0 = (gt[i0] - G[i0]) * scl[i0]; }
+            if (h1 && f.free[i1]) { s1 = (XT[i1] - X[i1]) / scl[i1]; y1 = (gt[i1] - G[i1]) * scl[i1]; }
             const double sy = wsum(s0 * y0 + s1 * y1);
             const double ss = wsum(s0 * s0 + s1 * s1), yy = wsum(y0 * y0 + y1 * y1);
             if (sy > 1e-10 * sqrt(ss * yy)) {
@@ -111,8 +116,8 @@ __global__ void __launch_bounds__(128) k_lbfgs(FitArgs f) {
             if (h0) { X[i0] = XT[i0]; G[i0] = gt[i0]; }
             if (h1) { X[i1] = XT[i1]; G[i1] = gt[i1]; }
             double pg = 0.0;
-            if (h0) pg = fmax(pg, fabs(proj_grad(f, i0, X[i0], G[i0])));
-            if (h1) pg = fmax(pg, fabs(proj_grad(f, i1, X[i1], G[i1])));
+            if (h0) pg = fmax(pg, fabs(proj_grad(f, scl, i0, X[i0], G[i0])));
+            if (h1) pg = fmax(pg, fabs(proj_grad(f, scl, i1, X[i1], G[i1])));
             pg = wmax(pg);
             // converged: projected gradient below gtol, or two full (not shortened) steps in a row
             // that each lowered the NLL by at most ftol relative
@@ -139,8 +144,8 @@ __global__ void __launch_bounds__(128) k_lbfgs(FitArgs f) {
     if (set_dir && !done) {
         // two-loop recursion on the projected gradient (scaled units)
         double q0 = 0.0, q1 = 0.0;
-        if (h0) q0 = proj_grad(f, i0, X[i0], G[i0]);
-        if (h1) q1 = proj_grad(f, i1, X[i1], G[i1]);
+        if (h0) q0 = proj_grad(f, scl, i0, X[i0], G[i0]);
+        if (h1) q1 = proj_grad(f, scl, i1, X[i1], G[i1]);
         // the recursion runs on the subspace of the variables that move
         const bool m0 = h0 && movable(f, i0, X[i0], G[i0]);
         const bool m1 = h1 && movable(f, i1, X[i1], G[i1]);
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(128) k_lbfgs(FitArgs f) {
             if (m1) q1 += S[slot * P + i1] * (al[k] - b);
         }
         double d0 = m0 ? -q0 : 0.0, d1 = m1 ? -q1 : 0.0;
-        const double pg0 = h0 ? proj_grad(f, i0, X[i0], G[i0]) : 0.0, pg1 = h1 ? proj_grad(f, i1, X[i1], G[i1]) : 0.0;
+        const double pg0 = h0 ? proj_grad(f, scl, i0, X[i0], G[i0]) : 0.0, pg1 = h1 ? proj_grad(f, scl, i1, X[i1], G[i1]) : 0.0;
         gd = wsum(d0 * pg0 + d1 * pg1);
         if (!(gd < 0.0)) {  // not a descent direction: steepest descent, history dropped
             d0 = -pg0; d1 = -pg1;
@@ -181,6 +186,9 @@ __global__ void __launch_bounds__(128) k_lbfgs(FitArgs f) {
         if (h0) Dd[i0] = d0;
         if (h1) Dd[i1] = d1;
         if (dmax == 0.0) { status = 0; done = true; }  // every free variable held at a bound
+        // estimated distance to the minimum, -g.d/2 with d = -H^-1 g the quasi-Newton step (the
+        // stopping rule of MINUIT's MIGRAD), once curvature pairs describe H
+        if (f.edm > 0.0 && nhist > 0 && -0.5 * gd < f.edm) { status = 0; done = true; }
         state = ST_SEARCH;
     }
     if (done) {
@@ -189,8 +197,8 @@ __global__ void __launch_bounds__(128) k_lbfgs(FitArgs f) {
         if (h1) XT[i1] = X[i1];
     } else {
         // next trial point: x + alpha d (scaled), projected onto the bounds
-        if (h0) XT[i0] = f.free[i0] ? fmin(fmax(X[i0] + alpha * Dd[i0] * f.scale[i0], f.lo[i0]), f.hi[i0]) : X[i0];
-        if (h1) XT[i1] = f.free[i1] ? fmin(fmax(X[i1] + alpha * Dd[i1] * f.scale[i1], f.lo[i1]), f.hi[i1]) : X[i1];
+        if (h0) XT[i0] = f.free[i0] ? fmin(fmax(X[i0] + alpha * Dd[i0] * scl[i0], f.lo[i0]), f.hi[i0]) : X[i0];
+        if (h1) XT[i1] = f.free[i1] ? fmin(fmax(X[i1] + alpha * Dd[i1] * scl[i1], f.lo[i1]), f.hi[i1]) : X[i1];
     }
     __syncwarp();
     if (lane == 0) {
@@ -199,6 +207,157 @@ __global__ void __launch_bounds__(128) k_lbfgs(FitArgs f) {
         sc[0] = F; sc[1] = alpha; sc[2] = gd;
         if (state != ST_DONE) atomicAdd(f.active, 1);
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-toy conditioning of the minimiser.  A toy fitted in a window that holds only part of a
+// species' spectrum constrains that species' rate less than the whole histograms do, so a scale
+// taken from the whole histograms (the caller's) is too small for it.  k_window_counts adds up,
+// at the toy's parameters, every species' expected counts over the whole histogram and inside
+// the toy's window of every dataset; the response is taken as a Gaussian of each column's mean
+// and variance (a scale needs no better).  k_window_scales multiplies the scale of every
+// parameter that fills only rate slots by sqrt(N_whole / N_window) of its species, within
+// [1, max_factor].
+constexpr int WC_CHUNK = 1024;
+constexpr int WC_WARPS = 8;
+
+DEV float gauss_mass(float lo, float hi, float mu, float isg) {
+    return hi > lo ? normcdff((hi - mu) * isg) - normcdff((lo - mu) * isg) : 0.0f;
+}
+
+__global__ void __launch_bounds__(WC_WARPS * 32) k_window_counts(KArgs a, double* nwin, double* nfull) {
+    const int t = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ float sp[2][MAXGDS][WC_CHUNK];     // column mass in the window / whole histogram
+    __shared__ double acc[2][MAXGDS][MAXS];
+    const double* prm = a.params + (long long)t * a.params_stride;
+    const int* win = a.win + (long long)t * a.win_stride;
+    for (int g = 0; g < a.G; ++g) {
+        if (!tb_g_active(a, g)) continue;
+        const int nds = tb_g_nds(a, g), J = tb_g_bins(a, g);
+        const double* ed = a.edges + tb_g_edge_off(a, g);
+        double rp[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const int ri = tb_g_resp(a, g, i);
+            rp[i] = ri >= 0 ? prm[ri] * tb_g_rscale(a, g, i) : 0.0;
+        }
+        const double alpha = 1.0 + rp[1] * a.s0, beta = rp[1] * a.s1;
+        float xl[MAXGDS] = {0.f, 0.f, 0.f}, xh[MAXGDS] = {0.f, 0.f, 0.f};
+        for (int dd = 0; dd < nds; ++dd) {
+            const int d = tb_g_ds(a, g, dd);
+            const int lo = max(win[2 * d], 0), hi = min(win[2 * d + 1], J);
+            if (hi > lo) { xl[dd] = (float)ed[lo]; xh[dd] = (float)ed[hi]; }
+        }
+        const float x0 = (float)ed[0], xJ = (float)ed[J];
+        for (int i = threadIdx.x; i < 2 * MAXGDS * MAXS; i += blockDim.x) (&acc[0][0][0])[i] = 0.0;
+        for (int k0 = 0; k0 < a.K; k0 += WC_CHUNK) {
+            const int nk = min(WC_CHUNK, a.K - k0);
+            __syncthreads();  // the previous chunk has been consumed (and acc cleared)
+            for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+                const double E = a.E[k0 + i];
+                const double Eq = beta > 0.0 ? E / alpha - beta / (alpha * alpha) * log1p(alpha * E / beta) : E / alpha;
+                const double mu = rp[0] * Eq;
+                const double var = rp[2] + mu * (rp[3] + rp[4] * mu);
+                const float isg = var > 0.0 ? (float)rsqrt(var) : 0.0f;
+                for (int dd = 0; dd < nds; ++dd) {
+                    sp[0][dd][i] = gauss_mass(xl[dd], xh[dd], (float)mu, isg);
+                    sp[1][dd][i] = gauss_mass(x0, xJ, (float)mu, isg);
+                }
+            }
+            __syncthreads();
+            for (int s = warp; s < a.S; s += WC_WARPS) {
+                if (a.ft.sp_kind[s] >= 2) continue;  // peaks and templates do not pass the response
+                // the spectra are on the device in the context's precision only
+                const float* Srf = a.precision == 1 ? a.Sf + (long long)s * a.K + k0 : nullptr;
+                const double* Srd = a.precision == 1 ? nullptr : a.Sd + (long long)s * a.K + k0;
+                float pw[MAXGDS] = {0.f, 0.f, 0.f}, pf[MAXGDS] = {0.f, 0.f, 0.f};
+                for (int i = lane; i < nk; i += 32) {
+                    const float sv = Srf ? Srf[i] : (float)Srd[i];
+                    for (int dd = 0; dd < nds; ++dd) {
+                        pw[dd] = fmaf(sv, sp[0][dd][i], pw[dd]);
+                        pf[dd] = fmaf(sv, sp[1][dd][i], pf[dd]);
+                    }
+                }
+                for (int dd = 0; dd < nds; ++dd) {
+                    const float w = warp_sum<float>(pw[dd]), f = warp_sum<float>(pf[dd]);
+                    if (lane == 0) { acc[0][dd][s] += w; acc[1][dd][s] += f; }
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nds * a.S; i += blockDim.x) {
+            const int dd = i / a.S, s = i % a.S, d = tb_g_ds(a, g, dd);
+            if (a.ft.sp_kind[s] >= 2) continue;
+            const double rf = a.rfac[d * a.S + s];
+            nwin[((long long)t * a.D + d) * a.S + s] = rf * acc[0][dd][s];
+            nfull[((long long)t * a.D + d) * a.S + s] = rf * acc[1][dd][s];
+        }
+        __syncthreads();
+    }
+    // peaks (a Gaussian in p.e.) and templates (their histograms), every dataset
+    for (int i = threadIdx.x; i < a.D * a.S; i += blockDim.x) {
+        const int d = i / a.S, s = i % a.S;
+        const int kind = a.ft.sp_kind[s];
+        const double rf = a.rfac[d * a.S + s];
+        if (kind < 2 || rf == 0.0) continue;
+        const int J = tb_ds_bins(a, d);
+        const double* ed = a.edges + tb_g_edge_off(a, tb_ds_group(a, d));
+        const int lo = max(win[2 * d], 0), hi = min(win[2 * d + 1], J);
+        double vw = 0.0, vf = 0.0;
+        if (kind == 2) {
+            const int* sm = a.slot_map + (long long)d * a.NSLOT;
+            const int im = sm[a.S + 5 + 2 * s], iw = sm[a.S + 6 + 2 * s];
+            const double m = im >= 0 ? prm[im] : 0.0, w = iw >= 0 ? fabs(prm[iw]) : 0.0;
+            if (w > 0.0) {
+                vf = normcdf((ed[J] - m) / w) - normcdf((ed[0] - m) / w);
+                if (hi > lo) vw = normcdf((ed[hi] - m) / w) - normcdf((ed[lo] - m) / w);
+            }
+        } else {
+            for (int q = a.tb->ds_tpl0[d]; q < a.tb->ds_tpl0[d] + a.tb->ds_ntpl[d]; ++q) {
+                if (a.tpl_s[q] != s) continue;
+                const double* h = a.tpl + a.tpl_off[q];
+                for (int j = 0; j < J; ++j) { vf += h[j]; if (j >= lo && j < hi) vw += h[j]; }
+            }
+        }
+        nwin[((long long)t * a.D + d) * a.S + s] = rf * vw;
+        nfull[((long long)t * a.D + d) * a.S + s] = rf * vf;
+    }
+}
+
+__global__ void k_window_scales(KArgs a, const double* nwin, const double* nfull, const double* scale,
+                                double max_factor, double* out) {
+    const int t = blockIdx.x;
+    for (int p = threadIdx.x; p < a.P; p += blockDim.x) {
+        double sw = 0.0, sf = 0.0;
+        bool rate = false, other = false;
+        for (int d = 0; d < a.D; ++d) {
+            const int* sm = a.slot_map + (long long)d * a.NSLOT;
+            for (int sl = 0; sl < a.NSLOT; ++sl) {
+                if (sm[sl] != p) continue;
+                if (sl < a.S) {
+                    rate = true;
+                    sw += nwin[((long long)t * a.D + d) * a.S + sl];
+                    sf += nfull[((long long)t * a.D + d) * a.S + sl];
+                } else {
+                    other = true;
+                }
+            }
+        }
+        double f = 1.0;
+        if (rate && !other && sf > 0.0) f = sw * max_factor * max_factor > sf ? sqrt(sf / sw) : max_factor;
+        out[(long long)t * a.P + p] = scale[p] * fmin(fmax(f, 1.0), max_factor);
+    }
+}
+
+cudaError_t launch_window_scales(const KArgs& a, double* nwin, double* nfull, const double* scale, double max_factor,
+                                 double* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(nwin, 0, sizeof(double) * a.T * a.D * a.S, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nfull, 0, sizeof(double) * a.T * a.D * a.S, st);
+    if (e != cudaSuccess) return e;
+    k_window_counts<<<a.T, WC_WARPS * 32, 0, st>>>(a, nwin, nfull);
+    k_window_scales<<<a.T, 64, 0, st>>>(a, nwin, nfull, scale, max_factor, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lbfgs(const FitArgs& f, cudaStream_t st) {

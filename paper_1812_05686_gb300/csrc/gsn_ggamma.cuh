@@ -182,11 +182,11 @@ DEV void gg_inc_gamma(double a, double y, double& P, double& Pa, double& py) {
 // Column prologue of the generalized gamma (FP64 for both precisions).  Fills the record fields
 // that depend on the response (everything but TN), the band [xmin, xmax] and the adjoint record
 // g (NFG values); mu, var: the column's mean and variance, p the power, deq = d E_q / d kB.
-// Returns the normalisation N_k that multiplies the T_dk (mixed: the density at the mean over the
-// SFU bias of the exponentials; FP64: 1).
+// Returns the normalisation N_k that multiplies the T_dk (mixed: the density at the mean times
+// ex2_scale = 1 / (1 + b), b the SFU exponentials' measured mean relative error; FP64: 1).
 template <class R>
 DEV double gg_column(double mu, double var, double p, double cut, double x1, bool zero_bin, bool mixed,
-                     R* f, double* gco, R& xmin, R& xmax) {
+                     double ex2_scale, R* f, double* gco, R& xmin, R& xmax) {
     const double a = 1.0 / p;
     const double r = log1p(var / (mu * mu));
     double Hx, lxs;                                   // dH/dx at the root, ln(d/p)
@@ -202,7 +202,7 @@ DEV double gg_column(double mu, double var, double p, double cut, double x1, boo
     const double lfm = log(p) - log(mu) + d * ls - A - lgx;
     double Nk = 1.0;
     if (mixed) {
-        Nk = exp(lfm) / (1.0 + EX2_MEAN_REL_ERR);
+        Nk = exp(lfm) * ex2_scale;
         f[F_A] = (R)(1.0 / mu);
         f[F_B] = (R)(1.4426950408889634 * A);
         f[F_C] = (R)(1.4426950408889634 * k1);

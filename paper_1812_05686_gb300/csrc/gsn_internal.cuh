@@ -86,6 +86,11 @@ struct KArgs {
     int res;          // 0 gauss, 1 gamma, 2 generalized gamma with a free power
     int precision;    // 0 fp64, 1 mixed
     double cut;       // band cut on the log-density
+    // mixed column normalisation: the SFU exponential's mean relative error b over a response
+    // profile is measured on the context's device when the context is created; every mixed value
+    // is N_k times a sum of such exponentials, so N_k carries the factor 1 / (1 + b)
+    float norm_hi, norm_lo;     // 1 / (sqrt(2 pi) (1 + b)) as an FP32 pair (fmaf(x, hi, x * lo))
+    double ex2_scale;           // 1 / (1 + b)
     double s0, s1;    // stopping power model
     int max_nds;                // most datasets in one response group
     int fast;                   // every group and dataset is in the kernel-parameter copy ft
@@ -130,6 +135,8 @@ struct KArgs {
     int nblk;
     int nbtask, bw_warps, bw_bsplit, NPART;
     int ntile;             // forward tiles per group (max over groups)
+    int* segoff;           // [T*G + 1] gamma forward: exclusive prefix of the 64-bin segments of every
+                           // (toy, group) window (written by the forward launcher)
     int dev_chunks;        // deviance blocks per toy
     double* devpart;       // [T][dev_chunks][2 + ntpl]: partial deviance sum, status flags,
                            // partial sum_j w_j T_j of every template
@@ -178,11 +185,13 @@ struct KArgs {
 struct FitArgs {
     int T, P, max_evals;
     double gtol, ftol;          // projected gradient (scaled units), relative NLL decrease
+    double edm;                 // estimated distance to the minimum at convergence (<= 0: not used)
     double fnoise;              // relative rounding of the NLL tolerated by the line search
     const unsigned char* free;  // [P] 1 = minimised over
     const double* lo;           // [P] bounds
     const double* hi;
-    const double* scale;        // [P] u = x / scale
+    const double* scale;        // [T][P] (scale_stride = P) or [P] shared (scale_stride = 0): u = x / scale
+    long long scale_stride;
     const double* nll;          // evaluation of the trial points XT
     const double* grad;
     const int* estatus;
@@ -199,7 +208,11 @@ struct FitArgs {
     int* active;                // toys still running after the update
 };
 cudaError_t launch_lbfgs(const FitArgs& f, cudaStream_t st);
-constexpr int FIT_HISTORY = 8;
+// per-toy minimiser scales: scale [P] (device) times sqrt(N_whole / N_window) for rate parameters;
+// nwin, nfull: [T][D][S] scratch; out [T][P]
+cudaError_t launch_window_scales(const KArgs& a, double* nwin, double* nfull, const double* scale, double max_factor,
+                                 double* out, cudaStream_t st);
+constexpr int FIT_HISTORY = 16;
 
 // launchers (gsn_kernels.cu); return cudaError_t of the launches
 cudaError_t launch_columns(const KArgs& a, cudaStream_t st);

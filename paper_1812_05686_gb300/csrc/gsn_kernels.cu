@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
             if constexpr (sizeof(R) == 4) f[F_MUL] = (R)(mud - (double)(R)mud);
             double gco[NFG];
             const double x1 = a.edges[tb_g_edge_off<FAST>(a, g) + 1];
-            Nk = (R)gg_column<R>(mud, vard, sres[5], a.cut, x1, tb_g_zero<FAST>(a, g) != 0, sizeof(R) == 4, f, gco,
+            Nk = (R)gg_column<R>(mud, vard, sres[5], a.cut, x1, tb_g_zero<FAST>(a, g) != 0, sizeof(R) == 4, a.ex2_scale, f, gco,
                                  xmin, xmax);
             double* g2 = a.colbuf2 + (((long long)t * a.G + g) * a.K + k) * NFG;
 #pragma unroll
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
             if constexpr (RES == 0) {
                 const R sig = sqrt(var), isg = R(1) / sig;
                 f[F_A] = isg;
-                if constexpr (sizeof(R) == 4) Nk = fmaf(isg, NORM_HI, isg * NORM_LO);
+                if constexpr (sizeof(R) == 4) Nk = fmaf(isg, a.norm_hi, isg * a.norm_lo);
                 const R zc = sqrt(R(2) * (R)a.cut);
                 xmin = mu - zc * sig;
                 xmax = mu + zc * sig;
@@ -157,12 +157,12 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
                         const float id = 1.0f / d, id2 = id * id;
                         const float corr = id * (1.0f / 12 - id2 * (1.0f / 360 - id2 * (1.0f / 1260 - id2 * (1.0f / 1680))));
                         const float nq = expf(-corr) * rsqrtf(var);
-                        Nk = fmaf(nq, NORM_HI, nq * NORM_LO);
+                        Nk = fmaf(nq, a.norm_hi, nq * a.norm_lo);
                         f[F_KAPPA] = 0.5f * id + id2 * (1.0f / 12 - id2 * (1.0f / 120 - id2 * (1.0f / 252 - id2 * (1.0f / 240))));
                     } else {
                         const double dd = (double)mu * (double)mu / (double)var, sd = (double)var / (double)mu;
-                        Nk = (float)(exp((dd - 1.0) * log((double)mu) - (double)mu / sd - dd * log(sd) - lgamma(dd)) /
-                                     (1.0 + EX2_MEAN_REL_ERR));
+                        Nk = (float)(exp((dd - 1.0) * log((double)mu) - (double)mu / sd - dd * log(sd) - lgamma(dd)) *
+                                     a.ex2_scale);
                         f[F_KAPPA] = (float)(log(dd) - digamma_d(dd));
                     }
                 } else {

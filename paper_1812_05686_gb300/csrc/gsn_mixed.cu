@@ -240,6 +240,229 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_m(KArgs a) {
     }
 }
 
+// ------------------------------------------------- forward, gamma, 2 bins per lane -----
+// Record fields of the two-bin forward after the per-warp transformation (negated copies let the
+// packed operations form differences without an extra negation; all negations are exact):
+//   q0 = (-mu_hi, -mu_lo, A, -A)   q1 = (Q, R, -R, -L2E A)   q2 = (TN0, TN1, TN2, P)
+//   A = 1/mu, P = L2E d, Q = L2E (d-1), R = L2E C (C = -1/s)
+DEV RecF transform_record_g2(const float4 r0, const float4 r1, const float4 r3) {
+    RecF o;
+    const float R = mul_l2e(r1.x);
+    o.q0 = make_float4(-r0.x, -r0.y, r0.z, -r0.z);
+    o.q1 = make_float4(fmaf(L2E, r0.w, fmaf(L2E_LO, r0.w - 1.0f, -L2E)), R, -R, -mul_l2e(r0.z));
+    o.q2 = make_float4(r3.y, r3.z, r3.w, mul_l2e(r0.w));
+    return o;
+}
+
+// two linear bins of one column (shape d >= D_POLY), packed: the scalar pair_value_poly per lane half
+DEV float2 pair_value_poly2(const RecF& c, float2 xc, float2 dl, float2 lp, float2 lm, float2 w0, float2 w1) {
+    const float2 Dx = add2(add2(xc, f2(c.q0.x)), f2(c.q0.y));
+    const float2 D = log1pmx_poly2(mul2(Dx, f2(c.q0.z)), mul2(Dx, f2(c.q0.w)));
+    const float2 Ec = fma2(f2(c.q1.x), D, mul2(Dx, f2(c.q1.w)));
+    const float2 ap = add2(fma2(f2(c.q1.x), lp, Ec), mul2(f2(c.q1.y), dl));
+    const float2 am = add2(fma2(f2(c.q1.x), lm, Ec), mul2(f2(c.q1.z), dl));
+    return fma2(w1, add2(ex2f2(ap), ex2f2(am)), mul2(w0, ex2f2(Ec)));
+}
+
+// one linear bin of one column, any shape (the scalar pair_value<1> on the two-bin record layout)
+DEV float pair_value_g2(const RecF& c, float xc, float dl, float lp, float lm, float w0, float w1) {
+    const float Dx = (xc + c.q0.x) + c.q0.y;
+    float L1;
+    const float Dt = log1pmx2_f(Dx * c.q0.z, L1);
+    const float Ec = fmaf(c.q2.w, Dt, -L2E * L1);
+    const float cd = c.q1.y * dl;
+    const float ap = fmaf(c.q1.x, lp, Ec) + cd;
+    const float am = fmaf(c.q1.x, lm, Ec) - cd;
+    return fmaf(w1, ex2f(ap) + ex2f(am), w0 * ex2f(Ec));
+}
+
+// Gamma response, lanes <-> bins j0 + lane and j0 + 32 + lane (64 bins per warp): the column record of
+// a batch is read once from shared memory for both bins, and the common case (every column of the
+// batch reaches the warp and has shape >= D_POLY) evaluates the two bins with packed FP32 operations.
+// Otherwise as k_forward_m.
+// 64-bin segments of every (toy, group) window, as an exclusive prefix: warp w of the forward takes
+// segment w - segoff[i] of the (toy, group) i with segoff[i] <= w < segoff[i + 1], so the blocks of
+// the forward hold only warps with work (a block whose warps had left early would keep its
+// registers until its last warp finished).  One block; T G <= 65535.
+template <bool FAST>
+__global__ void __launch_bounds__(1024) k_fwd_segments(KArgs a) {
+    __shared__ int part[1024];
+    const int n = a.T * a.G;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+    auto nseg = [&](int i) {
+        const int t = i / a.G, g = i % a.G;
+        if (!tb_g_active<FAST>(a, g)) return 0;
+        int wlo, whi;
+        toy_window_union<FAST>(a, t, g, wlo, whi);
+        return whi > wlo ? (whi - wlo + 63) / 64 : 0;
+    };
+    int sum = 0;
+    for (int i = i0; i < i1; ++i) sum += nseg(i);
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive scan of the per-thread sums
+        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - sum;
+    for (int i = i0; i < i1; ++i) { a.segoff[i] = run; run += nseg(i); }
+    if (threadIdx.x == blockDim.x - 1) a.segoff[n] = part[threadIdx.x];
+}
+
+// resident 256-thread blocks per SM the two-bin forward's register budget is sized for
+#ifndef GSN_FWD_MINBLOCKS
+#define GSN_FWD_MINBLOCKS 3
+#endif
+
+template <int NDS, bool FAST>
+__global__ void __launch_bounds__(FWD_WARPS * 32, GSN_FWD_MINBLOCKS) k_forward_m2(KArgs a) {
+    const int split = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this warp's (toy, group) and segment: the last i with segoff[i] <= gw (a warp-uniform search)
+    const int gw = blockIdx.x * FWD_WARPS + warp;
+    const int n = a.T * a.G;
+    if (gw >= a.segoff[n]) return;
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.segoff[mid] <= gw) lo = mid; else hi = mid;
+    }
+    const int t = lo / a.G, g = lo % a.G;
+    __shared__ RecF srec[FWD_WARPS][32];
+    int wlo, whi;
+    toy_window_union<FAST>(a, t, g, wlo, whi);
+    const int j0 = wlo + (gw - a.segoff[lo]) * 64;
+    const int jj[2] = {j0 + lane, j0 + 32 + lane};
+    const bool valid[2] = {jj[0] < whi, jj[1] < whi};
+    const int nb[2] = {tb_g_node_off<FAST>(a, g) + min(jj[0], whi - 1), tb_g_node_off<FAST>(a, g) + min(jj[1], whi - 1)};
+    const int jl = min(j0 + 63, whi - 1);
+    const float xlo_w = (float)a.edges[tb_g_edge_off<FAST>(a, g) + j0];
+    const float xhi_w = (float)a.edges[tb_g_edge_off<FAST>(a, g) + jl + 1];
+    const int nds = tb_g_nds<FAST>(a, g);
+    const int kchunk = (a.K + a.nsplit - 1) / a.nsplit;
+    const int k_beg = split * kchunk, k_end = min(a.K, k_beg + kchunk);
+    const float* blk = reinterpret_cast<const float*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
+
+    // column range of the band: first and last 256-column block that overlaps
+    int kfirst = k_end, klast = k_beg;
+    for (int b = k_beg / COLBLK; b * COLBLK < k_end; ++b) {
+        if (blk[2 * b + 1] < xlo_w || blk[2 * b] > xhi_w) continue;
+        kfirst = min(kfirst, max(b * COLBLK, k_beg));
+        klast = max(klast, min((b + 1) * COLBLK, k_end));
+    }
+
+    double accd[2][MAXGDS] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    int ncol = 0;
+    if (j0 < tb_g_jlin<FAST>(a, g)) {
+        // the warp holds bins below the first linear bin: general node table, one half at a time
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const unsigned char cls = a.bclass[nb[h]];
+            const float* nodes = a.ntab_f + (long long)nb[h] * 3 * NGM_F;
+            const float xc = a.xc_f[nb[h]];
+            float del[NG_LOG_F], lam[NG_LOG_F], wt[NG_LOG_F];
+#pragma unroll
+            for (int n = 0; n < NG_LOG_F; ++n) {
+                del[n] = nodes[n]; lam[n] = nodes[NGM_F + n]; wt[n] = valid[h] ? nodes[2 * NGM_F + n] : 0.f;
+            }
+            int nc = 0;
+            for (int k = kfirst; k < klast; ++k) {
+                const float* c = colrec<float>(a, t, g, k);
+                if (c[F_XMAX] < xlo_w || c[F_XMIN] > xhi_w) continue;
+                ++nc;
+                float v = bin_value_f<1, NG_LOG_F>(c, xc, del, lam, wt);
+                if (cls == BIN_ZERO) v = valid[h] ? c[F_P0] : 0.0f;
+#pragma unroll
+                for (int dd = 0; dd < MAXGDS; ++dd)
+                    if (dd < nds) accd[h][dd] += (double)(v * c[F_TN0 + dd]);
+            }
+            ncol = nc;
+        }
+    } else {
+        const float4 a0 = reinterpret_cast<const float4*>(a.btab_f)[2 * nb[0]];
+        const float4 a1 = reinterpret_cast<const float4*>(a.btab_f)[2 * nb[0] + 1];
+        const float4 b0 = reinterpret_cast<const float4*>(a.btab_f)[2 * nb[1]];
+        const float4 b1 = reinterpret_cast<const float4*>(a.btab_f)[2 * nb[1] + 1];
+        const float2 xc = make_float2(a0.x, b0.x), dl = make_float2(a0.y, b0.y);
+        const float2 lp = make_float2(a0.z, b0.z), lm = make_float2(a0.w, b0.w);
+        const float2 w0 = make_float2(valid[0] ? a1.x : 0.f, valid[1] ? b1.x : 0.f);
+        const float2 w1 = make_float2(valid[0] ? a1.y : 0.f, valid[1] ? b1.y : 0.f);
+        float s[2][MAXGDS] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, cc[2][MAXGDS] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        const float4* rec = reinterpret_cast<const float4*>(colrec<float>(a, t, g, 0));
+        float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0, r3 = r0;
+        auto load = [&](int k) {
+            if (k < klast) {
+                const float4* p = rec + (long long)k * 4;
+                r0 = p[0]; r1 = p[1]; r2 = p[2]; r3 = p[3];
+            } else {
+                r2 = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
+            }
+        };
+        load(kfirst + lane);
+        for (int kb = kfirst; kb < klast; kb += 32) {
+            const bool hit = !(r2.y < xlo_w || r2.x > xhi_w);  // (XMIN, XMAX) of column kb + lane
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            // every column of the batch has shape >= D_POLY (or is not evaluated)
+            const bool poly = __all_sync(0xffffffffu, !hit || r0.w >= D_POLY);
+            srec[warp][lane] = transform_record_g2(r0, r1, r3);
+            __syncwarp();
+            load(kb + 32 + lane);
+            ncol += __popc(m);
+            float2 acc[MAXGDS] = {f2(0.f), f2(0.f), f2(0.f)};
+            if (m == 0xffffffffu && poly) {
+                // dense batch of wide columns: both bins per instruction, four columns in flight
+#pragma unroll 4
+                for (int cidx = 0; cidx < 32; ++cidx) {
+                    const RecF c = srec[warp][cidx];
+                    const float2 v = pair_value_poly2(c, xc, dl, lp, lm, w0, w1);
+                    acc[0] = fma2(v, f2(c.q2.x), acc[0]);
+                    if (NDS > 1) acc[1] = fma2(v, f2(c.q2.y), acc[1]);
+                    if (NDS > 2) acc[2] = fma2(v, f2(c.q2.z), acc[2]);
+                }
+            } else {
+                while (m) {
+                    const int cidx = __ffs(m) - 1;
+                    m &= m - 1;
+                    const RecF c = srec[warp][cidx];
+                    const float va = pair_value_g2(c, xc.x, dl.x, lp.x, lm.x, w0.x, w1.x);
+                    const float vb = pair_value_g2(c, xc.y, dl.y, lp.y, lm.y, w0.y, w1.y);
+                    const float tn[MAXGDS] = {c.q2.x, c.q2.y, c.q2.z};
+#pragma unroll
+                    for (int dd = 0; dd < NDS; ++dd) {
+                        acc[dd].x = fmaf(va, tn[dd], acc[dd].x);
+                        acc[dd].y = fmaf(vb, tn[dd], acc[dd].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int dd = 0; dd < NDS; ++dd) {
+                two_sum_acc(s[0][dd], cc[0][dd], acc[dd].x);
+                two_sum_acc(s[1][dd], cc[1][dd], acc[dd].y);
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int dd = 0; dd < MAXGDS; ++dd) accd[h][dd] = (double)s[h][dd] + (double)cc[h][dd];
+    }
+    if (a.work) {
+        const unsigned bins = __popc(__ballot_sync(0xffffffffu, valid[0])) + __popc(__ballot_sync(0xffffffffu, valid[1]));
+        if (lane == 0) atomicAdd(&a.work[K_FORWARD], (unsigned long long)ncol * bins);
+    }
+    double* out = a.mubuf + ((long long)t * a.nsplit + split) * a.total_bins;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!valid[h]) continue;
+#pragma unroll
+        for (int dd = 0; dd < MAXGDS; ++dd)
+            if (dd < nds) out[tb_ds_off<FAST>(a, tb_g_ds<FAST>(a, g, dd)) + jj[h]] = accd[h][dd];
+    }
+}
+
 // ------------------------------------------------------------ backward -----
 
 // resident 256-thread blocks per SM the adjoint's register budget is sized for
@@ -555,6 +778,17 @@ __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
 
 template <int RES, bool FAST>
 static cudaError_t launch_fwd(const KArgs& a, cudaStream_t st, int nds) {
+    if (RES == 1) {
+        // 64 bins per warp; the grid covers every (toy, group) with the most segments a window can
+        // have (a.ntile * 32 FWD_WARPS >= Jmax bins), and blocks past the last segment return at once
+        k_fwd_segments<FAST><<<1, 1024, 0, st>>>(a);
+        const long long nseg_max = (long long)a.T * a.G * ((a.ntile * FWD_WARPS * 32 + 63) / 64);
+        dim3 grid((unsigned)((nseg_max + FWD_WARPS - 1) / FWD_WARPS), a.nsplit, 1);
+        if (nds == 1) k_forward_m2<1, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else if (nds == 2) k_forward_m2<2, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        else k_forward_m2<3, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     dim3 grid(a.ntile, a.nsplit, a.T * a.G);
     if (nds == 1) k_forward_m<RES, 1, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
     else if (nds == 2) k_forward_m<RES, 2, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);

@@ -78,6 +78,9 @@ def load_library(path: str = LIB_PATH):
                                              C.c_int, C.c_double, C.c_double, vp, vp, vp]),
         "gsn_set_secondary": (C.c_int, [vp, C.c_int, C.c_int, _IP, C.c_int, _DP, _DP]),
         "gsn_n_counts": (C.c_int, [vp]),
+        "gsn_minimize_batch_scaled_dev": (C.c_int, [vp, C.c_int, vp, vp, vp, C.POINTER(C.c_ubyte), _DP, _DP, vp,
+                                                    C.c_int, C.c_double, C.c_double, C.c_double, vp, vp, vp]),
+        "gsn_window_scales_dev": (C.c_int, [vp, C.c_int, vp, vp, _DP, C.c_double, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -94,7 +97,7 @@ def exported_symbols():
             "gsn_eval_grad_batch", "gsn_eval_grad_batch_dev", "gsn_expected", "gsn_stream",
             "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe", "gsn_eval_grad_noalloc",
             "gsn_plan_info", "gsn_set_dataset_factors", "gsn_set_template", "gsn_minimize_batch_dev",
-            "gsn_set_secondary", "gsn_n_counts"]
+            "gsn_set_secondary", "gsn_n_counts", "gsn_minimize_batch_scaled_dev", "gsn_window_scales_dev"]
 
 
 GSN_K_COUNT = 8
@@ -250,9 +253,11 @@ class Context:
         self._check(self.lib.gsn_set_dataset_factors(self.h, self.n_datasets, self.n_species, pr, pf))
 
     def minimize_batch_dev(self, params, counts, wins, free, lo=None, hi=None, scale=None, max_evals=200,
-                           gtol=-1.0, ftol=-1.0, nll=None, evals=None, status=None):
-        """Batched L-BFGS minimisation (gsn_minimize_batch_dev); params (torch, device) is overwritten
-        with the minima.  Returns (nll, evals, status) device tensors."""
+                           gtol=-1.0, ftol=-1.0, nll=None, evals=None, status=None, scale_dev=None, edm=0.0):
+        """Batched L-BFGS minimisation (gsn_minimize_batch_dev; with scale_dev, a [T][P] device tensor
+        of per-toy scales, gsn_minimize_batch_scaled_dev, which also takes the edm stopping rule);
+        params (torch, device) is overwritten with the minima.  Returns (nll, evals, status) device
+        tensors."""
         import torch
         T = params.shape[0]
         dev = params.device
@@ -267,12 +272,30 @@ class Context:
             else:
                 a, pa = _d(v)
                 args.append((a, pa))
-        self._check(self.lib.gsn_minimize_batch_dev(
-            self.h, T, C.c_void_p(params.data_ptr()), C.c_void_p(counts.data_ptr()), C.c_void_p(wins.data_ptr()),
-            fr.ctypes.data_as(C.POINTER(C.c_ubyte)), *(a[1] if a else None for a in args), int(max_evals),
-            float(gtol), float(ftol), C.c_void_p(nll.data_ptr()), C.c_void_p(evals.data_ptr()),
-            C.c_void_p(status.data_ptr())))
+        head = (self.h, T, C.c_void_p(params.data_ptr()), C.c_void_p(counts.data_ptr()), C.c_void_p(wins.data_ptr()),
+                fr.ctypes.data_as(C.POINTER(C.c_ubyte)), args[0][1] if args[0] else None,
+                args[1][1] if args[1] else None)
+        outs = (C.c_void_p(nll.data_ptr()), C.c_void_p(evals.data_ptr()), C.c_void_p(status.data_ptr()))
+        if scale_dev is not None:
+            self._check(self.lib.gsn_minimize_batch_scaled_dev(*head, C.c_void_p(scale_dev.data_ptr()), int(max_evals),
+                                                               float(gtol), float(ftol), float(edm), *outs))
+        else:
+            if edm > 0.0:
+                raise ValueError("the edm stopping rule needs per-toy scales (scale_dev)")
+            self._check(self.lib.gsn_minimize_batch_dev(*head, args[2][1] if args[2] else None, int(max_evals),
+                                                        float(gtol), float(ftol), *outs))
         return nll, evals, status
+
+    def window_scales_dev(self, params, wins, scale=None, max_factor=0.0, out=None):
+        """Per-toy minimiser scales (gsn_window_scales_dev): a [T][P] device tensor."""
+        import torch
+        T = params.shape[0]
+        out = out if out is not None else torch.empty(T, self.n_params, dtype=torch.float64, device=params.device)
+        sc = None if scale is None else _d(scale)
+        self._check(self.lib.gsn_window_scales_dev(self.h, T, C.c_void_p(params.data_ptr()),
+                                                   C.c_void_p(wins.data_ptr()), sc[1] if sc else None,
+                                                   float(max_factor), C.c_void_p(out.data_ptr())))
+        return out
 
     def set_secondary(self, dataset, slice_start, shapes, counts=None):
         """Secondary observable of a dataset: slice boundaries (Q+1,), shapes (S, Q, M), counts (Q, M)."""

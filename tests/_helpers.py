@@ -42,8 +42,9 @@ def _workload(name):
 
 def oracle_task(task):
     """One oracle job of a pool: ("toy", workload, (params, counts, windows, want_grad)) -> (NLL,
-    gradient or None); ("fisher", workload, (params, windows)) -> Fisher diagonal.  The workload is
-    a workload dictionary or the name of a full-size one built in the child."""
+    gradient or None); ("fisher", workload, (params, windows)) -> Fisher diagonal; ("fit", workload,
+    (counts, start, free, lo, windows, scale)) -> (minimum, NLL there).  The workload is a workload
+    dictionary or the name of a full-size one built in the child."""
     kind, w, args = task
     w = _workload(w) if isinstance(w, str) else w
     if kind == "toy":
@@ -53,6 +54,9 @@ def oracle_task(task):
     if kind == "fisher":
         params, windows = args
         return O.fisher_diagonal(w, params, windows)
+    if kind == "fit":
+        counts, start, free, lo, windows, scale = args
+        return O.fit(w, counts, start, free, lo=lo, windows=windows, scale=scale)
     raise ValueError(kind)
 
 
