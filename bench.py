@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mv-toys", type=int, default=1024, help="toys of the multivariate workload")
     ap.add_argument("--fit-toys", type=int, default=1024, help="toys of the discovery-test workload")
+    ap.add_argument("--minimiser", default="newton", choices=["newton", "lbfgs"],
+                    help="discovery workload: batched Newton rate fits, or L-BFGS with window scales")
     ap.add_argument("--secondary", default=None, metavar="QxM",
                     help="toys workload with a secondary observable on both datasets: Q energy slices with "
                          "M secondary bins each (section 2.4 multivariate pieces), e.g. 8x16")
@@ -460,6 +462,20 @@ def run_ours(args, rank, world, local_rank):
             "frac": achieved / peak, "traffic": None if (gg or sec) else ncu_traffic(dom), "kernel": dom,
             "peak_basis": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock {sm_mhz:.0f} MHz",
             "pairs_per_launch": kunits / max(kn, 1), "ms_per_launch": per_launch_s * 1e3}
+    # method-level figures beside the FLOP fraction: (bin, column) pairs per second of both response
+    # kernels against the measured rate of one quadrature node (2 FFMA + EX2 + FFMA, three nodes per
+    # pair), and the FLOP rate against the measured FFMA rate (probes outside the timed region)
+    node_rate = gsn.peak_probe(gsn.GSN_PROBE_NODE, local_rank)
+    ffma_rate = gsn.peak_probe(gsn.GSN_PROBE_FFMA, local_rank)
+    roof["frac_of_measured_ffma"] = achieved / (2.0 * ffma_rate)
+    roof["measured_ffma_tflops"] = 2.0 * ffma_rate / 1e12
+    method = {}
+    for kname in ("forward", "backward"):
+        kms_, kn_, ku_ = prof[kname]
+        if kn_ and ku_:
+            pps = ku_ / (kms_ * 1e-3)
+            method[kname] = {"pairs_per_s": pps, "node_evals_per_s": 3.0 * pps, "measured_node_peak_per_s": node_rate,
+                             "frac_of_node_peak": 3.0 * pps / node_rate}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -484,7 +500,8 @@ def run_ours(args, rank, world, local_rank):
                                          "value is the traced run (events around every launch)"},
                 "plan": ctx.plan_info(min(T, 4096), True),
                 "status_nonzero_toys": int(np.count_nonzero(st)),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "roofline": roof, "pairs_vs_node_peak": method, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches,
                 "kernels": {k: {"ms_total": v[0], "launches": v[1], "pairs": v[2]} for k, v in prof.items() if v[1]}}
         print(json.dumps(line), flush=True)
     if dist:
@@ -788,14 +805,20 @@ def run_discovery(args):
     torch.cuda.synchronize(dev)
     EDM = 1e-5  # stop at an estimated distance to the minimum of 1e-5 in NLL (q0 to 2e-5)
 
+    newton = args.minimiser == "newton"
+
     def fits():
         x1 = torch.from_numpy(start.copy()).to(dev)
-        sc1 = ctx.window_scales_dev(x1, wins, scale=scale)
-        f1, e1, s1 = ctx.minimize_batch_dev(x1, counts, wins, free=free, lo=lo, max_evals=300, scale_dev=sc1,
-                                            edm=EDM)
         x0 = torch.from_numpy(start0.copy()).to(dev)
-        f0, e0, s0 = ctx.minimize_batch_dev(x0, counts, wins, free=free0, lo=lo, max_evals=300, scale_dev=sc1,
-                                            edm=EDM)
+        if newton:  # exact Newton on the rates (the response held): gsn_fit_rates_batch_dev
+            f1, e1, s1 = ctx.fit_rates_batch_dev(x1, counts, wins, free=free, lo=lo)
+            f0, e0, s0 = ctx.fit_rates_batch_dev(x0, counts, wins, free=free0, lo=lo)
+        else:       # L-BFGS with per-toy window scales and the EDM rule
+            sc1 = ctx.window_scales_dev(x1, wins, scale=scale)
+            f1, e1, s1 = ctx.minimize_batch_dev(x1, counts, wins, free=free, lo=lo, max_evals=300, scale_dev=sc1,
+                                                edm=EDM)
+            f0, e0, s0 = ctx.minimize_batch_dev(x0, counts, wins, free=free0, lo=lo, max_evals=300, scale_dev=sc1,
+                                                edm=EDM)
         return f1, e1, s1, f0, e0, s0
 
     fits()  # warm-up: plans, graphs
@@ -815,12 +838,14 @@ def run_discovery(args):
             "dtype": "f32 response, f64 deviance and minimiser state", "data": "synthetic",
             "config": {"workload": WORKLOAD + "; every toy in its own window (600..1200 bins)", "toys": T,
                        "free": [w["param_names"][i] for i in np.nonzero(free)[0]], "signal": w["param_names"][sig],
-                       "minimiser": "projected L-BFGS per toy, history 16, per-toy window scales, stop at "
-                                    "gtol 1e-4 (scaled) or an estimated distance to the minimum below 1e-5"},
-            "evals_per_fit": {"mean": float(ev.mean()), "max": int(ev.max())},
+                       "minimiser": ("projected Newton on the rates with the exact Hessian (response held), "
+                                     "stop at a Newton decrement / 2 below 1e-8") if newton else
+                                    ("projected L-BFGS per toy, history 16, per-toy window scales, stop at "
+                                     "gtol 1e-4 (scaled) or an estimated distance to the minimum below 1e-5")},
+            ("newton_iterations_per_fit" if newton else "evals_per_fit"): {"mean": float(ev.mean()), "max": int(ev.max())},
             "status_counts": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
             "q0": {"median": float(np.median(q0)), "p90": float(np.percentile(q0, 90)), "max": float(q0.max())},
-            "nll_evals_per_s": float(ev.sum() * 1.0 / dt), "clocks": clk}
+            **({} if newton else {"nll_evals_per_s": float(ev.sum() * 1.0 / dt)}), "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

@@ -92,7 +92,7 @@ extern "C" {
 #define GSN_MAX_DATASETS  512  /* histograms, or slices of histograms (section 2.4) */
 #define GSN_MAX_SPECIES   64
 #define GSN_MAX_GROUPS    256  /* distinct (edges, response slots, response multipliers);
-                                  at most 3 datasets share one response evaluation */
+                                  at most 4 datasets share one response evaluation */
 
 typedef struct gsn_ctx gsn_ctx;
 
@@ -305,6 +305,39 @@ int gsn_minimize_batch_scaled_dev(gsn_ctx* ctx, int n_toys, double* params_dev, 
                                   const int* toy_win_dev, const unsigned char* free_mask, const double* lo,
                                   const double* hi, const double* scale_dev, int max_evals, double gtol, double ftol,
                                   double edm, double* nll_dev, int* evals_dev, int* status_dev);
+
+/* Batched profile-likelihood fits over rates only (section 4.2: the discovery test fits rates
+ * with the detector response held).  With the response parameters fixed, every species' expected
+ * counts are a fixed shape times its rate, so a toy's expected counts are linear in the free rates
+ * and its NLL is convex in them; each toy is minimised by projected Newton iterations with the
+ * exact Hessian sum_i n_i B_i B_i^T / mu_i^2 (B_i the free rates' shapes in bin i, pulls added),
+ * backtracking on the exact NLL change, until the Newton decrement g.H^-1.g / 2 (the estimated
+ * distance to the minimum) is below tol.  Strongly correlated rates, which slow the L-BFGS of
+ * gsn_minimize_batch_dev, cost Newton nothing.  The shapes are computed once per call at the toys'
+ * start points (the response parameters and the held rates are taken from params_dev).
+ * A free rate whose expected counts inside the toy's window are at most 1e3 exp(-band_cut) of its
+ * expected counts over the whole histograms (1e-6 with the mixed default band, 1e-12 with FP64)
+ * stays at its start value: it reaches the window only through response tails that the band
+ * truncates, and its rate is not determined by the data there.
+ *   params_dev   [n_toys][n_params] device: start points in, minima out
+ *   toy_counts_dev, toy_win_dev   as in gsn_eval_grad_batch_dev
+ *   free_mask    [n_params] host: 1 = minimised over; every free parameter must fill rate slots
+ *                only (else GSN_ERR_ARG); at most 48 free rates
+ *   lo, hi       [n_params] host bounds (NULL: unbounded); rates usually lo = 0
+ *   max_iter     Newton iterations per toy (<= 0: 200: a rate that the window barely constrains
+ *                may have to grow by orders of magnitude, about a factor 2 per iteration); tol:
+ *                decrement at convergence, NLL units
+ *                (<= 0: 1e-8)
+ *   nll_dev      [n_toys] device: NLL at the minimum (FP64 sums of the context's expected counts)
+ *   iters_dev    [n_toys] device or NULL: iterations used
+ *   status_dev   [n_toys] device or NULL: 0 converged, 1 iteration limit, 2 no acceptable step
+ *                (the point returned is the best found), -4 non-finite NLL
+ * Synchronous.  Contexts with secondary observables are not taken (GSN_ERR_ARG).  The paper fits
+ * toys one after another with MINUIT. */
+int gsn_fit_rates_batch_dev(gsn_ctx* ctx, int n_toys, double* params_dev, const double* toy_counts_dev,
+                            const int* toy_win_dev, const unsigned char* free_mask, const double* lo,
+                            const double* hi, int max_iter, double tol, double* nll_dev, int* iters_dev,
+                            int* status_dev);
 
 /* Per-toy minimiser scales for fits in windows of the toys' own (section 4.2 toy Monte Carlo with
  * uneven fit ranges).  A toy's window holds part of each species' spectrum, and the rate of a

@@ -27,6 +27,7 @@ struct gsn_ctx {
     int dev = 0;
     double ex2_bias = 0.0;   // measured mean relative error of the SFU exponential on this device
     Buf wscale_b;            // gsn_window_scales_dev: [T][D][S] counts in the window and whole, scales [P]
+    Buf rfit_cfg, rfit_ws;   // gsn_fit_rates_batch_dev: bounds and indices; design rows, mu
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int nsm = 1;
@@ -63,6 +64,7 @@ struct gsn_ctx {
     // scratch
     Buf secRq_b, secN_b, secV_b, secW_b, secpart_b, secU_b;  // per-toy buffers of the secondary pieces
     Buf segbuf;              // forward segment prefix [T*G + 1]
+    Buf zerobuf;             // bin-at-zero records [T][G][K][NFZ] (gamma-family responses)
     Buf colbuf, colbuf2, blkbuf, mubuf, wbuf, partbuf, gdirect, devbuf, params, counts_b, win_b, nll_b, grad_b, status_b, Mbuf,
         outbuf;
     unsigned long long scratch_gen = 0;  // bumped whenever a buffer is (re)allocated
@@ -446,13 +448,16 @@ int finalize(gsn_ctx* c) {
         if ((rc = upload(c, ntab_d, &a.ntab_d))) return rc;
     }
     // fine centres and spectra
-    std::vector<float> Ehi(c->K), Elo(c->K), Sf(c->Sn.size());
+    std::vector<float> Ehi(c->K), Elo(c->K), Sf(c->Sn.size()), Sflo(c->Sn.size());
     for (int k = 0; k < c->K; ++k) { Ehi[k] = (float)c->E[k]; Elo[k] = (float)(c->E[k] - (double)Ehi[k]); }
-    for (size_t i = 0; i < Sf.size(); ++i) Sf[i] = (float)c->Sn[i];
+    for (size_t i = 0; i < Sf.size(); ++i) { Sf[i] = (float)c->Sn[i]; Sflo[i] = (float)(c->Sn[i] - (double)Sf[i]); }
     if ((rc = upload(c, c->E, &a.E))) return rc;
     if ((rc = upload(c, Ehi, &a.E_hi))) return rc;
     if ((rc = upload(c, Elo, &a.E_lo))) return rc;
-    if (mixed) { if ((rc = upload(c, Sf, &a.Sf))) return rc; }
+    if (mixed) {
+        if ((rc = upload(c, Sf, &a.Sf))) return rc;
+        if ((rc = upload(c, Sflo, &a.Sf_lo))) return rc;
+    }
     else       { if ((rc = upload(c, c->Sn, &a.Sd))) return rc; }
     if ((rc = upload(c, c->slot_map, &a.slot_map))) return rc;
     if ((rc = upload(c, c->pull_p, &a.pull_param))) return rc;
@@ -493,6 +498,26 @@ int finalize(gsn_ctx* c) {
             if ((rc = upload(c, sqhi, &a.sq_hi))) return rc;
             if ((rc = upload(c, sqsec, &a.sq_sec))) return rc;
             if ((rc = upload(c, sslice, &a.sec_slice))) return rc;
+            // per group: the next slice edge above every bin (node-table order)
+            int nnodes = 0;
+            for (int g = 0; g < c->G; ++g) nnodes = std::max(nnodes, tb.g_node_off[g] + tb.g_bins[g]);
+            std::vector<int> segend(nnodes, 0);
+            for (int g = 0; g < c->G; ++g) {
+                const int Jg = tb.g_bins[g];
+                std::vector<char> edge(Jg + 1, 0);
+                edge[Jg] = 1;
+                for (int dd = 0; dd < tb.g_nds[g]; ++dd) {
+                    const auto it = c->sec.find(tb.g_ds[g][dd]);
+                    if (it == c->sec.end()) continue;
+                    for (int e : it->second.start) if (e >= 0 && e <= Jg) edge[e] = 1;
+                }
+                int nxt = Jg;
+                for (int j = Jg - 1; j >= 0; --j) {
+                    if (edge[j + 1]) nxt = j + 1;
+                    segend[tb.g_node_off[g] + j] = nxt;
+                }
+            }
+            if ((rc = upload(c, segend, &a.sec_segend))) return rc;
         }
     }
     std::vector<double> cnt;
@@ -519,6 +544,8 @@ int reserve(gsn_ctx* c, int T, const Plan& p) {
     const int npart = NRESP + MAXGDS * c->S;
     int rc;
     if ((rc = ensure(c, c->colbuf, (size_t)T * c->G * c->K * NFP * rs))) return rc;
+    if (c->opt.resolution != GSN_RES_GAUSS &&
+        (rc = ensure(c, c->zerobuf, (size_t)T * c->G * c->K * NFZ * rs))) return rc;
     if (c->opt.resolution == GSN_RES_GGAMMA &&
         (rc = ensure(c, c->colbuf2, (size_t)T * c->G * c->K * NFG * sizeof(double)))) return rc;
     if ((rc = ensure(c, c->blkbuf, (size_t)T * c->G * nblk * 2 * rs))) return rc;
@@ -549,6 +576,7 @@ void fill(gsn_ctx* c, int T, const Plan& p, KArgs& a) {
     a.dev_chunks = p.dev_chunks;
     a.colbuf = c->colbuf.p; a.colbuf2 = (double*)c->colbuf2.p; a.blkbuf = c->blkbuf.p; a.mubuf = (double*)c->mubuf.p;
     a.segoff = (int*)c->segbuf.p;
+    a.zerobuf = c->opt.resolution != GSN_RES_GAUSS ? c->zerobuf.p : nullptr;
     a.wbuf = c->wbuf.p; a.partbuf = (double*)c->partbuf.p; a.gdirect = (double*)c->gdirect.p;
     a.devpart = (double*)c->devbuf.p;
     if (a.nsec) {
@@ -899,10 +927,10 @@ void gsn_destroy(gsn_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     free_owned(c);
-    for (Buf* b : {&c->fit_ws, &c->fit_cfg, &c->fit_eval, &c->fit_ist, &c->wscale_b})
+    for (Buf* b : {&c->fit_ws, &c->fit_cfg, &c->fit_eval, &c->fit_ist, &c->wscale_b, &c->rfit_cfg, &c->rfit_ws})
         if (b->p) cudaFree(b->p);
     for (Buf* b : {&c->secRq_b, &c->secN_b, &c->secV_b, &c->secW_b, &c->secpart_b, &c->secU_b,
-                   &c->segbuf, &c->colbuf, &c->colbuf2, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
+                   &c->segbuf, &c->zerobuf, &c->colbuf, &c->colbuf2, &c->blkbuf, &c->mubuf, &c->wbuf, &c->partbuf, &c->gdirect, &c->devbuf, &c->params, &c->counts_b,
                    &c->win_b, &c->nll_b, &c->grad_b, &c->status_b, &c->Mbuf, &c->outbuf, &c->s_hi, &c->s_lo,
                    &c->tc_part, &c->tc_err})
         if (b->p) cudaFree(b->p);
@@ -1493,6 +1521,93 @@ int gsn_minimize_batch_scaled_dev(gsn_ctx* c, int n_toys, double* params_dev, co
                           max_evals, gtol, ftol, edm, nll_dev, evals_dev, status_dev);
 }
 
+int gsn_fit_rates_batch_dev(gsn_ctx* c, int n_toys, double* params_dev, const double* toy_counts_dev,
+                            const int* toy_win_dev, const unsigned char* free_mask, const double* lo, const double* hi,
+                            int max_iter, double tol, double* nll_dev, int* iters_dev, int* status_dev) {
+    if (!c) return GSN_ERR_ARG;
+    int rc;
+    if ((rc = finalize(c))) return rc;
+    if (n_toys < 0) return fail(c, GSN_ERR_ARG, "n_toys must be >= 0");
+    if (n_toys == 0) return GSN_OK;
+    if (!params_dev || !toy_counts_dev || !toy_win_dev || !nll_dev || !free_mask)
+        return fail(c, GSN_ERR_ARG, "NULL argument");
+    if (c->base.nsec) return fail(c, GSN_ERR_ARG, "rate fits do not take secondary observables");
+    if (max_iter < 1) max_iter = 200;
+    if (!(tol > 0.0)) tol = 1e-8;
+    const int P = c->P, S = c->S, NSLOT = gsn_n_slots(S);
+    // free parameters: each must fill rate slots only
+    std::vector<int> fidx, pfree(P, -1);
+    std::vector<double> flo, fhi;
+    for (int p = 0; p < P; ++p) {
+        if (!free_mask[p]) continue;
+        bool rate = false;
+        for (int d = 0; d < c->D; ++d)
+            for (int sl = 0; sl < NSLOT; ++sl)
+                if (c->slot_map[(size_t)d * NSLOT + sl] == p) {
+                    if (sl >= S) return fail(c, GSN_ERR_ARG, "free parameter " + std::to_string(p) + " is not a rate");
+                    rate = true;
+                }
+        if (!rate) return fail(c, GSN_ERR_ARG, "free parameter " + std::to_string(p) + " fills no rate slot");
+        const double l = lo ? lo[p] : -INFINITY, h = hi ? hi[p] : INFINITY;
+        if (std::isnan(l) || std::isnan(h) || l > h) return fail(c, GSN_ERR_ARG, "bad bounds of parameter " + std::to_string(p));
+        pfree[p] = (int)fidx.size();
+        fidx.push_back(p); flo.push_back(l); fhi.push_back(h);
+    }
+    const int nf = (int)fidx.size();
+    if (nf > RF_NFMAX) return fail(c, GSN_ERR_ARG, "at most " + std::to_string(RF_NFMAX) + " free rates");
+    // toys per pass: per-species shapes and the design rows within 4 GiB
+    const size_t per_toy = (size_t)c->G * S * c->Jmax * sizeof(double) +
+                           (size_t)c->total_bins * ((size_t)nf + 4) * sizeof(double);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>({(size_t)c->opt.max_toys_per_launch,
+                                                                 (size_t)65535 / std::max(1, c->G),
+                                                                 ((size_t)4 << 30) / std::max<size_t>(per_toy, 1)}));
+    const int T0 = std::min(chunk, n_toys);
+    std::vector<double> cfg((size_t)2 * std::max(nf, 1));
+    for (int f = 0; f < nf; ++f) { cfg[f] = flo[f]; cfg[nf + f] = fhi[f]; }
+    std::vector<int> icfg(fidx);
+    icfg.insert(icfg.end(), pfree.begin(), pfree.end());
+    if ((rc = ensure(c, c->rfit_cfg, cfg.size() * sizeof(double) + icfg.size() * sizeof(int)))) return rc;
+    const size_t nb = (size_t)T0 * c->total_bins;
+    if ((rc = ensure(c, c->rfit_ws, nb * ((size_t)std::max(nf, 1) + 4) * sizeof(double)))) return rc;
+    if ((rc = ensure(c, c->Mbuf, (size_t)T0 * c->G * S * c->Jmax * sizeof(double)))) return rc;
+    double* cf = (double*)c->rfit_cfg.p;
+    int* ic = (int*)(cf + cfg.size());
+    CUDA_TRY(c, cudaMemcpyAsync(cf, cfg.data(), cfg.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(ic, icfg.data(), icfg.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    for (int t0 = 0; t0 < n_toys; t0 += chunk) {
+        const int T = std::min(chunk, n_toys - t0);
+        KArgs a = c->base;
+        const Plan p = make_plan(c, T);
+        if ((rc = prepare(c, T, p, a))) return rc;
+        a.params = params_dev + (size_t)t0 * P; a.params_stride = P;
+        a.counts = toy_counts_dev + (size_t)t0 * c->n_counts; a.counts_stride = c->n_counts;
+        a.win = toy_win_dev + (size_t)t0 * c->D * 2; a.win_stride = 2 * c->D;
+        a.Mbuf = (double*)c->Mbuf.p; a.mstride = (long long)c->G * S * c->Jmax;
+        a.sp_first = 0; a.sp_count = S;
+        a.want_grad = 0;
+        if (a.response) {
+            CUDA_TRY(c, cudaMemsetAsync(c->Mbuf.p, 0, (size_t)T * c->G * S * c->Jmax * sizeof(double), c->stream));
+            if ((rc = launch(c, K_COLUMNS, a, launch_columns))) return rc;
+            if ((rc = launch(c, K_SPECIES, a, launch_species))) return rc;
+        }
+        RateArgs r{};
+        r.nf = nf; r.max_iter = max_iter; r.tol = tol; r.fnoise = 1e-12;
+        r.share_min = 1e3 * std::exp(-c->opt.band_cut);
+        r.fidx = ic; r.pfree = ic + nf; r.lo = cf; r.hi = cf + nf;
+        r.params = params_dev + (size_t)t0 * P;
+        double* ws = (double*)c->rfit_ws.p;
+        const size_t nbT = (size_t)T * c->total_bins;
+        r.B = ws; r.C = ws + nbT * std::max(nf, 1); r.N = r.C + nbT; r.mu = r.N + nbT;
+        r.dmu = r.mu + nbT;
+        r.nll = nll_dev + t0;
+        r.iters = iters_dev ? iters_dev + t0 : nullptr;
+        r.status = status_dev ? status_dev + t0 : nullptr;
+        CUDA_TRY(c, launch_rate_fit(a, r, c->stream));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host configuration must outlive its copies
+    return GSN_OK;
+}
+
 int gsn_window_scales_dev(gsn_ctx* c, int n_toys, const double* params_dev, const int* toy_win_dev,
                           const double* scale, double max_factor, double* scale_dev) {
     if (!c) return GSN_ERR_ARG;
@@ -1617,7 +1732,7 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     KArgs a = c->base;
     const Plan p = make_plan(c, 1);
     const size_t rs = c->opt.precision == GSN_MIXED ? sizeof(float) : sizeof(double);
-    const size_t sizes[9] = {
+    const size_t sizes[10] = {
         (size_t)c->G * c->K * NFP * rs,                         // column records
         (size_t)c->G * a.nblk * 2 * rs,                         // band summaries
         (size_t)p.nsplit * c->total_bins * sizeof(double),      // partial mu
@@ -1626,9 +1741,10 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
         (size_t)c->P * sizeof(double),                          // direct gradient terms
         (size_t)p.dev_chunks * (2 + c->base.ntpl) * sizeof(double),   // deviance and template partials
         c->opt.resolution == GSN_RES_GGAMMA ? (size_t)c->G * c->K * NFG * sizeof(double) : 0,  // adjoint coefficients
-        ((size_t)c->G + 1) * sizeof(int)};                      // forward segment prefix
-    size_t off[9], total = 0;
-    for (int i = 0; i < 9; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
+        ((size_t)c->G + 1) * sizeof(int),                       // forward segment prefix
+        c->opt.resolution != GSN_RES_GAUSS ? (size_t)c->G * c->K * NFZ * rs : 0};  // bin-at-zero records
+    size_t off[10], total = 0;
+    for (int i = 0; i < 10; ++i) { off[i] = total; total += (sizes[i] + 255) & ~(size_t)255; }
     if (total > GSN_NOALLOC_SCRATCH_BYTES)
         return fail(c, GSN_ERR_ARG, "this problem needs " + std::to_string(total) + " bytes of scratch; the "
                     "no-allocation entry point holds " + std::to_string((size_t)GSN_NOALLOC_SCRATCH_BYTES));
@@ -1640,6 +1756,7 @@ extern "C" int gsn_eval_grad_noalloc(gsn_ctx* c, const double* params_dev, doubl
     a.dev_chunks = p.dev_chunks; a.devpart = (double*)(base + off[6]);
     a.colbuf2 = (double*)(base + off[7]);
     a.segoff = (int*)(base + off[8]);
+    a.zerobuf = c->opt.resolution != GSN_RES_GAUSS ? (void*)(base + off[9]) : nullptr;
     a.params = params_dev; a.params_stride = c->P;
     a.counts_stride = 0; a.win_stride = 0;
     a.nll = nll_dev; a.grad = grad_dev; a.status = status_dev;

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(WC_WARPS * 32) k_window_counts(KArgs a, double
             rp[i] = ri >= 0 ? prm[ri] * tb_g_rscale(a, g, i) : 0.0;
         }
         const double alpha = 1.0 + rp[1] * a.s0, beta = rp[1] * a.s1;
-        float xl[MAXGDS] = {0.f, 0.f, 0.f}, xh[MAXGDS] = {0.f, 0.f, 0.f};
+        float xl[MAXGDS] = {}, xh[MAXGDS] = {};
         for (int dd = 0; dd < nds; ++dd) {
             const int d = tb_g_ds(a, g, dd);
             const int lo = max(win[2 * d], 0), hi = min(win[2 * d + 1], J);
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(WC_WARPS * 32) k_window_counts(KArgs a, double
                 // the spectra are on the device in the context's precision only
                 const float* Srf = a.precision == 1 ? a.Sf + (long long)s * a.K + k0 : nullptr;
                 const double* Srd = a.precision == 1 ? nullptr : a.Sd + (long long)s * a.K + k0;
-                float pw[MAXGDS] = {0.f, 0.f, 0.f}, pf[MAXGDS] = {0.f, 0.f, 0.f};
+                float pw[MAXGDS] = {}, pf[MAXGDS] = {};
                 for (int i = lane; i < nk; i += 32) {
                     const float sv = Srf ? Srf[i] : (float)Srd[i];
                     for (int dd = 0; dd < nds; ++dd) {

@@ -186,7 +186,7 @@ DEV void gg_inc_gamma(double a, double y, double& P, double& Pa, double& py) {
 // ex2_scale = 1 / (1 + b), b the SFU exponentials' measured mean relative error; FP64: 1).
 template <class R>
 DEV double gg_column(double mu, double var, double p, double cut, double x1, bool zero_bin, bool mixed,
-                     double ex2_scale, R* f, double* gco, R& xmin, R& xmax) {
+                     double ex2_scale, R* f, R* z, double* gco, R& xmin, R& xmax) {
     const double a = 1.0 / p;
     const double r = log1p(var / (mu * mu));
     double Hx, lxs;                                   // dH/dx at the root, ln(d/p)
@@ -258,7 +258,7 @@ DEV double gg_column(double mu, double var, double p, double cut, double x1, boo
         gg_inc_gamma(xs, y, P, Pa, py);
         P0 = P; P0d = Pa / p; P0s = -p * py; P0p = -(d / (p * p)) * Pa + py * lxs;
     }
-    f[F_P0] = (R)(P0 / Nk);
+    z[Z_P0] = (R)(P0 / Nk);
     // moment matching H(x, a) = ln rho, ln s = ln mu - G(x, a): implicit derivatives of x and u = ln s
     // dH/da = 2 [psi(x + 2a) - psi(x + a)] = 2 (dH/dx + [psi(x + a) - psi(x)]): no cancellation
     const double da = gg_digamma_diff(xs, a);

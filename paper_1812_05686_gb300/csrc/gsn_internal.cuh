@@ -8,7 +8,7 @@ namespace gsn {
 constexpr int MAXD = 512;    // datasets (histograms, or slices of histograms along a second observable)
 constexpr int MAXS = 64;     // species
 constexpr int MAXG = 256;    // response groups
-constexpr int MAXGDS = 3;    // datasets sharing one response group
+constexpr int MAXGDS = 4;    // datasets sharing one response group
 
 // Gauss-Legendre nodes per bin.  Mixed: 3 linear nodes, 6 log-spaced nodes for
 // bins whose lower edge lies below XLOG_F.  FP64: 5 linear, 10 log-spaced below XLOG_D.
@@ -24,7 +24,10 @@ constexpr int NFP = 16;      // fields per column record
 
 // Column record fields.
 //  mixed gamma : MUH/MUL double-float mean, A = 1/mu, B = d, C = -1/s,
-//                N = density at the mean, KAPPA = ln d - psi(d)
+//                KAPPA = ln d - psi(d), XM = log2 f(mode)/f(mu) (0 for d <= 1), N = density
+//                at the mode: the response kernels evaluate log2 f(x)/f(mu) - XM, whose
+//                maximum is 0, as the SFU exponential's calibration (a profile peaking at 0)
+//                assumes
 //  mixed gauss : MUH/MUL, A = 1/sigma, N = 1/(sigma sqrt(2 pi))
 //  fp64 gamma  : MUH = mu, A = -d ln s - lgamma(d), B = d-1, C = 1/s,
 //                KAPPA = ln s + psi(d), N = 1
@@ -34,13 +37,17 @@ constexpr int NFP = 16;      // fields per column record
 //                (log f(x)/f(mu) = kappa_1 L - A_p (e^(pL) - 1 - pL), L = ln(x/mu))
 //  fp64 ggamma : MUH = mu, A = ln p - d ln s - lgamma(d/p), B = d-1, C = ln s,
 //                KAPPA = p, N = 1
-//  all         : DEQ = d E_q / d kB, XMIN/XMAX = band in p.e., P0 = bin-at-zero
-//                content / N; P0D/P0S its derivatives (gamma): fp64 dP/dd and s^2 dP/ds,
-//                mixed (mu/d) dP/dmu|var / N and s^2 dP/dvar|mu / N;
+//  all         : DEQ = d E_q / d kB, XMIN/XMAX = band in p.e.,
 //                TN0.. = N_k * T_dk of each dataset of the group
-enum { F_MUH = 0, F_MUL, F_A, F_B, F_C, F_N, F_KAPPA, F_DEQ, F_XMIN, F_XMAX,
-       F_P0, F_P0D, F_P0S, F_TN0 };
-static_assert(F_TN0 + MAXGDS <= NFP, "column record too small");
+enum { F_MUH = 0, F_MUL, F_A, F_B, F_C, F_N, F_KAPPA, F_DEQ, F_XMIN, F_XMAX, F_TN0 };
+constexpr int F_XM = F_TN0 + MAXGDS;
+static_assert(F_XM < NFP, "column record too small");
+// Bin-at-zero record of a column (gamma-family responses, NFZ values, zerobuf): P0 = content of the
+// bin starting at 0 over N; P0D/P0S its derivatives (gamma): fp64 dP/dd and s^2 dP/ds, mixed
+// (mu/d) dP/dmu|var / N and s^2 dP/dvar|mu / N.  Kept out of the column record, which the response
+// kernels stream for every bin, so that the record holds a T_dk for up to MAXGDS datasets.
+constexpr int NFZ = 4;
+enum { Z_P0 = 0, Z_P0D, Z_P0S };
 
 // Adjoint coefficients of a generalized-gamma column (second record, NFG doubles): the adjoint
 // accumulates over the band U = (sum W rho, sum W S1, sum W S2, sum W S3, W at the bin at zero),
@@ -115,6 +122,8 @@ struct KArgs {
     const float* E_hi;          // double-float split of E
     const float* E_lo;
     const float* Sf;            // normalised shifted spectra [S][K]
+    const float* Sf_lo;         // their FP32 residuals S' - Sf (mixed): a piecewise-constant spectrum
+                                // would otherwise carry one rounding error over its whole range
     const double* Sd;
     const int* slot_map;        // [D][NSLOT]
     const int* pull_param;
@@ -126,6 +135,7 @@ struct KArgs {
     const int* win;        long long win_stride;      // [T][D][2]
     // scratch
     void* colbuf;          // [T][G][K][NFP] of Real
+    void* zerobuf;         // [T][G][K][NFZ] of Real: bin-at-zero values (gamma-family responses)
     double* colbuf2;       // [T][G][K][NFG]: adjoint coefficients (generalized gamma only)
     void* blkbuf;          // [T][G][nblk][2] of Real: min xmin, max xmax
     double* mubuf;         // [T][nsplit][total_bins]
@@ -167,6 +177,9 @@ struct KArgs {
     const int* sq_hi;
     const int* sq_sec;     // [Qtot] secondary dataset index of the slice
     const int* sec_slice;  // [total_bins] global slice of every energy bin, -1 outside the slices
+    const int* sec_segend; // [group bins, node-table order] first slice edge of any dataset of the
+                           // group above the bin (or the group's bin count): batches of the tuned
+                           // kernels end there, so a batch lies in one slice of every dataset
     double* secN;          // [T][Qtot][S] unscaled per-species slice sums
     double* secV;          // [T][Qtot][S] dNLL / dN_sq per unit rate coefficient
     double* secW;          // [T][nsecb] 1 - n/mu of every secondary bin
@@ -208,6 +221,29 @@ struct FitArgs {
     int* active;                // toys still running after the update
 };
 cudaError_t launch_lbfgs(const FitArgs& f, cudaStream_t st);
+
+// Newton fits over rates only (gsn_ratefit.cu); per toy t, bins i of all datasets
+constexpr int RF_NFMAX = 48;    // free rates at most
+struct RateArgs {
+    int nf, max_iter;
+    double tol;                 // Newton decrement / 2 at convergence (NLL units)
+    double fnoise;              // relative rounding allowance of the Armijo test
+    double share_min;           // a free rate with window share at most this stays at its start
+    const int* fidx;            // [nf] global index of each free rate
+    const int* pfree;           // [P] free index of a parameter, -1 if held
+    const double* lo;           // [nf] bounds
+    const double* hi;
+    double* params;             // [T][P]: start points in, minima out
+    double* B;                  // [T][total_bins][nf] summed shapes of the free rates (whole histograms)
+    double* C;                  // [T][total_bins] expected counts of the held species
+    double* N;                  // [T][total_bins] counts, -1 outside the window
+    double* mu;                 // [T][total_bins]
+    double* dmu;                // [T][total_bins]
+    double* nll;                // [T]
+    int* iters;                 // [T] or NULL
+    int* status;                // [T] or NULL
+};
+cudaError_t launch_rate_fit(const KArgs& a, const RateArgs& r, cudaStream_t st);
 // per-toy minimiser scales: scale [P] (device) times sqrt(N_whole / N_window) for rate parameters;
 // nwin, nfull: [T][D][S] scratch; out [T][P]
 cudaError_t launch_window_scales(const KArgs& a, double* nwin, double* nfull, const double* scale, double max_factor,
@@ -233,6 +269,7 @@ cudaError_t launch_backward_mixed(const KArgs& a, cudaStream_t st);
 cudaError_t launch_secondary(const KArgs& a, cudaStream_t st);
 cudaError_t launch_secondary_weights(const KArgs& a, cudaStream_t st);
 cudaError_t launch_slice_sums(const KArgs& a, cudaStream_t st);
+cudaError_t launch_slice_sums_mixed(const KArgs& a, cudaStream_t st);
 
 constexpr int K_COLUMNS = 0, K_FORWARD = 1, K_DEVIANCE = 2, K_BACKWARD = 3, K_GRADFINAL = 4,
               K_SPECIES = 5, K_MU = 6, K_DEVFINAL = 7, K_COUNT = 8;

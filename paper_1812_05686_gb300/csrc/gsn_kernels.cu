@@ -72,9 +72,11 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
     R xmin = (R)INFINITY, xmax = (R)-INFINITY;
     if (k < a.K) {
         R* rec = colrec<R>(a, t, g, k);
-        R f[NFP];
+        R f[NFP], z[NFZ];
 #pragma unroll
         for (int i = 0; i < NFP; ++i) f[i] = 0;
+#pragma unroll
+        for (int i = 0; i < NFZ; ++i) z[i] = 0;
         R Nk = 1;
         if constexpr (RES == 2) {
             // generalized gamma: mean, variance and everything of the column in FP64
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
             if constexpr (sizeof(R) == 4) f[F_MUL] = (R)(mud - (double)(R)mud);
             double gco[NFG];
             const double x1 = a.edges[tb_g_edge_off<FAST>(a, g) + 1];
-            Nk = (R)gg_column<R>(mud, vard, sres[5], a.cut, x1, tb_g_zero<FAST>(a, g) != 0, sizeof(R) == 4, a.ex2_scale, f, gco,
+            Nk = (R)gg_column<R>(mud, vard, sres[5], a.cut, x1, tb_g_zero<FAST>(a, g) != 0, sizeof(R) == 4, a.ex2_scale, f, z, gco,
                                  xmin, xmax);
             double* g2 = a.colbuf2 + (((long long)t * a.G + g) * a.K + k) * NFG;
 #pragma unroll
@@ -152,17 +154,44 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
                     f[F_A] = 1.0f / mu;
                     f[F_B] = d;
                     f[F_C] = -1.0f / s;
+                    // exponent offset XM: the log2 density at the mode t = -1/d over that at the
+                    // mean, L2E ((d-1) ln(1 - 1/d) + 1) = L2E sum_k u^k / (k (k+1)), u = 1/d, from
+                    // the FP32 shape the kernels use; the normalisation takes the factor 2^XM, so
+                    // that values are unchanged
                     if (d >= 8.0f) {
                         // density at the mean: exp(-corr(d)) / (sigma sqrt(2 pi)), corr = Stirling remainder
                         const float id = 1.0f / d, id2 = id * id;
                         const float corr = id * (1.0f / 12 - id2 * (1.0f / 360 - id2 * (1.0f / 1260 - id2 * (1.0f / 1680))));
-                        const float nq = expf(-corr) * rsqrtf(var);
+                        float m = fmaf(id, 1.0f / 72, 1.0f / 56);
+                        m = fmaf(m, id, 1.0f / 42);
+                        m = fmaf(m, id, 1.0f / 30);
+                        m = fmaf(m, id, 1.0f / 20);
+                        m = fmaf(m, id, 1.0f / 12);
+                        m = fmaf(m, id, 1.0f / 6);
+                        m = fmaf(m, id, 0.5f);
+                        const float xm = mul_l2e(m * id);
+                        f[F_XM] = xm;
+                        // exp(y), |y| < 0.06, by its Taylor polynomial (remainder below 1e-12), and a
+                        // correctly rounded 1/sigma: expf and rsqrtf go through SFU approximations
+                        // whose errors vary slowly with the argument, and y and the variance vary
+                        // slowly from column to column, so neighbouring columns would share the error
+                        const float y = fmaf(xm, 0.69314718f, -corr);
+                        float ey = fmaf(y, 1.0f / 720, 1.0f / 120);
+                        ey = fmaf(ey, y, 1.0f / 24);
+                        ey = fmaf(ey, y, 1.0f / 6);
+                        ey = fmaf(ey, y, 0.5f);
+                        ey = fmaf(ey, y, 1.0f);
+                        ey = fmaf(ey, y, 1.0f);
+                        const float nq = ey * (1.0f / sqrtf(var));
                         Nk = fmaf(nq, a.norm_hi, nq * a.norm_lo);
                         f[F_KAPPA] = 0.5f * id + id2 * (1.0f / 12 - id2 * (1.0f / 120 - id2 * (1.0f / 252 - id2 * (1.0f / 240))));
                     } else {
+                        const double df = (double)d;
+                        const float xm = df > 1.0 ? (float)(1.4426950408889634 * fma(df - 1.0, log1p(-1.0 / df), 1.0)) : 0.0f;
+                        f[F_XM] = xm;
                         const double dd = (double)mu * (double)mu / (double)var, sd = (double)var / (double)mu;
-                        Nk = (float)(exp((dd - 1.0) * log((double)mu) - (double)mu / sd - dd * log(sd) - lgamma(dd)) *
-                                     a.ex2_scale);
+                        Nk = (float)(exp((dd - 1.0) * log((double)mu) - (double)mu / sd - dd * log(sd) - lgamma(dd) +
+                                         0.69314718055994531 * (double)xm) * a.ex2_scale);
                         f[F_KAPPA] = (float)(log(dd) - digamma_d(dd));
                     }
                 } else {
@@ -208,13 +237,13 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
                     if (xmin <= x1) {
                         R P, Pd, Ps2;
                         gamma_bin_zero<R>(d, s, x1, P, Pd, Ps2);
-                        f[F_P0] = P / Nk;
+                        z[Z_P0] = P / Nk;
                         if constexpr (sizeof(R) == 4) {
                             // mixed adjoint: (mu/d) dP/dmu at fixed variance, s^2 dP/dvar at fixed mean
-                            f[F_P0D] = (R(2) * Pd - Ps2 / mu) / Nk;
-                            f[F_P0S] = (Ps2 / mu - Pd) / Nk;
+                            z[Z_P0D] = (R(2) * Pd - Ps2 / mu) / Nk;
+                            z[Z_P0S] = (Ps2 / mu - Pd) / Nk;
                         } else {
-                            f[F_P0D] = Pd; f[F_P0S] = Ps2;
+                            z[Z_P0D] = Pd; z[Z_P0S] = Ps2;
                         }
                     }
                 }
@@ -224,19 +253,35 @@ __global__ void __launch_bounds__(COLBLK) k_columns(KArgs a) {
         f[F_XMIN] = xmin;
         f[F_XMAX] = xmax;
         for (int dd = 0; dd < tb_g_nds<FAST>(a, g); ++dd) {
-            R T = 0;
             if constexpr (sizeof(R) == 4) {
-                // the lo parts first: the hi products then enter exactly into the running sum, so
-                // the correction survives the roundings (added last, it would be below half an ulp)
-                for (int s = 0; s < a.S; ++s) T = fmaf(srate_lo[dd][s], a.Sf[(long long)s * a.K + k], T);
-                for (int s = 0; s < a.S; ++s) T = fmaf(srate[dd][s], a.Sf[(long long)s * a.K + k], T);
+                // T = sum_s rate_s S'_sk as an unevaluated FP32 pair (Th + Tl): the products' and the
+                // sums' rounding errors and the rates' and spectra's residuals go to Tl, and T N is
+                // rounded once.  Where the spectra are constant over a range of columns (a flat or
+                // shoulder species), a rounded T would repeat one rounding error in all of them;
+                // the rounding of T N varies with N from column to column.
+                float Th = 0.f, Tl = 0.f;
+                for (int s = 0; s < a.S; ++s) {
+                    const float sv = a.Sf[(long long)s * a.K + k], r = srate[dd][s];
+                    const float p = r * sv;
+                    Tl = fmaf(r, sv, -p) + Tl;
+                    Tl = fmaf(srate_lo[dd][s], sv, Tl);
+                    Tl = fmaf(r, a.Sf_lo[(long long)s * a.K + k], Tl);
+                    two_sum_acc(Th, Tl, p);
+                }
+                f[F_TN0 + dd] = fmaf(Th, Nk, Tl * Nk);
             } else {
+                R T = 0;
                 for (int s = 0; s < a.S; ++s) T = fma(srate[dd][s], a.Sd[(long long)s * a.K + k], T);
+                f[F_TN0 + dd] = T * Nk;
             }
-            f[F_TN0 + dd] = T * Nk;
         }
 #pragma unroll
         for (int i = 0; i < NFP; ++i) rec[i] = f[i];
+        if (a.zerobuf) {
+            R* zr = zerorec<R>(a, t, g, k);
+#pragma unroll
+            for (int i = 0; i < NFZ; ++i) zr[i] = z[i];
+        }
     }
     // band summary of this column block
     R mn = warp_min<R>(xmin), mx = warp_max<R>(xmax);
@@ -281,7 +326,7 @@ DEV int forward_loop(const KArgs& a, int t, int g, int split, float xlo_w, float
     for (int b = k_beg / COLBLK; b * COLBLK < k_end; ++b) {
         if (blk[2 * b + 1] < (R)xlo_w || blk[2 * b] > (R)xhi_w) continue;
         // FP32: partial sums of up to 32 columns folded into compensated (s, cs) pairs
-        R acc[MAXGDS] = {0, 0, 0}, sacc[MAXGDS] = {0, 0, 0}, cacc[MAXGDS] = {0, 0, 0};
+        R acc[MAXGDS] = {}, sacc[MAXGDS] = {}, cacc[MAXGDS] = {};
         const int kb = max(b * COLBLK, k_beg), ke = min((b + 1) * COLBLK, k_end);
         for (int k = kb; k < ke; ++k) {
             const R* c = colrec<R>(a, t, g, k);
@@ -292,11 +337,11 @@ DEV int forward_loop(const KArgs& a, int t, int g, int split, float xlo_w, float
                 if constexpr (RES == 2 && NG == 3) v = gg_bin_value_f3(c, xc, lam, wt, sides);
                 else if constexpr (RES == 2) v = gg_bin_value_f<NG>(c, xc, lam, wt);
                 else v = bin_value_f<RES, NG>(c, xc, del, lam, wt);
-                if (RES >= 1 && is_zero) v = valid ? c[F_P0] : 0.0f;
+                if (RES >= 1 && is_zero) v = valid ? zerorec<R>(a, t, g, k)[Z_P0] : 0.0f;
             } else {
                 if constexpr (RES == 2) v = gg_bin_value_d<NG>(c, lam, wt);
                 else v = bin_value_gamma_d<NG>(c, del, lam, wt);
-                if (is_zero) v = valid ? c[F_P0] : 0.0;
+                if (is_zero) v = valid ? zerorec<R>(a, t, g, k)[Z_P0] : 0.0;
             }
 #pragma unroll
             for (int dd = 0; dd < MAXGDS; ++dd)
@@ -349,7 +394,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(KArgs a) {
     const float xhi_w = (float)a.edges[tb_g_edge_off(a, g) + jl + 1];
     const unsigned char cls = a.bclass[nb];
     const bool low = __any_sync(0xffffffffu, cls != BIN_LIN);
-    double accd[MAXGDS] = {0.0, 0.0, 0.0};
+    double accd[MAXGDS] = {};
     int ncol;
     if constexpr (sizeof(R) == 4) {
         const float* nodes = a.ntab_f + (long long)nb * 3 * NGM_F;
@@ -389,7 +434,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32) k_forward_gauss64(KArgs a) {
     const int kchunk = (a.K + a.nsplit - 1) / a.nsplit;
     const int k_beg = split * kchunk, k_end = min(a.K, k_beg + kchunk);
     const double* blk = reinterpret_cast<const double*>(a.blkbuf) + ((long long)t * a.G + g) * a.nblk * 2;
-    double acc[MAXGDS] = {0.0, 0.0, 0.0};
+    double acc[MAXGDS] = {};
     int ncol = 0;
     for (int b = k_beg / COLBLK; b * COLBLK < k_end; ++b) {
         if (blk[2 * b + 1] < xlo_w || blk[2 * b] > xhi_w) continue;
@@ -716,11 +761,11 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
             }
         return u * c[F_N];
     };
-    R U0[MAXGDS] = {0, 0, 0};
+    R U0[MAXGDS] = {};
     R U1 = 0, U2 = 0;
     // generalized gamma: W-weighted node sums (rho, S1, S2, S3; compensated in FP32) and the W of
     // the bin at zero, mapped to the mean / variance / power derivatives by the adjoint record
-    R Gs[4] = {0, 0, 0, 0}, Gc[4] = {0, 0, 0, 0}, Z0 = 0, U0c[MAXGDS] = {0, 0, 0};
+    R Gs[4] = {0, 0, 0, 0}, Gc[4] = {0, 0, 0, 0}, Z0 = 0, U0c[MAXGDS] = {};
     const int nbase = tb_g_node_off(a, g);
     if constexpr (RES == 2) {
         const R p = c[F_KAPPA];
@@ -751,7 +796,7 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
             const unsigned char cls = a.bclass[nbase + j];
             R rho = 0;
             if (cls == BIN_ZERO) {
-                rho = c[F_P0];
+                rho = zerorec<R>(a, t, g, kval ? k : a.K - 1)[Z_P0];
                 Z0 += Wj;
             } else {
                 R s1 = 0, s2 = 0, s3 = 0;
@@ -844,9 +889,10 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
             const unsigned char cls = a.bclass[nbase + j];
             R rho = 0;
             if (RES == 1 && cls == BIN_ZERO) {
-                rho = c[F_P0];
-                U1 = fma(Wj, c[F_P0D], U1);
-                U2 = fma(Wj, c[F_P0S], U2);
+                const R* zr = zerorec<R>(a, t, g, kval ? k : a.K - 1);
+                rho = zr[Z_P0];
+                U1 = fma(Wj, zr[Z_P0D], U1);
+                U2 = fma(Wj, zr[Z_P0S], U2);
             } else if constexpr (sizeof(R) == 4) {
                 const float* nd = a.ntab_f + (long long)(nbase + j) * 3 * NGM_F;
                 const float Dx = (a.xc_f[nbase + j] - c[F_MUH]) - c[F_MUL];
@@ -871,7 +917,7 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
                     const float Dt = log1pmx2_f(tt, L1);
                     const float P2 = mul_l2e(c[F_B]), Q2 = fmaf(L2E, c[F_B], fmaf(L2E_LO, c[F_B] - 1.0f, -L2E));
                     const float R2 = mul_l2e(c[F_C]);
-                    const float Ec = fmaf(P2, Dt, -L2E * L1);
+                    const float Ec = fmaf(P2, Dt, fmaf(-L2E, L1, -c[F_XM]));
                     const float kap = c[F_KAPPA];
                     float u1 = 0.f, u2 = 0.f;
                     for (int n = 0; n < NG; ++n) {
@@ -1050,11 +1096,11 @@ DEV void species_loop(const KArgs& a, int t, int g, float xlo_w, float xhi_w, bo
             if constexpr (sizeof(R) == 4) {
                 if constexpr (RES == 2) v = gg_bin_value_f<NG>(c, xc, lam, wt);
                 else v = bin_value_f<RES, NG>(c, xc, del, lam, wt);
-                if (RES >= 1 && is_zero) v = valid ? c[F_P0] : 0.0f;
+                if (RES >= 1 && is_zero) v = valid ? zerorec<R>(a, t, g, k)[Z_P0] : 0.0f;
             } else {
                 if constexpr (RES == 2) v = gg_bin_value_d<NG>(c, lam, wt);
                 else v = bin_value_gamma_d<NG>(c, del, lam, wt);
-                if (is_zero) v = valid ? c[F_P0] : 0.0;
+                if (is_zero) v = valid ? zerorec<R>(a, t, g, k)[Z_P0] : 0.0;
             }
             v *= c[F_N];
 #pragma unroll
@@ -1349,8 +1395,8 @@ cudaError_t launch_devfinal(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_backward(const KArgs& a, cudaStream_t st) {
-    // the tuned mixed adjoint serves the Gaussian and gamma responses without a secondary observable
-    if (a.precision == 1 && a.res != 2 && a.nsec == 0) return launch_backward_mixed(a, st);
+    // the tuned mixed adjoint serves the Gaussian and gamma responses (with or without secondary observables)
+    if (a.precision == 1 && a.res != 2) return launch_backward_mixed(a, st);
     dim3 grid(a.nbtask, a.G, a.T);
     const int threads = a.bw_warps * 32;
     const size_t rs = a.precision == 1 ? sizeof(float) : sizeof(double);

@@ -86,11 +86,12 @@ __global__ void __launch_bounds__(256) k_secondary(KArgs a) {
                 // FP32 products in compensated (TwoSum) lane sums: the FP64 rate would bound this
                 const float* Rq = reinterpret_cast<const float*>(a.secRq) + ((long long)t * a.Qtot + q0 + q) * a.K;
                 const float* Sr = a.Sf + (long long)s * a.K;
+                const float* Srl = a.Sf_lo + (long long)s * a.K;
                 float us = 0.f, uc = 0.f;
                 for (int k = lane; k < a.K; k += 32) {
                     const float pr = Rq[k] * Sr[k];
                     two_sum_acc(us, uc, pr);
-                    uc = fmaf(Rq[k], Sr[k], -pr) + uc;   // the product's rounding error
+                    uc = fmaf(Rq[k], Srl[k], fmaf(Rq[k], Sr[k], -pr) + uc);   // the product's rounding error, S' residual
                 }
                 u = (double)us + (double)uc;
             } else {
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(256) k_slice_sums(KArgs a) {
                     const unsigned char cls = a.bclass[nbase + j];
                     R v;
                     if (RES >= 1 && cls == BIN_ZERO) {
-                        v = c[F_P0];
+                        v = zerorec<R>(a, t, g, kval ? k : a.K - 1)[Z_P0];
                     } else if constexpr (sizeof(R) == 4) {
                         const float* nd = a.ntab_f + (long long)(nbase + j) * 3 * NGM_F;
                         const float xc = a.xc_f[nbase + j];
@@ -258,8 +259,7 @@ __global__ void __launch_bounds__(256) k_slice_sums(KArgs a) {
     }
 }
 
-// grid (column blocks, slices, toys)
-template <class R>
+// FP64: grid (column blocks, slices, toys)
 __global__ void __launch_bounds__(256) k_secondary_weights(KArgs a) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y, t = blockIdx.z;
     if (k >= a.K) return;
@@ -271,10 +271,57 @@ __global__ void __launch_bounds__(256) k_secondary_weights(KArgs a) {
         const double v = V[s], f = a.rfac[d * a.S + s];
         const int p = a.slot_map[d * a.NSLOT + s];
         if (v == 0.0 || f == 0.0 || p < 0 || a.ft.sp_kind[s] >= 2) continue;
-        const double sv = sizeof(R) == 4 ? (double)a.Sf[(long long)s * a.K + k] : a.Sd[(long long)s * a.K + k];
-        u = fma(v * f * prm[p], sv, u);
+        u = fma(v * f * prm[p], a.Sd[(long long)s * a.K + k], u);
     }
-    reinterpret_cast<R*>(a.secU)[((long long)t * a.Qtot + q) * a.K + k] = (R)u;
+    reinterpret_cast<double*>(a.secU)[((long long)t * a.Qtot + q) * a.K + k] = u;
+}
+
+// Mixed precision: the weight is added to the adjoint's FP32 pair weights, so it is formed in FP32.
+// The coefficients c_qs = v_sq eps f_ds r_s of a block of SW_Q slices are built once per block
+// (FP64, rounded to FP32) in shared memory; each thread holds one column and reads S'_sk once per
+// block of slices.  Grid (column blocks, toys).
+constexpr int SW_Q = 16;
+__global__ void __launch_bounds__(256) k_secondary_weights_f(KArgs a) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y;
+    const int S = a.S;
+    extern __shared__ float scoef[];                       // [SW_Q][S]
+    int* slist = reinterpret_cast<int*>(scoef + SW_Q * S);  // smeared species
+    __shared__ int ns;
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int sp = 0; sp < S; ++sp)
+            if (a.ft.sp_kind[sp] < 2) slist[n++] = sp;
+        ns = n;
+    }
+    const double* prm = a.params + (long long)t * a.params_stride;
+    float* out = reinterpret_cast<float*>(a.secU) + (long long)t * a.Qtot * a.K;
+    for (int q0 = 0; q0 < a.Qtot; q0 += SW_Q) {
+        const int nq = min(SW_Q, a.Qtot - q0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < SW_Q * S; e += blockDim.x) {
+            const int qq = e / S, sp = e % S;
+            float v = 0.f;
+            if (qq < nq) {
+                const int q = q0 + qq, d = a.sec_ds[a.sq_sec[q]];
+                const double vs = a.secV[((long long)t * a.Qtot + q) * S + sp], f = a.rfac[d * S + sp];
+                const int pp = a.slot_map[d * a.NSLOT + sp];
+                if (vs != 0.0 && f != 0.0 && pp >= 0) v = (float)(vs * f * prm[pp]);
+            }
+            scoef[qq * S + sp] = v;
+        }
+        __syncthreads();
+        if (k >= a.K) continue;
+        float u[SW_Q] = {};
+        for (int i = 0; i < ns; ++i) {
+            const int sp = slist[i];
+            const float sv = a.Sf[(long long)sp * a.K + k];
+#pragma unroll
+            for (int qq = 0; qq < SW_Q; ++qq) u[qq] = fmaf(scoef[qq * S + sp], sv, u[qq]);
+        }
+#pragma unroll
+        for (int qq = 0; qq < SW_Q; ++qq)
+            if (qq < nq) out[(long long)(q0 + qq) * a.K + k] = u[qq];
+    }
 }
 
 cudaError_t launch_secondary(const KArgs& a, cudaStream_t st) {
@@ -283,6 +330,8 @@ cudaError_t launch_secondary(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_slice_sums(const KArgs& a, cudaStream_t st) {
+    // mixed Gaussian and gamma responses: the batched, lanes-on-columns kernel of gsn_mixed.cu
+    if (a.precision == 1 && a.res != 2) return launch_slice_sums_mixed(a, st);
     const dim3 grid((a.K + 255) / 256, a.G, a.T);
     if (a.precision == 1) {
         if (a.res == 0)      k_slice_sums<float, 0><<<grid, 256, 0, st>>>(a);
@@ -297,9 +346,12 @@ cudaError_t launch_slice_sums(const KArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_secondary_weights(const KArgs& a, cudaStream_t st) {
-    const dim3 grid((a.K + 255) / 256, a.Qtot, a.T);
-    if (a.precision == 1) k_secondary_weights<float><<<grid, 256, 0, st>>>(a);
-    else                  k_secondary_weights<double><<<grid, 256, 0, st>>>(a);
+    if (a.precision == 1) {
+        const size_t sh = (size_t)SW_Q * a.S * sizeof(float) + (size_t)a.S * sizeof(int);
+        k_secondary_weights_f<<<dim3((a.K + 255) / 256, a.T), 256, sh, st>>>(a);
+    } else {
+        k_secondary_weights<<<dim3((a.K + 255) / 256, a.Qtot, a.T), 256, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_species_tc(const __grid_constant__ 
                 float v = 0.f;
                 if (!(c[F_XMAX] < xlo_w || c[F_XMIN] > xhi_w)) {
                     v = low ? bin_value_f<RES, NG_LOG_F>(c, xc, del, lam, wt) : bin_value_f<RES, NG_LIN_F>(c, xc, del, lam, wt);
-                    if (RES == 1 && cls == BIN_ZERO) v = valid ? c[F_P0] : 0.f;
+                    if (RES == 1 && cls == BIN_ZERO) v = valid ? zerorec<float>(a, 0, g, k0 + q + e)[Z_P0] : 0.f;
                     v *= c[F_N];
                 }
                 const uint32_t h = tf32_rna(v);

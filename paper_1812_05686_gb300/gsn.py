@@ -81,6 +81,8 @@ def load_library(path: str = LIB_PATH):
         "gsn_minimize_batch_scaled_dev": (C.c_int, [vp, C.c_int, vp, vp, vp, C.POINTER(C.c_ubyte), _DP, _DP, vp,
                                                     C.c_int, C.c_double, C.c_double, C.c_double, vp, vp, vp]),
         "gsn_window_scales_dev": (C.c_int, [vp, C.c_int, vp, vp, _DP, C.c_double, vp]),
+        "gsn_fit_rates_batch_dev": (C.c_int, [vp, C.c_int, vp, vp, vp, C.POINTER(C.c_ubyte), _DP, _DP, C.c_int,
+                                              C.c_double, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -97,7 +99,8 @@ def exported_symbols():
             "gsn_eval_grad_batch", "gsn_eval_grad_batch_dev", "gsn_expected", "gsn_stream",
             "gsn_profile", "gsn_profile_read", "gsn_kernel_name", "gsn_peak_probe", "gsn_eval_grad_noalloc",
             "gsn_plan_info", "gsn_set_dataset_factors", "gsn_set_template", "gsn_minimize_batch_dev",
-            "gsn_set_secondary", "gsn_n_counts", "gsn_minimize_batch_scaled_dev", "gsn_window_scales_dev"]
+            "gsn_set_secondary", "gsn_n_counts", "gsn_minimize_batch_scaled_dev", "gsn_window_scales_dev",
+            "gsn_fit_rates_batch_dev"]
 
 
 GSN_K_COUNT = 8
@@ -285,6 +288,25 @@ class Context:
             self._check(self.lib.gsn_minimize_batch_dev(*head, args[2][1] if args[2] else None, int(max_evals),
                                                         float(gtol), float(ftol), *outs))
         return nll, evals, status
+
+    def fit_rates_batch_dev(self, params, counts, wins, free, lo=None, hi=None, max_iter=0, tol=0.0):
+        """Newton fits over the free rates of every toy (gsn_fit_rates_batch_dev); params (torch,
+        device) is overwritten with the minima.  Returns (nll, iters, status) device tensors."""
+        import torch
+        T = params.shape[0]
+        dev = params.device
+        nll = torch.empty(T, dtype=torch.float64, device=dev)
+        iters = torch.empty(T, dtype=torch.int32, device=dev)
+        status = torch.empty(T, dtype=torch.int32, device=dev)
+        fr = np.ascontiguousarray(np.asarray(free, dtype=np.uint8))
+        lo_ = None if lo is None else _d(lo)
+        hi_ = None if hi is None else _d(hi)
+        self._check(self.lib.gsn_fit_rates_batch_dev(
+            self.h, T, C.c_void_p(params.data_ptr()), C.c_void_p(counts.data_ptr()), C.c_void_p(wins.data_ptr()),
+            fr.ctypes.data_as(C.POINTER(C.c_ubyte)), lo_[1] if lo_ else None, hi_[1] if hi_ else None,
+            int(max_iter), float(tol), C.c_void_p(nll.data_ptr()), C.c_void_p(iters.data_ptr()),
+            C.c_void_p(status.data_ptr())))
+        return nll, iters, status
 
     def window_scales_dev(self, params, wins, scale=None, max_factor=0.0, out=None):
         """Per-toy minimiser scales (gsn_window_scales_dev): a [T][P] device tensor."""

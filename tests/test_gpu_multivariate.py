@@ -49,9 +49,10 @@ def test_slices_against_oracle(slices, precision):
 
 
 @pytest.mark.parametrize("precision", [FP64, MIXED])
-def test_more_datasets_per_slice_than_a_group_holds(precision):
-    """4 datasets share each slice's response: groups of 3 + 1."""
-    w = I.multivariate_like(seed=6, n_datasets=4, n_slices=2, n_bins=80, n_fine=1200, n_species=5)
+@pytest.mark.parametrize("n_datasets", [4, 5])
+def test_datasets_sharing_a_slice_response(precision, n_datasets):
+    """4 datasets share each slice's response (one full group of 4), or 5 (groups of 4 + 1)."""
+    w = I.multivariate_like(seed=6, n_datasets=n_datasets, n_slices=2, n_bins=80, n_fine=1200, n_species=5)
     n = _data(w, 311)
     _check(w, n, I.perturbed_points(w["theta0"], 1, 312)[0], precision)
 
