@@ -1006,9 +1006,13 @@ cudaError_t launch_slice_sums_mixed(const KArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// (toy, group) pairs from which the gamma forward takes two bins per lane: below, a launch (a single
+// point, a few toys) has too few 64-bin segments to fill the GPU, and one bin per lane is faster
+constexpr int FWD2_MIN_PAIRS = 32;
+
 template <int RES, bool FAST>
 static cudaError_t launch_fwd(const KArgs& a, cudaStream_t st, int nds) {
-    if constexpr (RES == 1) {
+    if (RES == 1 && a.T * a.G >= FWD2_MIN_PAIRS) {
         // 64 bins per warp; the grid covers every (toy, group) with the most segments a window can
         // have (a.ntile * 32 FWD_WARPS >= Jmax bins), and blocks past the last segment return at once
         k_fwd_segments<FAST><<<1, 1024, 0, st>>>(a);
@@ -1019,14 +1023,13 @@ static cudaError_t launch_fwd(const KArgs& a, cudaStream_t st, int nds) {
         else if (nds == 3) k_forward_m2<3, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
         else k_forward_m2<4, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
         return cudaGetLastError();
-    } else {
+    }
     dim3 grid(a.ntile, a.nsplit, a.T * a.G);
     if (nds == 1) k_forward_m<RES, 1, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
     else if (nds == 2) k_forward_m<RES, 2, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
     else if (nds == 3) k_forward_m<RES, 3, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
     else k_forward_m<RES, 4, FAST><<<grid, FWD_WARPS * 32, 0, st>>>(a);
     return cudaGetLastError();
-    }
 }
 
 template <int RES, bool FAST, bool SEC>
