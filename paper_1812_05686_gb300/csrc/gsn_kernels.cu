@@ -374,9 +374,10 @@ DEV void count_work(const KArgs& a, int kind, bool lane_valid, long long n_other
         atomicAdd(&a.work[kind], (unsigned long long)n_other * (unsigned long long)__popc(m));
 }
 
-// lanes <-> bins (32 per warp), loop over the columns of the band
+// lanes <-> bins (32 per warp), loop over the columns of the band.  The FP32 generalized gamma is
+// held to 64 registers: four resident blocks per SM instead of three
 template <class R, int RES>
-__global__ void __launch_bounds__(FWD_WARPS * 32) k_forward(KArgs a) {
+__global__ void __launch_bounds__(FWD_WARPS * 32, (sizeof(R) == 4 && RES == 2) ? 4 : 1) k_forward(KArgs a) {
     const int tile = blockIdx.x, split = blockIdx.y;
     const int t = blockIdx.z / a.G, g = blockIdx.z % a.G;
     if (!tb_g_active(a, g)) return;  // no smeared species in the group
@@ -771,8 +772,10 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
         const R p = c[F_KAPPA];
         // FP32, linear bins: side-node terms Q(e), E1(e), e = p ln(x_n/x_c), of the bins of the
         // current 32-bin batch, one bin per lane, handed to every lane by shuffle (the lanes share
-        // the toy and so p); the nodes then follow from the centre by the addition formula
+        // the toy and so p); the nodes then follow from the centre by the addition formula.  FP32
+        // sums run plain within a batch and are folded into the compensated accumulators at its end.
         [[maybe_unused]] float sQ0 = 0.f, sE0 = 0.f, sQ2 = 0.f, sE2 = 0.f;
+        [[maybe_unused]] float bG[4] = {0.f, 0.f, 0.f, 0.f}, bU[MAXGDS] = {};
         for (int j = ja; j <= jb; ++j) {
             if constexpr (sizeof(R) == 4) {
                 if (((j - ja) & 31) == 0) {
@@ -839,17 +842,26 @@ __global__ void __launch_bounds__(256) k_backward(KArgs a) {
                         rho += fw; s1 = fma(fw, l, s1); s2 = fma(fw, y, s2); s3 = fma(fw * y, l, s3);
                     }
                 }
-                const R q[4] = {Wj * rho, Wj * s1, Wj * s2, Wj * s3};
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if constexpr (sizeof(R) == 4) two_sum_acc(Gs[i], Gc[i], q[i]);
-                    else Gs[i] += q[i];
+                if constexpr (sizeof(R) == 4) {
+                    bG[0] = fmaf(Wj, rho, bG[0]); bG[1] = fmaf(Wj, s1, bG[1]);
+                    bG[2] = fmaf(Wj, s2, bG[2]); bG[3] = fmaf(Wj, s3, bG[3]);
+                } else {
+                    Gs[0] += Wj * rho; Gs[1] += Wj * s1; Gs[2] += Wj * s2; Gs[3] += Wj * s3;
                 }
             }
+            if constexpr (sizeof(R) == 4) {
 #pragma unroll
-            for (int dd = 0; dd < MAXGDS; ++dd) {
-                if constexpr (sizeof(R) == 4) two_sum_acc(U0[dd], U0c[dd], wj[dd] * rho);
-                else U0[dd] = fma(wj[dd], rho, U0[dd]);
+                for (int dd = 0; dd < MAXGDS; ++dd)
+                    if (dd < nds) bU[dd] = fmaf(wj[dd], rho, bU[dd]);
+                if (((j - ja) & 31) == 31 || j == jb) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) { two_sum_acc(Gs[i], Gc[i], bG[i]); bG[i] = 0.f; }
+#pragma unroll
+                    for (int dd = 0; dd < MAXGDS; ++dd) { two_sum_acc(U0[dd], U0c[dd], bU[dd]); bU[dd] = 0.f; }
+                }
+            } else {
+#pragma unroll
+                for (int dd = 0; dd < MAXGDS; ++dd) U0[dd] = fma(wj[dd], rho, U0[dd]);
             }
         }
     } else if constexpr (sizeof(R) == 8 && RES == 0) {
