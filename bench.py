@@ -86,6 +86,26 @@ def parse():
 
 
 # ------------------------------------------------------------ inputs -------
+def rank_toy_seed(rank, n_toys):
+    """First toy seed of a rank's batch: ranks draw disjoint toys (weak scaling, no exchange)."""
+    return 1000 + rank * n_toys
+
+
+def max_over_ranks(value, dist, device):
+    """The job's step time: the slowest rank's, returned to every rank (value itself on one rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, n_toys, ms):
+    """Whole-job evaluations per second: every rank's toys over the slowest rank's step time."""
+    return world * n_toys / (ms * 1e-3)
+
+
 def make_inputs(n_toys, seed0, power=None, secondary=None):
     """Toys of the 1200-bin workload; with a power p, the generalized-gamma response (the counts are
     still drawn from the gamma response's expectation: only the model evaluated differs).  With a
@@ -345,7 +365,7 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     T = args.toys
-    w, b = make_inputs(T, 1000 + rank * T, args.power, args.secondary)
+    w, b = make_inputs(T, rank_toy_seed(rank, T), args.power, args.secondary)
     gg = args.power is not None
     sec = args.secondary is not None
     # a dedicated stream: the library launches on it and the timing events are recorded on it
@@ -384,13 +404,10 @@ def run_ours(args, rank, world, local_rank):
     prof = ctx.profile_read()
     ctx.profile(False)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     st = status.cpu().numpy()
     nll_mixed = nll.cpu().numpy()
-    value = world * T / (ms * 1e-3)
+    value = job_rate(world, T, ms)
 
     # FP64 path on a stride of toys over the whole batch (every launch chunk): throughput and the
     # mixed path's errors against it (--fp64-toys 0: skipped)
