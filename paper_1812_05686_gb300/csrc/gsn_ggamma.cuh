@@ -16,9 +16,12 @@ namespace gsn {
 
 constexpr double GG_XSTIR = 10.0;
 
-// lnGamma(z) - [(z - 1/2) ln z - z + ln(2 pi)/2] for z >= 10: sum_n B_2n / (2n (2n-1) z^(2n-1)), n <= 8
-DEV double gg_lgamma_tail(double z) {
-    const double iz = 1.0 / z, v = iz * iz;
+// Stirling tails at one argument z >= 10, sharing 1/z:
+//   lt = lnGamma(z) - [(z - 1/2) ln z - z + ln(2 pi)/2] = sum_n B_2n / (2n (2n-1) z^(2n-1)), n <= 8
+//   dt = psi(z) - [ln z - 1/(2z)] = -sum_n B_2n / (2n z^2n), n <= 8
+DEV void gg_tails(double z, double& lt, double& dt, double& iz) {
+    iz = 1.0 / z;
+    const double v = iz * iz;
     double s = fma(v, -3617.0 / 122400, 1.0 / 156);
     s = fma(s, v, -691.0 / 360360);
     s = fma(s, v, 1.0 / 1188);
@@ -26,64 +29,39 @@ DEV double gg_lgamma_tail(double z) {
     s = fma(s, v, 1.0 / 1260);
     s = fma(s, v, -1.0 / 360);
     s = fma(s, v, 1.0 / 12);
-    return s * iz;
-}
-// psi(z) - [ln z - 1/(2z)] for z >= 10: -sum_n B_2n / (2n z^2n), n <= 8
-DEV double gg_digamma_tail(double z) {
-    const double iz = 1.0 / z, v = iz * iz;
-    double s = fma(v, -3617.0 / 8160, 1.0 / 12);
-    s = fma(s, v, -691.0 / 32760);
-    s = fma(s, v, 1.0 / 132);
-    s = fma(s, v, -1.0 / 240);
-    s = fma(s, v, 1.0 / 252);
-    s = fma(s, v, -1.0 / 120);
-    s = fma(s, v, 1.0 / 12);
-    return -s * v;
+    lt = s * iz;
+    double u = fma(v, -3617.0 / 8160, 1.0 / 12);
+    u = fma(u, v, -691.0 / 32760);
+    u = fma(u, v, 1.0 / 132);
+    u = fma(u, v, -1.0 / 240);
+    u = fma(u, v, 1.0 / 252);
+    u = fma(u, v, -1.0 / 120);
+    u = fma(u, v, 1.0 / 12);
+    dt = -u * v;
 }
 DEV int gg_shift(double x) { return x >= GG_XSTIR ? 0 : (int)ceil(GG_XSTIR - x); }
 
-// lnGamma(x + c) - lnGamma(x), x > 0, c >= 0
-DEV double gg_lgamma_diff(double x, double c) {
+// H(x) = ln[Gamma(x + 2a) Gamma(x) / Gamma(x + a)^2] and dH/dx = psi(x + 2a) - 2 psi(x + a) + psi(x),
+// evaluated together (the tails at x, x + a, x + 2a and ln(1 - q^2), q = a/(x + a), serve both)
+DEV void gg_H_Hx(double x, double a, double& H, double& Hx) {
     const int m = gg_shift(x);
     const double xm = x + m;
-    double r = fma(xm - 0.5, log1p(c / xm), c * log(xm + c) - c) + (gg_lgamma_tail(xm + c) - gg_lgamma_tail(xm));
-    for (int i = 0; i < m; ++i) r -= log1p(c / (x + i));
-    return r;
-}
-// psi(x + c) - psi(x)
-DEV double gg_digamma_diff(double x, double c) {
-    const int m = gg_shift(x);
-    const double xm = x + m;
-    double r = log1p(c / xm) + c / (2.0 * xm * (xm + c)) + (gg_digamma_tail(xm + c) - gg_digamma_tail(xm));
-    for (int i = 0; i < m; ++i) r += c / ((x + i) * (x + c + i));
-    return r;
-}
-// H(x) = ln[Gamma(x + 2a) Gamma(x) / Gamma(x + a)^2]
-DEV double gg_H(double x, double a) {
-    const int m = gg_shift(x);
-    const double xm = x + m;
-    const double e = a / xm, q = e / (1.0 + e);
-    double r = fma(xm - 0.5, log1p(-q * q), 2.0 * a * log1p(a / (xm + a))) +
-               ((gg_lgamma_tail(xm + 2.0 * a) - 2.0 * gg_lgamma_tail(xm + a)) + gg_lgamma_tail(xm));
+    double l0, d0, i0, l1, d1, i1, l2, d2, i2;
+    gg_tails(xm, l0, d0, i0);
+    gg_tails(xm + a, l1, d1, i1);
+    gg_tails(xm + 2.0 * a, l2, d2, i2);
+    const double q = a * i1;
+    const double lq = log1p(-q * q);
+    double h = fma(xm - 0.5, lq, 2.0 * a * log1p(q)) + ((l2 - 2.0 * l1) + l0);
+    double hx = lq - a * a * (i0 * i1 * i2) + ((d2 - 2.0 * d1) + d0);
     for (int i = 0; i < m; ++i) {
         const double xi = x + i, ei = a / xi;
-        if (ei < 0.5) { const double qi = ei / (1.0 + ei); r -= log1p(-qi * qi); }
-        else r -= log(xi) + log(xi + 2.0 * a) - 2.0 * log(xi + a);
+        if (ei < 0.5) { const double qi = ei / (1.0 + ei); h -= log1p(-qi * qi); }
+        else h -= log(xi) + log(xi + 2.0 * a) - 2.0 * log(xi + a);
+        hx -= 2.0 * a * a / (xi * (xi + a) * (xi + 2.0 * a));
     }
-    return r;
-}
-// dH/dx = psi(x + 2a) - 2 psi(x + a) + psi(x)
-DEV double gg_Hx(double x, double a) {
-    const int m = gg_shift(x);
-    const double xm = x + m;
-    const double q = a / (xm + a);
-    double r = log1p(-q * q) - a * a / (xm * (xm + a) * (xm + 2.0 * a)) +
-               ((gg_digamma_tail(xm + 2.0 * a) - 2.0 * gg_digamma_tail(xm + a)) + gg_digamma_tail(xm));
-    for (int i = 0; i < m; ++i) {
-        const double xi = x + i;
-        r -= 2.0 * a * a / (xi * (xi + a) * (xi + 2.0 * a));
-    }
-    return r;
+    H = h;
+    Hx = hx;
 }
 
 // x = d/p solving H(x) = r = ln(1 + var/mu^2): Newton's method on ln H against ln x, started from
@@ -102,8 +80,8 @@ DEV double gg_solve_shape(double r, double a, double& lnx, double& hx) {
     if (!(x > 0.0) || !isfinite(x) || x < 0.5 / y0) x = 1.0 / y0;
     double u = log(x);
     for (int it = 0; it < 60; ++it) {
-        const double h = gg_H(x, a);
-        hx = gg_Hx(x, a);
+        double h;
+        gg_H_Hx(x, a, h, hx);
         const double step = fmin(5.0, fmax(-5.0, -log(h / r) * h / (x * hx)));
         u += step;
         x = exp(u);
@@ -116,12 +94,33 @@ DEV double gg_solve_shape(double r, double a, double& lnx, double& hx) {
     return -1.0;
 }
 
-// lnGamma(x) and psi(x) from Stirling's series for x >= 10 (lx = ln x), library / recurrence below
-DEV double gg_lgamma(double x, double lx) {
-    return x >= GG_XSTIR ? fma(x - 0.5, lx, -x) + 0.91893853320467274178 + gg_lgamma_tail(x) : lgamma(x);
-}
-DEV double gg_digamma(double x, double lx) {
-    return x >= GG_XSTIR ? lx - 0.5 / x + gg_digamma_tail(x) : digamma_d(x);
+// At the matched shape x = d/p (lx = ln x): ls = lnGamma(x + a) - lnGamma(x), psi(x), lnGamma(x) and
+// da = psi(x + a) - psi(x), evaluated together (the tails at x and x + a and ln(1 + a/x) serve all
+// four; below 10 the recurrences move the differences' arguments, and lnGamma / psi come from the
+// library / digamma_d)
+DEV void gg_at_shape(double x, double lx, double a, double& ls, double& psi, double& lgx, double& da) {
+    const int m = gg_shift(x);
+    const double xm = x + m;
+    double l0, d0, i0, l1, d1, i1;
+    gg_tails(xm, l0, d0, i0);
+    gg_tails(xm + a, l1, d1, i1);
+    const double lq = log1p(a * i0);
+    double g = fma(xm - 0.5, lq, a * log(xm + a) - a) + (l1 - l0);
+    double dd = lq + 0.5 * a * (i0 * i1) + (d1 - d0);
+    for (int i = 0; i < m; ++i) {
+        const double xi = x + i;
+        g -= log1p(a / xi);
+        dd += a / (xi * (xi + a));
+    }
+    ls = g;
+    da = dd;
+    if (m == 0) {
+        psi = lx - 0.5 * i0 + d0;
+        lgx = fma(x - 0.5, lx, -x) + 0.91893853320467274178 + l0;
+    } else {
+        psi = digamma_d(x);
+        lgx = lgamma(x);
+    }
 }
 
 // ---- FP32 helpers of the mixed path ----
@@ -192,12 +191,11 @@ DEV double gg_column(double mu, double var, double p, double cut, double x1, boo
     double Hx, lxs;                                   // dH/dx at the root, ln(d/p)
     const double xs = gg_solve_shape(r, a, lxs, Hx);  // d/p
     const double d = p * xs;
-    const double ls = gg_lgamma_diff(xs, a);          // ln(mu/s)
+    double ls, psi, lgx, da;                          // ln(mu/s), psi(d/p), lnGamma(d/p), psi(d/p + a) - psi(d/p)
+    gg_at_shape(xs, lxs, a, ls, psi, lgx, da);
     const double lns = log(mu) - ls;                  // ln s
     const double A = exp(p * ls);                     // (mu/s)^p
     const double k1 = (d - 1.0) - p * A;
-    const double psi = gg_digamma(xs, lxs);
-    const double lgx = gg_lgamma(xs, lxs);
     // density at the mean: ln f(mu) = ln p - ln mu + d ln(mu/s) - A - lnGamma(d/p)
     const double lfm = log(p) - log(mu) + d * ls - A - lgx;
     double Nk = 1.0;
@@ -261,7 +259,6 @@ DEV double gg_column(double mu, double var, double p, double cut, double x1, boo
     z[Z_P0] = (R)(P0 / Nk);
     // moment matching H(x, a) = ln rho, ln s = ln mu - G(x, a): implicit derivatives of x and u = ln s
     // dH/da = 2 [psi(x + 2a) - psi(x + a)] = 2 (dH/dx + [psi(x + a) - psi(x)]): no cancellation
-    const double da = gg_digamma_diff(xs, a);
     const double Ha = 2.0 * (Hx + da);
     const double Gx = da, Ga = psi + da;              // psi(x + a) = psi(x) + [psi(x + a) - psi(x)]
     const double r_mu = -2.0 * var / (mu * (mu * mu + var)), r_var = 1.0 / (mu * mu + var);
