@@ -26,9 +26,10 @@ namespace gsn {
 
 constexpr float SQ_HALF_L2E = 0.84932180028801904f;   // sqrt(log2(e) / 2)
 constexpr float SQ_HALF_L2E_LO = (float)(0.84932180028801904 - (double)SQ_HALF_L2E);
-// Columns of shape d >= D_POLY take the branch-free series for ln(1+t) - t: inside their band
-// every point with density above ~1e-8 of the peak has |t/(2+t)| <= 1/3, and the truncated
-// series stays finite and far below the cut elsewhere.
+// Columns of shape d >= D_POLY take a branch-free series for ln(1+t) - t, through u^11
+// (u = t/(2+t)): inside their band |u| <= 0.5 (d = 50, the far left tail; 0.35 at d = 100), and
+// the omitted terms, 2 u^13/13 + ..., change a column's mass over its band by at most 4e-10
+// (d = 50; 6e-12 at d = 100, 1e-14 at d = 300), below the FP32 roundings of its constants.
 constexpr float D_POLY = 50.0f;
 
 // record fields after the per-warp transformation of the forward kernel
@@ -80,9 +81,7 @@ DEV float2 rcp2(float2 x) {
 DEV float2 log1pmx_poly2(float2 t, float2 nt) {
     const float2 u = mul2(t, rcp2(add2(t, f2(2.0f))));
     const float2 v = mul2(u, u);
-    float2 p = fma2(v, f2(2.0f / 15.0f), f2(2.0f / 13.0f));
-    p = fma2(p, v, f2(2.0f / 11.0f));
-    p = fma2(p, v, f2(2.0f / 9.0f));
+    float2 p = fma2(v, f2(2.0f / 11.0f), f2(2.0f / 9.0f));
     p = fma2(p, v, f2(2.0f / 7.0f));
     p = fma2(p, v, f2(2.0f / 5.0f));
     p = fma2(p, v, f2(2.0f / 3.0f));
