@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
         // per-column constants of the packed path
         const float2 Av = f2(A), nAv = f2(-A), nmuhv = f2(-c[F_MUH]), nmulv = f2(-c[F_MUL]);
         const float2 Q2v = f2(Q2), R2v = f2(R2), nR2v = f2(-R2), mL2EAv = f2(mL2EA), nXMv = f2(nXM);
-        const float2 kapv = f2(kap), twokapv = f2(2.0f * kap);
+        const float2 kapv = f2(kap);
         const float2 TN0v = f2(TN0), TN1v = f2(TN1), TN2v = f2(TN2), TN3v = f2(TN3);
         for (int jj0 = jstart; jj0 <= jb;) {
             {
@@ -707,9 +707,10 @@ __global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
                     const float2 rho = add2(add2(e0, ep), em);
                     const float2 Ls = fma2(ep, lp, mul2(em, lm));                  // sum w f ln(x_n / x_c)
                     const float2 XAn = mul2(fma2(ep, f2(-1.f), em), mul2(dl, Av));  // -sum w f (x_n - x_c) / mu
-                    const float2 cmu = fma2(f2(2.f), Dt, add2(tt, twokapv));        // 2 (ln(1+t) + kappa) - t
+                    const float2 gk = add2(Dt, kapv);                               // D + kappa
+                    const float2 cmu = fma2(f2(2.f), gk, tt);                       // 2 (ln(1+t) + kappa) - t
                     const float2 u1 = fma2(cmu, rho, fma2(f2(2.f), Ls, XAn));
-                    const float2 nu2 = fma2(add2(Dt, kapv), rho, add2(XAn, Ls));
+                    const float2 nu2 = fma2(gk, rho, add2(XAn, Ls));
                     a0 = fma2(wd0, rho, a0);
                     if (NDS > 1) a1 = fma2(wd1, rho, a1);
                     if (NDS > 2) a2 = fma2(wd2, rho, a2);
