@@ -497,8 +497,10 @@ __global__ void __launch_bounds__(FWD_WARPS * 32, GSN_FWD_MINBLOCKS) k_forward_m
 // active slice q of a dataset of the group adds U_qk N_k to its weight (k_secondary_weights); the
 // batches of linear bins then end at the slices' edges, so the added weight is one per-column value
 // per batch.
+// Groups of three or four datasets keep twice as many accumulators: their adjoint gets the register
+// budget of three resident blocks (80 registers; at 64 it spilled ~300 bytes per thread).
 template <int RES, int NDS, bool FAST, bool SEC>
-__global__ void __launch_bounds__(256, GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
+__global__ void __launch_bounds__(256, NDS > 2 ? 3 : GSN_BW_MINBLOCKS) k_backward_m(KArgs a) {
     const int task = blockIdx.x, g = blockIdx.y, t = blockIdx.z;
     if (!tb_g_active<FAST>(a, g)) return;  // no smeared species in the group
     const int W = a.bw_warps;
