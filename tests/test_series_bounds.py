@@ -42,3 +42,31 @@ def test_truncated_series_changes_a_column_mass_within_the_stated_bound(d, bound
 def test_one_more_omitted_term_would_break_the_bound():
     rel, _ = _mass_change(50.0, 4)       # through u^9
     assert rel > 1e-9, rel
+
+
+def test_mode_offset_series_matches_its_closed_form():
+    """The gamma column's exponent offset XM = log2 f(mode)/f(mu), for shape d >= 8, is summed as
+    M(d) = (d-1) ln(1 - 1/d) + 1 = sum_k u^k / (k (k+1)), u = 1/d, truncated after u^8 (the column
+    prologue's series); held against the closed form evaluated with log1p in FP64."""
+    d = np.geomspace(8.0, 1e5, 2000)
+    u = 1.0 / d
+    m = np.zeros_like(u)
+    for k in reversed(range(1, 9)):
+        m = (m + 1.0 / (k * (k + 1))) * u
+    exact = (d - 1.0) * np.log1p(-1.0 / d) + 1.0
+    assert np.max(np.abs(m / exact - 1.0)) < 2e-9
+
+
+def test_normalisation_exponential_polynomial():
+    """exp(y) of the column normalisation, |y| < 0.06 (y = XM ln 2 - Stirling remainder, d >= 8),
+    by its degree-6 Taylor polynomial: remainder below 1e-12 relative."""
+    y = np.linspace(-0.06, 0.06, 20001)
+    p = np.zeros_like(y)
+    for k in reversed(range(7)):
+        p = p * y + 1.0 / np.prod(np.arange(1, k + 1, dtype=float))
+    assert np.max(np.abs(p / np.exp(y) - 1.0)) < 1e-12
+    # the argument's range: XM ln 2 - corr for d >= 8
+    d = np.geomspace(8.0, 1e5, 2000)
+    xm = np.log2(np.e) * ((d - 1.0) * np.log1p(-1.0 / d) + 1.0)
+    corr = 1.0 / (12.0 * d) - 1.0 / (360.0 * d ** 3)
+    assert np.max(np.abs(xm * np.log(2.0) - corr)) < 0.06
