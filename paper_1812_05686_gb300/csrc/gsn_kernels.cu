@@ -699,9 +699,10 @@ __global__ void __launch_bounds__(256) k_devfinal(KArgs a) {
 }
 
 // ------------------------------------------------------------ backward -----
-// lanes <-> columns; each warp sweeps the bins of its columns' band.
+// lanes <-> columns; each warp sweeps the bins of its columns' band.  The FP32 generalized gamma is
+// held to 64 registers (four resident blocks per SM instead of three)
 template <class R, int RES>
-__global__ void __launch_bounds__(256) k_backward(KArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && RES == 2) ? 4 : 1) k_backward(KArgs a) {
     const int task = blockIdx.x, g = blockIdx.y, t = blockIdx.z;
     if (!tb_g_active(a, g)) return;  // no smeared species in the group
     const int W = a.bw_warps;
